@@ -1,0 +1,239 @@
+/*
+ * chemo.h -- C ABI of the GB300 (sm_103a) particle step of the hybrid
+ * chemotaxis model of Bruna, Maini & Robinson, "Particle-based simulations of
+ * reaction-diffusion processes with Aboria" (arXiv:1805.11007).
+ *
+ * One simulation object holds N cells (point particles of up to 8 species)
+ * in a 2D or 3D box and, optionally, the chemical concentration c on a
+ * regular grid. One step (chemo_step) advances both by dt:
+ *
+ *   a1  bin each cell into a cell list (Sect. 2.2, 3.1: neighbourhood search)
+ *   a2  counting-sort the cells by bin (Z-order) and build the bin offsets
+ *   a3  sum the finite-range soft repulsion over neighbouring bins
+ *       (Sect. 3.2 interaction loop; pair term of Eq. (1a)/(1b))
+ *   a4  interpolate the central-difference gradient of c^n to each cell
+ *       (Sect. 2.3, 3.5 D1x/D1y, 3.6) for the chemotactic drift of Eq. (1b)
+ *   a5  Euler-Maruyama move (Eq. (2)) with reflecting walls (Sect. 3.2) or a
+ *       periodic box with unwrapped displacement (Sect. 4)
+ *   a6  deposit the secretion (and consumption) of the moved cells on the
+ *       grid by cloud-in-cell weights (Sect. 2.3, random measures Eq. (1e))
+ *   a7  explicit PDE step of Eq. (1d): centred differences in space, forward
+ *       Euler in time (Sect. 3.5), with substeps when stability requires.
+ *
+ * Conventions (every function):
+ *   - returns an int status (CHEMO_OK = 0, negative on error) and never
+ *     throws; chemo_last_error() gives a thread-local message;
+ *   - pointers passed in are borrowed for the duration of the call only;
+ *     the library owns all device memory of a simulation;
+ *   - `mem_kind` says where a caller buffer lives: CHEMO_MEM_HOST (pageable
+ *     or pinned host memory; the call synchronises the stream before it
+ *     returns) or CHEMO_MEM_DEVICE (device memory of the current device; the
+ *     call is asynchronous on `stream`);
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); work is
+ *     ordered on it. Errors found on the device (non-finite position, bin or
+ *     buffer overflow, a bounded wait that ran out) are latched in the
+ *     simulation and reported by the next chemo_check / chemo_read_* call.
+ *   - Particle arrays are indexed by particle id (0..n-1, the order given to
+ *     chemo_create); positions are n x dim row-major float32; grids are
+ *     C-order [z][y][x] float32 with x fastest (2D: [y][x]).
+ */
+#ifndef CHEMO_H
+#define CHEMO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CHEMO_ABI_VERSION 1
+#define CHEMO_MAX_SPECIES 8
+
+/* Status codes. */
+enum {
+    CHEMO_OK = 0,
+    CHEMO_EINVAL = -1,     /* invalid argument or parameter set */
+    CHEMO_ENOMEM = -2,     /* device or host allocation failed */
+    CHEMO_ECUDA = -3,      /* a CUDA runtime call failed */
+    CHEMO_EDOMAIN = -4,    /* a particle left the domain */
+    CHEMO_ENONFINITE = -5, /* a non-finite position appeared */
+    CHEMO_EOVERFLOW = -6,  /* a bin, buffer or index range overflowed */
+    CHEMO_ETIMEOUT = -7,   /* a bounded device-side wait gave up */
+    CHEMO_ENOTSUP = -8     /* option not supported by this build */
+};
+
+enum { CHEMO_MEM_HOST = 0, CHEMO_MEM_DEVICE = 1 };
+
+/* Model parameters, copied at chemo_create / chemo_set_params.
+ * Defaults: zero-fill the struct, then set struct_size = sizeof(chemo_params)
+ * and the fields below. Per-species arrays use entries [0, n_species). */
+typedef struct chemo_params {
+    uint32_t struct_size;        /* sizeof(chemo_params), for ABI checks */
+    int32_t dim;                 /* 2 or 3 (the paper's model is 2D, Sect. 2) */
+    int32_t boundary;            /* 0 reflecting walls (Sect. 3.2), 1 periodic (Sect. 4) */
+    double lo[3], hi[3];         /* domain box [lo, hi] per axis */
+    int32_t n_species;           /* 1..8 (the paper: alpha = 0, beta = 1) */
+    float diameter[CHEMO_MAX_SPECIES];    /* sigma_s; pair length eps_ij = (sigma_i+sigma_j)/2 */
+    float D[CHEMO_MAX_SPECIES];           /* diffusivity D_s, Eq. (1a)/(1b) */
+    float chemotactic[CHEMO_MAX_SPECIES]; /* multiplier of chi (Eq. (1b): beta 1, alpha 0) */
+    float secrete[CHEMO_MAX_SPECIES];     /* k_s: source k_s rho_s of Eq. (1d) */
+    float consume[CHEMO_MAX_SPECIES];     /* kappa_s: sink -kappa_s rho_s c of Eq. (1d) */
+    float react_k0[CHEMO_MAX_SPECIES];    /* constant switching rate (r_alpha, Eq. (1c)) */
+    float react_kc[CHEMO_MAX_SPECIES];    /* switching rate per unit c (r_beta(c), Eq. (1c)) */
+    int32_t react_to[CHEMO_MAX_SPECIES];  /* species a switching cell becomes */
+    int32_t reactions;           /* 0 off, 1 fixed-step switching (Sect. 2.1, 3.4) */
+    float chi;                   /* chemotactic sensitivity chi, Eq. (1b) */
+    float inter;                 /* strength of the soft repulsion (Sect. 3.2) */
+    float cutoff_factor;         /* r_c,ij = cutoff_factor * eps_ij (default 1) */
+    int32_t cutoff_mode;         /* 0 hard truncation at r_c (as in Sect. 3.2),
+                                    1 force shifted to zero at r_c */
+    int32_t chem_mode;           /* 0 chemical on the grid (Eq. (1d)),
+                                    1 fixed gradient fixed_grad (Sect. 4, c = x) */
+    float fixed_grad[3];
+    int32_t grid[3];             /* nodes per axis (>= 3); nodes at lo + k h with
+                                    h = L/(N-1) (walls) or L/N (periodic) */
+    float Dc, gamma;             /* chemical diffusivity and decay, Eq. (1d) */
+    int32_t pde_bc;              /* 0 Neumann / no flux (mirror ghost nodes),
+                                    1 Dirichlet (wall nodes held), 2 periodic */
+    int32_t pde_substeps;        /* 0 = automatic: s = ceil(sum_a 2 Dc dt/h_a^2 / 0.9) */
+    double dt;                   /* time step */
+    uint64_t seed;               /* Philox4x32-10 key (seed lo, seed hi) */
+    int32_t track_displacement;  /* keep the unwrapped displacement (Sect. 4, MSD) */
+    float bin_side;              /* cell-list bin side (0 = automatic) */
+    int32_t search_mode;         /* 0 automatic, 1 3^d bins of side >= r_c,
+                                    2 2^d bins of side >= 2 r_c */
+    int32_t bin_order;           /* 0 automatic, 1 row-major (x fastest), 2 Z-order */
+} chemo_params;
+
+/* Layout facts of a simulation (read-only). */
+typedef struct chemo_info {
+    int64_t n;                   /* particles */
+    int32_t dim;
+    int32_t search_mode;         /* 1 or 2, as resolved */
+    int32_t nbins[3];            /* bins per axis */
+    int64_t bin_slots;           /* entries of the bin table (Morton padded) */
+    float bin_side[3];
+    int32_t morton;              /* 1 if bins are stored in Z-order */
+    int32_t pde_substeps;        /* as resolved */
+    int64_t grid_nodes;
+    int64_t device_bytes;        /* device memory held by the simulation */
+    int32_t launches_per_step;   /* kernels one chemo_step launches */
+} chemo_info;
+
+typedef struct chemo_sim chemo_sim;
+
+/* Creates a simulation of n cells. pos: n x dim float32 positions (inside
+ * the box), species: n uint8 values < n_species; both in memory of mem_kind.
+ * Particle ids are 0..n-1 in input order; the Philox counter of a cell is
+ * (id, step lo, stream tag, step hi). The chemical field starts at 0 (set it
+ * with chemo_write_field). n = 0 is allowed. On success *out receives the
+ * handle; release it with chemo_destroy. Errors: EINVAL (bad parameters:
+ * dim, species, grid < 3 nodes, periodic box narrower than 2 r_c, more than
+ * 2^29 particles...), ENOMEM, ECUDA. */
+int chemo_create(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species,
+                 int mem_kind, void *stream, chemo_sim **out);
+
+/* Replaces the particle state: pos (n x dim), species (n) and, if the
+ * simulation tracks it, disp (n x dim, NULL = zero). Ids are the array
+ * indices. The step index is kept. */
+int chemo_write_state(chemo_sim *sim, const float *pos, const uint8_t *species, const float *disp,
+                      int mem_kind, void *stream);
+
+/* Replaces the chemical field c (grid_nodes float32, C-order). EINVAL if the
+ * simulation has no grid (chem_mode 1). */
+int chemo_write_field(chemo_sim *sim, const float *c, int mem_kind, void *stream);
+
+/* Advances one step dt (rows a1-a7 above) on stream. */
+int chemo_step(chemo_sim *sim, void *stream);
+
+/* Advances nsteps steps; the result equals nsteps calls of chemo_step. The
+ * steps are replayed from a CUDA graph captured on first use. */
+int chemo_step_n(chemo_sim *sim, int64_t nsteps, void *stream);
+
+/* Copies the state out by particle id: pos_out (n x dim), species_out (n),
+ * disp_out (n x dim; EINVAL if not tracked). Any output may be NULL.
+ * Synchronises `stream` when mem_kind is HOST and reports latched device
+ * errors. */
+int chemo_read_state(chemo_sim *sim, float *pos_out, uint8_t *species_out, float *disp_out,
+                     int mem_kind, void *stream);
+
+/* Copies the chemical field c^n out (grid_nodes float32, C-order). */
+int chemo_read_field(chemo_sim *sim, float *c_out, int mem_kind, void *stream);
+
+/* Vector-Jacobian product of nsteps steps (adjoint of chemo_step_n) with
+ * checkpoints every ckpt_every steps: given dL/dpos of the final state (and
+ * optionally dL/dc), returns dL/dparams = [chi, inter, D_0..D_{S-1}] and,
+ * if dL_dpos0 is non-NULL, dL/dpos of the initial state. The forward noise
+ * is frozen (same Philox counters). The simulation state is left at the
+ * final step. Not available in this build: returns ENOTSUP. */
+int chemo_gradient(chemo_sim *sim, int64_t nsteps, int32_t ckpt_every, const float *dL_dpos_final,
+                   const float *dL_dc_final, float *dL_dparams, float *dL_dpos0, int mem_kind,
+                   void *stream);
+
+/* Replaces the model parameters of a live simulation. Geometry (dim, box,
+ * grid, boundary, species count, bin layout) must not change: EINVAL. */
+int chemo_set_params(chemo_sim *sim, const chemo_params *params);
+
+/* Absolute index of the next step (0 after create). */
+int64_t chemo_step_index(const chemo_sim *sim);
+
+/* Sets the absolute step index (the Philox counter of the next step). */
+int chemo_set_step_index(chemo_sim *sim, int64_t step, void *stream);
+
+/* Synchronises stream and returns the first latched device error, then
+ * clears it. */
+int chemo_check(chemo_sim *sim, void *stream);
+
+/* Fills *info. */
+int chemo_get_info(const chemo_sim *sim, chemo_info *info);
+
+/* Releases every resource of sim (NULL is ignored). Synchronises the device
+ * work of the simulation first. */
+void chemo_destroy(chemo_sim *sim);
+
+/* Static text of a status code. */
+const char *chemo_status_string(int status);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *chemo_last_error(void);
+
+/* ---------------------------------------------------------------------- */
+/* Stage-level entry points. They run the step's own kernels on the current */
+/* state without advancing it, so each row of the step can be checked on   */
+/* its own. Outputs are indexed by particle id unless stated.              */
+/* ---------------------------------------------------------------------- */
+
+/* Raw Philox4x32-10 words (Salmon et al., SC'11) of the device generator:
+ * ctr n x 4 uint32, key (seed lo, seed hi), out n x 4 uint32. */
+int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, int mem_kind,
+                 void *stream);
+
+/* Row a1: the bin cell of every particle, n x dim int32 (cell coordinates
+ * per axis, not the Morton key). */
+int chemo_stage_bins(chemo_sim *sim, int32_t *cells_out, int mem_kind, void *stream);
+
+/* Row a2: the sorted order: ids_out[j] = id of the j-th particle in the
+ * sorted (binned) arrays (n uint32), and bin_start_out (bin_slots + 1
+ * uint32) the offsets of every bin slot in that order (NULL to skip). */
+int chemo_stage_sort(chemo_sim *sim, uint32_t *ids_out, uint32_t *bin_start_out, int mem_kind,
+                     void *stream);
+
+/* Row a3: the pair force F_i (n x dim float32), and optionally per particle
+ * the number of neighbours inside the cutoff (count_out, n int32) and the
+ * sum of their ids (idsum_out, n uint64). */
+int chemo_stage_forces(chemo_sim *sim, float *F_out, int32_t *count_out, uint64_t *idsum_out,
+                       int mem_kind, void *stream);
+
+/* Row a4: the chemotactic drift chi * chemotactic_s * grad c(X_i) (n x dim). */
+int chemo_stage_drift(chemo_sim *sim, float *drift_out, int mem_kind, void *stream);
+
+/* Row a6: the density terms deposited by the current positions on the grid:
+ * S_out = dt sum_i k_s w_ik/(tau_k h^d) and R_out = sum_i kappa_s w_ik/(tau_k
+ * h^d) (grid_nodes each, C-order; either may be NULL). */
+int chemo_stage_deposit(chemo_sim *sim, float *S_out, float *R_out, int mem_kind, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHEMO_H */

@@ -1,0 +1,416 @@
+"""ctypes binding of the GB300 chemotaxis-step library (``include/chemo.h``).
+
+Argument marshalling only: every step of the path runs in the CUDA kernels of
+``libchemo_gb300.so``. The functions carry the C ABI's names. Buffers may be
+CUDA torch tensors (device memory; asynchronous on the given stream) or numpy
+arrays / CPU tensors (host memory; the call synchronises). ``stream`` is a
+``torch.cuda.Stream``, a raw ``cudaStream_t`` integer, or None (the current
+torch stream when torch is loaded, else the legacy default stream).
+
+The library must have been built (``paper_1805_11007_gb300.build.build()`` or
+``__graft_entry__.build()``); importing this module without it fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAXS = 8
+OK, EINVAL, ENOMEM, ECUDA, EDOMAIN, ENONFINITE, EOVERFLOW, ETIMEOUT, ENOTSUP = 0, -1, -2, -3, -4, -5, -6, -7, -8
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+class ChemoError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%d): %s" % (where, _status_text(status), status, msg))
+        self.status = status
+
+
+class chemo_params(ctypes.Structure):
+    _fields_ = [
+        ("struct_size", ctypes.c_uint32),
+        ("dim", ctypes.c_int32),
+        ("boundary", ctypes.c_int32),
+        ("lo", ctypes.c_double * 3),
+        ("hi", ctypes.c_double * 3),
+        ("n_species", ctypes.c_int32),
+        ("diameter", ctypes.c_float * MAXS),
+        ("D", ctypes.c_float * MAXS),
+        ("chemotactic", ctypes.c_float * MAXS),
+        ("secrete", ctypes.c_float * MAXS),
+        ("consume", ctypes.c_float * MAXS),
+        ("react_k0", ctypes.c_float * MAXS),
+        ("react_kc", ctypes.c_float * MAXS),
+        ("react_to", ctypes.c_int32 * MAXS),
+        ("reactions", ctypes.c_int32),
+        ("chi", ctypes.c_float),
+        ("inter", ctypes.c_float),
+        ("cutoff_factor", ctypes.c_float),
+        ("cutoff_mode", ctypes.c_int32),
+        ("chem_mode", ctypes.c_int32),
+        ("fixed_grad", ctypes.c_float * 3),
+        ("grid", ctypes.c_int32 * 3),
+        ("Dc", ctypes.c_float),
+        ("gamma", ctypes.c_float),
+        ("pde_bc", ctypes.c_int32),
+        ("pde_substeps", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+        ("track_displacement", ctypes.c_int32),
+        ("bin_side", ctypes.c_float),
+        ("search_mode", ctypes.c_int32),
+        ("bin_order", ctypes.c_int32),
+    ]
+
+
+class chemo_info(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int64),
+        ("dim", ctypes.c_int32),
+        ("search_mode", ctypes.c_int32),
+        ("nbins", ctypes.c_int32 * 3),
+        ("bin_slots", ctypes.c_int64),
+        ("bin_side", ctypes.c_float * 3),
+        ("morton", ctypes.c_int32),
+        ("pde_substeps", ctypes.c_int32),
+        ("grid_nodes", ctypes.c_int64),
+        ("device_bytes", ctypes.c_int64),
+        ("launches_per_step", ctypes.c_int32),
+    ]
+
+
+def make_params(d: dict) -> chemo_params:
+    """chemo_params from a dict keyed by the field names (missing = 0 /
+    library defaults; per-species lists may be shorter than 8)."""
+    p = chemo_params()
+    p.struct_size = ctypes.sizeof(chemo_params)
+    p.dim = int(d["dim"])
+    p.boundary = int(d.get("boundary", 0))
+    for a in range(3):
+        p.lo[a] = float(d.get("lo", [0.0] * 3)[a])
+        p.hi[a] = float(d.get("hi", [1.0] * 3)[a])
+    ns = int(d["n_species"])
+    p.n_species = ns
+    for name in ("diameter", "D", "chemotactic", "secrete", "consume", "react_k0", "react_kc"):
+        vals = list(d.get(name, [0.0] * ns))
+        arr = getattr(p, name)
+        for s in range(MAXS):
+            arr[s] = float(vals[s]) if s < len(vals) else 0.0
+    rt = list(d.get("react_to", list(range(ns))))
+    for s in range(MAXS):
+        p.react_to[s] = int(rt[s]) if s < len(rt) else s
+    p.reactions = int(d.get("reactions", 0))
+    p.chi = float(d.get("chi", 0.0))
+    p.inter = float(d.get("inter", 1.0))
+    p.cutoff_factor = float(d.get("cutoff_factor", 1.0))
+    p.cutoff_mode = int(d.get("cutoff_mode", 0))
+    p.chem_mode = int(d.get("chem_mode", 0))
+    fg = list(d.get("fixed_grad", [0.0] * 3))
+    for a in range(3):
+        p.fixed_grad[a] = float(fg[a]) if a < len(fg) else 0.0
+    g = list(d.get("grid", [3, 3, 3]))
+    for a in range(3):
+        p.grid[a] = int(g[a]) if a < len(g) else 1
+    p.Dc = float(d.get("Dc", 0.0))
+    p.gamma = float(d.get("gamma", 0.0))
+    p.pde_bc = int(d.get("pde_bc", 0))
+    p.pde_substeps = int(d.get("pde_substeps", 0))
+    p.dt = float(d["dt"])
+    p.seed = int(d.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    p.track_displacement = int(d.get("track_displacement", 0))
+    p.bin_side = float(d.get("bin_side", 0.0))
+    p.search_mode = int(d.get("search_mode", 0))
+    p.bin_order = int(d.get("bin_order", 0))
+    return p
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise ImportError("libchemo_gb300.so is not built (run __graft_entry__.build()): %s" % path)
+        L = ctypes.CDLL(path)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    PP = ctypes.POINTER(chemo_params)
+    sigs = {
+        "chemo_create": ([PP, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "chemo_write_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_write_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_step": ([vp, vp], ctypes.c_int),
+        "chemo_step_n": ([vp, i64, vp], ctypes.c_int),
+        "chemo_read_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_read_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_gradient": ([vp, i64, i32, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_set_params": ([vp, PP], ctypes.c_int),
+        "chemo_step_index": ([vp], i64),
+        "chemo_set_step_index": ([vp, i64, vp], ctypes.c_int),
+        "chemo_check": ([vp, vp], ctypes.c_int),
+        "chemo_get_info": ([vp, ctypes.POINTER(chemo_info)], ctypes.c_int),
+        "chemo_destroy": ([vp], None),
+        "chemo_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "chemo_last_error": ([], ctypes.c_char_p),
+        "chemo_philox": ([ctypes.c_uint64, vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_stage_bins": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_stage_sort": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_stage_forces": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_stage_drift": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_stage_deposit": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+
+
+def _status_text(status: int) -> str:
+    try:
+        return lib().chemo_status_string(int(status)).decode()
+    except Exception:
+        return "status"
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise ChemoError(status, where, lib().chemo_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _buf(x, dtype):
+    """(pointer, mem_kind, keepalive) of an array-like for the C call."""
+    if x is None:
+        return None, None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            want = {np.float32: torch.float32, np.uint8: torch.uint8, np.int32: torch.int32,
+                    np.uint32: torch.int32, np.uint64: torch.int64}[dtype]
+            if x.dtype != want and not (dtype == np.uint32 and x.dtype in (torch.int32, torch.uint32)) and \
+                    not (dtype == np.uint64 and x.dtype in (torch.int64, torch.uint64)):
+                raise TypeError("tensor dtype %s, expected %s" % (x.dtype, want))
+            return ctypes.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST), x
+    except ImportError:
+        pass
+    a = np.asarray(x)
+    if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("numpy buffer must be C-contiguous %s" % np.dtype(dtype))
+    return a.ctypes.data_as(ctypes.c_void_p), MEM_HOST, a
+
+
+def _kind(*kinds):
+    ks = {k for k in kinds if k is not None}
+    if len(ks) > 1:
+        raise ValueError("all buffers of one call must live in the same memory (host or device)")
+    return ks.pop() if ks else MEM_HOST
+
+
+class Sim:
+    """Owned handle of a simulation (chemo_destroy on close / garbage)."""
+
+    def __init__(self, handle, params: dict, n: int):
+        self.handle = handle
+        self.params = dict(params)
+        self.n = int(n)
+        self.dim = int(params["dim"])
+
+    def close(self):
+        if self.handle:
+            lib().chemo_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _h(sim):
+    if not isinstance(sim, Sim) or not sim.handle:
+        raise ValueError("not an open simulation")
+    return sim.handle
+
+
+def chemo_create(params: dict, pos, species, stream=None) -> Sim:
+    """Creates a simulation; pos (n, dim) float32, species (n,) uint8, both
+    host or both device."""
+    pp, kp_, _a = _buf(pos, np.float32)
+    sp, ks, _b = _buf(species, np.uint8)
+    n = int(np.prod(pos.shape[:1])) if pos is not None else 0
+    out = ctypes.c_void_p()
+    prm = make_params(params)
+    _check(lib().chemo_create(ctypes.byref(prm), n, pp, sp, _kind(kp_, ks), _stream(stream), ctypes.byref(out)),
+           "chemo_create")
+    return Sim(out, params, n)
+
+
+def chemo_write_state(sim: Sim, pos, species, disp=None, stream=None):
+    pp, k1, _a = _buf(pos, np.float32)
+    sp, k2, _b = _buf(species, np.uint8)
+    dp, k3, _c = _buf(disp, np.float32)
+    _check(lib().chemo_write_state(_h(sim), pp, sp, dp, _kind(k1, k2, k3), _stream(stream)), "chemo_write_state")
+
+
+def chemo_write_field(sim: Sim, c, stream=None):
+    cp, k, _a = _buf(c, np.float32)
+    _check(lib().chemo_write_field(_h(sim), cp, k, _stream(stream)), "chemo_write_field")
+
+
+def chemo_step(sim: Sim, stream=None):
+    _check(lib().chemo_step(_h(sim), _stream(stream)), "chemo_step")
+
+
+def chemo_step_n(sim: Sim, nsteps: int, stream=None):
+    _check(lib().chemo_step_n(_h(sim), int(nsteps), _stream(stream)), "chemo_step_n")
+
+
+def chemo_read_state(sim: Sim, pos_out=None, species_out=None, disp_out=None, stream=None):
+    pp, k1, _a = _buf(pos_out, np.float32)
+    sp, k2, _b = _buf(species_out, np.uint8)
+    dp, k3, _c = _buf(disp_out, np.float32)
+    _check(lib().chemo_read_state(_h(sim), pp, sp, dp, _kind(k1, k2, k3), _stream(stream)), "chemo_read_state")
+
+
+def chemo_read_field(sim: Sim, c_out, stream=None):
+    cp, k, _a = _buf(c_out, np.float32)
+    _check(lib().chemo_read_field(_h(sim), cp, k, _stream(stream)), "chemo_read_field")
+
+
+def chemo_gradient(sim: Sim, nsteps: int, ckpt_every: int, dL_dpos_final, dL_dc_final, dL_dparams, dL_dpos0=None,
+                   stream=None):
+    a, k1, _a = _buf(dL_dpos_final, np.float32)
+    b, k2, _b = _buf(dL_dc_final, np.float32)
+    c, k3, _c = _buf(dL_dparams, np.float32)
+    d, k4, _d = _buf(dL_dpos0, np.float32)
+    _check(lib().chemo_gradient(_h(sim), int(nsteps), int(ckpt_every), a, b, c, d, _kind(k1, k2, k3, k4),
+                                _stream(stream)), "chemo_gradient")
+
+
+def chemo_set_params(sim: Sim, params: dict):
+    prm = make_params(params)
+    _check(lib().chemo_set_params(_h(sim), ctypes.byref(prm)), "chemo_set_params")
+    sim.params = dict(params)
+
+
+def chemo_step_index(sim: Sim) -> int:
+    return int(lib().chemo_step_index(_h(sim)))
+
+
+def chemo_set_step_index(sim: Sim, step: int, stream=None):
+    _check(lib().chemo_set_step_index(_h(sim), int(step), _stream(stream)), "chemo_set_step_index")
+
+
+def chemo_check(sim: Sim, stream=None):
+    _check(lib().chemo_check(_h(sim), _stream(stream)), "chemo_check")
+
+
+def chemo_get_info(sim: Sim) -> dict:
+    info = chemo_info()
+    _check(lib().chemo_get_info(_h(sim), ctypes.byref(info)), "chemo_get_info")
+    return {name: (list(getattr(info, name)) if hasattr(getattr(info, name), "__len__") else getattr(info, name))
+            for name, _ in chemo_info._fields_}
+
+
+def chemo_destroy(sim: Sim):
+    sim.close()
+
+
+def chemo_status_string(status: int) -> str:
+    return lib().chemo_status_string(int(status)).decode()
+
+
+def chemo_last_error() -> str:
+    return lib().chemo_last_error().decode()
+
+
+def chemo_philox(seed: int, ctr, out, stream=None):
+    cp, k1, _a = _buf(ctr, np.uint32)
+    op, k2, _b = _buf(out, np.uint32)
+    n = int(np.prod(ctr.shape)) // 4
+    _check(lib().chemo_philox(int(seed) & 0xFFFFFFFFFFFFFFFF, cp, op, n, _kind(k1, k2), _stream(stream)),
+           "chemo_philox")
+
+
+def chemo_stage_bins(sim: Sim, cells_out, stream=None):
+    cp, k, _a = _buf(cells_out, np.int32)
+    _check(lib().chemo_stage_bins(_h(sim), cp, k, _stream(stream)), "chemo_stage_bins")
+
+
+def chemo_stage_sort(sim: Sim, ids_out=None, bin_start_out=None, stream=None):
+    ip, k1, _a = _buf(ids_out, np.uint32)
+    bp, k2, _b = _buf(bin_start_out, np.uint32)
+    _check(lib().chemo_stage_sort(_h(sim), ip, bp, _kind(k1, k2), _stream(stream)), "chemo_stage_sort")
+
+
+def chemo_stage_forces(sim: Sim, F_out, count_out=None, idsum_out=None, stream=None):
+    fp, k1, _a = _buf(F_out, np.float32)
+    cp, k2, _b = _buf(count_out, np.int32)
+    ip, k3, _c = _buf(idsum_out, np.uint64)
+    _check(lib().chemo_stage_forces(_h(sim), fp, cp, ip, _kind(k1, k2, k3), _stream(stream)), "chemo_stage_forces")
+
+
+def chemo_stage_drift(sim: Sim, drift_out, stream=None):
+    dp, k, _a = _buf(drift_out, np.float32)
+    _check(lib().chemo_stage_drift(_h(sim), dp, k, _stream(stream)), "chemo_stage_drift")
+
+
+def chemo_stage_deposit(sim: Sim, S_out=None, R_out=None, stream=None):
+    sp, k1, _a = _buf(S_out, np.float32)
+    rp, k2, _b = _buf(R_out, np.float32)
+    _check(lib().chemo_stage_deposit(_h(sim), sp, rp, _kind(k1, k2), _stream(stream)), "chemo_stage_deposit")
+
+
+# ---------------------------------------------------------------------------
+# Host-array conveniences (numpy in, numpy out) over the calls above.
+# ---------------------------------------------------------------------------
+def grid_shape(params: dict) -> tuple:
+    return tuple(int(params["grid"][a]) for a in reversed(range(int(params["dim"]))))
+
+
+def read_state_host(sim: Sim):
+    pos = np.zeros((sim.n, sim.dim), np.float32)
+    sp = np.zeros(sim.n, np.uint8)
+    disp = np.zeros((sim.n, sim.dim), np.float32) if sim.params.get("track_displacement") else None
+    chemo_read_state(sim, pos, sp, disp)
+    return pos, sp, disp
+
+
+def read_field_host(sim: Sim):
+    c = np.zeros(grid_shape(sim.params), np.float32)
+    chemo_read_field(sim, c)
+    return c

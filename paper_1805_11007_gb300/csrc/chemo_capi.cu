@@ -1,0 +1,887 @@
+// chemo_capi.cu -- engine and C ABI (include/chemo.h) of the GB300
+// chemotaxis step (arXiv:1805.11007): parameter validation, cell-list and
+// grid layout, device buffers, the per-step launch sequence (PDE overlapped
+// with the particle kernel on a second stream when one substep suffices) and
+// CUDA-graph replay of repeated steps.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/chemo.h"
+#include "chemo_internal.cuh"
+
+using namespace chemo;
+
+namespace {
+
+thread_local char g_last_error[512] = "";
+
+int fail(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return status;
+}
+
+#define CUDA_TRY(expr)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (expr);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(e_ == cudaErrorMemoryAllocation ? CHEMO_ENOMEM : CHEMO_ECUDA,    \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+__global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v; }
+
+}  // namespace
+
+struct chemo_sim {
+    chemo_params prm{};
+    KP kp{};
+    int cur = 0;                 // c[cur] holds c^n
+    int64_t step = 0;            // host mirror of the next step index
+    int launches_per_step = 0;
+    cudaStream_t aux = nullptr;  // second stream for the PDE
+    cudaStream_t cap = nullptr;  // capture stream for graphs
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // 2-step and 16-step replays
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    void *scratch = nullptr;     // staging for host transfers and stage outputs
+    size_t scratch_bytes = 0;
+};
+
+namespace {
+
+int dalloc(chemo_sim *s, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(CHEMO_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    s->allocs.push_back(*p);
+    s->bytes += (int64_t)bytes;
+    return CHEMO_OK;
+}
+
+int scratch(chemo_sim *s, size_t bytes, void **out)
+{
+    if (bytes > s->scratch_bytes) {
+        if (s->scratch) {
+            cudaError_t e = cudaDeviceSynchronize();
+            if (e != cudaSuccess) return fail(CHEMO_ECUDA, "sync: %s", cudaGetErrorString(e));
+            cudaFree(s->scratch);
+            s->bytes -= (int64_t)s->scratch_bytes;
+            s->scratch = nullptr;
+            s->scratch_bytes = 0;
+        }
+        size_t b = (bytes + 255) & ~(size_t)255;
+        cudaError_t e = cudaMalloc(&s->scratch, b);
+        if (e != cudaSuccess) {
+            s->scratch = nullptr;
+            return fail(CHEMO_ENOMEM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
+        }
+        s->scratch_bytes = b;
+        s->bytes += (int64_t)b;
+    }
+    *out = s->scratch;
+    return CHEMO_OK;
+}
+
+bool is_device_ptr(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+double grid_h(const chemo_params &p, int a)
+{
+    const double L = p.hi[a] - p.lo[a];
+    return p.pde_bc == 2 ? L / p.grid[a] : L / (p.grid[a] - 1);
+}
+
+int resolve_substeps(const chemo_params &p)
+{
+    if (p.pde_substeps > 0) return p.pde_substeps;
+    double lam = 0.0;
+    for (int a = 0; a < p.dim; ++a) {
+        const double h = grid_h(p, a);
+        lam += 2.0 * (double)p.Dc * p.dt / (h * h);
+    }
+    const int s = (int)std::ceil(lam / 0.9);
+    return s < 1 ? 1 : s;
+}
+
+// Validates p; on success fills the model constants of kp (not the layout).
+int check_params(const chemo_params &p)
+{
+    if (p.struct_size != sizeof(chemo_params))
+        return fail(CHEMO_EINVAL, "chemo_params.struct_size = %u, expected %zu", p.struct_size, sizeof(chemo_params));
+    if (p.dim != 2 && p.dim != 3) return fail(CHEMO_EINVAL, "dim must be 2 or 3 (got %d)", p.dim);
+    if (p.boundary != 0 && p.boundary != 1) return fail(CHEMO_EINVAL, "boundary must be 0 or 1");
+    if (p.n_species < 1 || p.n_species > CHEMO_MAX_SPECIES) return fail(CHEMO_EINVAL, "n_species must be 1..8");
+    for (int a = 0; a < p.dim; ++a)
+        if (!(p.hi[a] > p.lo[a]) || !std::isfinite(p.lo[a]) || !std::isfinite(p.hi[a]))
+            return fail(CHEMO_EINVAL, "empty or non-finite box on axis %d", a);
+    if (!(p.dt > 0.0) || !std::isfinite(p.dt)) return fail(CHEMO_EINVAL, "dt must be positive");
+    for (int s = 0; s < p.n_species; ++s) {
+        if (!(p.diameter[s] >= 0.f) || !(p.D[s] >= 0.f)) return fail(CHEMO_EINVAL, "species %d: negative diameter or D", s);
+        if (p.react_to[s] < 0 || p.react_to[s] >= p.n_species) return fail(CHEMO_EINVAL, "species %d: react_to out of range", s);
+    }
+    if (p.cutoff_mode != 0 && p.cutoff_mode != 1) return fail(CHEMO_EINVAL, "cutoff_mode must be 0 or 1");
+    if (!(p.cutoff_factor >= 0.f)) return fail(CHEMO_EINVAL, "cutoff_factor must be >= 0");
+    if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
+    if (p.search_mode < 0 || p.search_mode > 2) return fail(CHEMO_EINVAL, "search_mode must be 0, 1 or 2");
+    if (p.bin_order < 0 || p.bin_order > 2) return fail(CHEMO_EINVAL, "bin_order must be 0, 1 or 2");
+    if (p.chem_mode == 0) {
+        if (p.pde_bc < 0 || p.pde_bc > 2) return fail(CHEMO_EINVAL, "pde_bc must be 0, 1 or 2");
+        if ((p.pde_bc == 2) != (p.boundary == 1))
+            return fail(CHEMO_EINVAL, "pde_bc = 2 (periodic) goes with boundary = 1 and only with it");
+        for (int a = 0; a < p.dim; ++a)
+            if (p.grid[a] < 3) return fail(CHEMO_EINVAL, "grid[%d] = %d: need at least 3 nodes", a, p.grid[a]);
+        if (p.pde_substeps < 0) return fail(CHEMO_EINVAL, "pde_substeps must be >= 0");
+    }
+    return CHEMO_OK;
+}
+
+double max_cutoff(const chemo_params &p)
+{
+    double m = 0.0;
+    for (int s = 0; s < p.n_species; ++s)
+        for (int t = 0; t < p.n_species; ++t)
+            m = std::max(m, (double)p.cutoff_factor * 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]));
+    return m;
+}
+
+// Model constants that chemo_set_params may change.
+void fill_model(const chemo_params &p, KP &kp)
+{
+    kp.ns = p.n_species;
+    const double hd = [&] {
+        double v = 1.0;
+        if (p.chem_mode == 0)
+            for (int a = 0; a < p.dim; ++a) v *= grid_h(p, a);
+        return v;
+    }();
+    for (int s = 0; s < MAXS; ++s) {
+        for (int t = 0; t < MAXS; ++t) {
+            const int i = s * MAXS + t;
+            kp.rc2[i] = 0.f;
+            kp.inv_eps[i] = 0.f;
+            kp.amp_f[i] = 0.f;
+            kp.shift[i] = 0.f;
+            if (s < p.n_species && t < p.n_species) {
+                const double eps = 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]);
+                if (eps > 0.0) {
+                    const double rc = (double)p.cutoff_factor * eps;
+                    kp.rc2[i] = (float)(rc * rc);
+                    kp.inv_eps[i] = (float)(1.0 / eps);
+                    kp.amp_f[i] = (float)((double)p.inter / eps);
+                    kp.shift[i] = p.cutoff_mode == 1 ? (float)std::exp(-(double)p.cutoff_factor) : 0.f;
+                }
+            }
+        }
+        const bool in = s < p.n_species;
+        kp.noise[s] = in ? (float)std::sqrt(2.0 * (double)p.D[s] * p.dt) : 0.f;
+        kp.chem[s] = in ? p.chi * p.chemotactic[s] : 0.f;
+        kp.src[s] = in ? (float)((double)p.secrete[s] * p.dt / hd) : 0.f;
+        kp.cons[s] = in ? (float)((double)p.consume[s] / hd) : 0.f;
+        kp.rk0[s] = in ? p.react_k0[s] : 0.f;
+        kp.rkc[s] = in ? p.react_kc[s] : 0.f;
+        kp.rto[s] = in ? p.react_to[s] : s;
+    }
+    kp.reactions = p.reactions ? 1 : 0;
+    kp.dt = (float)p.dt;
+    kp.dt_d = p.dt;
+    kp.seed_lo = (uint32_t)p.seed;
+    kp.seed_hi = (uint32_t)(p.seed >> 32);
+    kp.chem_mode = p.chem_mode;
+    for (int a = 0; a < 3; ++a) kp.fixed_g[a] = a < p.dim ? p.fixed_grad[a] : 0.f;
+    kp.Dc = p.Dc;
+    kp.gamma = p.gamma;
+}
+
+// Cell-list layout: bin side >= r_c (3^d search) or >= 2 r_c (2^d search),
+// row-major or Z-order storage.
+int fill_layout(const chemo_params &p, int64_t n, KP &kp)
+{
+    kp.dim = p.dim;
+    kp.periodic = p.boundary == 1;
+    for (int a = 0; a < 3; ++a) {
+        kp.lo[a] = a < p.dim ? (float)p.lo[a] : 0.f;
+        kp.hi[a] = a < p.dim ? (float)p.hi[a] : 0.f;
+        kp.L[a] = a < p.dim ? (float)(p.hi[a] - p.lo[a]) : 0.f;
+        kp.halfL[a] = 0.5f * kp.L[a];
+        kp.nb[a] = 1;
+        kp.inv_b[a] = 0.f;
+    }
+    const double rc = max_cutoff(p);
+    const bool pairs = rc > 0.0 && p.inter != 0.f;
+    int search = (p.search_mode == 0 || !pairs) ? 1 : p.search_mode;
+    kp.pairs = pairs ? 1 : 0;
+    double bmin;
+    if (pairs) {
+        bmin = (search == 2 ? 2.0 : 1.0) * rc * (1.0 + 1.0 / 4096.0);
+        if (p.bin_side > 0.f) {
+            if ((double)p.bin_side < bmin)
+                return fail(CHEMO_EINVAL, "bin_side %g is below the %s search minimum %g", (double)p.bin_side,
+                            search == 2 ? "2^d" : "3^d", bmin);
+            bmin = p.bin_side;
+        }
+    } else {
+        // no interaction: bins only order the particles (about 2^d per bin)
+        double vol = 1.0;
+        for (int a = 0; a < p.dim; ++a) vol *= p.hi[a] - p.lo[a];
+        bmin = p.bin_side > 0.f ? (double)p.bin_side
+                                : std::pow(vol * (double)(1 << p.dim) / (double)std::max<int64_t>(n, 1), 1.0 / p.dim);
+    }
+    int64_t total = 1;
+    int maxnb = 1;
+    for (int a = 0; a < p.dim; ++a) {
+        const double L = p.hi[a] - p.lo[a];
+        double m = std::floor(L / bmin);
+        if (m < 1.0) m = 1.0;
+        if (!pairs) m = std::min(m, 1024.0);
+        if (m > 65535.0) return fail(CHEMO_EINVAL, "axis %d needs %g bins: cutoff too small for the box", a, m);
+        kp.nb[a] = (int)m;
+        kp.inv_b[a] = (float)((double)kp.nb[a] / L);
+        total *= kp.nb[a];
+        maxnb = std::max(maxnb, kp.nb[a]);
+    }
+    if (pairs && kp.periodic) {
+        for (int a = 0; a < p.dim; ++a) {
+            if (search == 1 && kp.nb[a] < 3)
+                return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= r_c; need >= 3 (box too small "
+                                          "for the cutoff; try search_mode 2)", a, kp.nb[a]);
+            if (search == 2 && kp.nb[a] < 2)
+                return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= 2 r_c; need >= 2", a, kp.nb[a]);
+        }
+    }
+    if (total > (int64_t)1 << 31) return fail(CHEMO_EINVAL, "cell list would need %lld bins", (long long)total);
+    int bits = 0;
+    while ((1 << bits) < maxnb) ++bits;
+    const int64_t mslots = (int64_t)1 << (bits * p.dim);
+    bool morton;
+    if (p.bin_order == 1) morton = false;
+    else if (p.bin_order == 2) morton = true;
+    else morton = mslots <= 2 * total;
+    if (morton && ((p.dim == 3 && bits > 10) || (p.dim == 2 && bits > 15) || mslots > ((int64_t)1 << 31)))
+        return fail(CHEMO_EINVAL, "Z-order bin table too large (%d bits per axis)", bits);
+    kp.morton = morton ? 1 : 0;
+    kp.mbits = bits;
+    kp.bin_slots = morton ? mslots : total;
+    kp.search = search;
+    return CHEMO_OK;
+}
+
+int fill_grid(const chemo_params &p, KP &kp)
+{
+    kp.has_grid = p.chem_mode == 0 ? 1 : 0;
+    kp.G = 0;
+    for (int a = 0; a < 3; ++a) {
+        kp.g[a] = 1;
+        kp.inv_h[a] = kp.inv_2h[a] = kp.inv_h2[a] = 0.f;
+    }
+    kp.pde_bc = p.pde_bc;
+    kp.substeps = 1;
+    kp.dts = (float)p.dt;
+    kp.fused_deposit = 0;
+    if (!kp.has_grid) return CHEMO_OK;
+    int64_t G = 1;
+    for (int a = 0; a < p.dim; ++a) {
+        kp.g[a] = p.grid[a];
+        G *= p.grid[a];
+        const double h = grid_h(p, a);
+        kp.inv_h[a] = (float)(1.0 / h);
+        kp.inv_2h[a] = (float)(0.5 / h);
+        kp.inv_h2[a] = (float)(1.0 / (h * h));
+    }
+    if (G > ((int64_t)1 << 34)) return fail(CHEMO_EINVAL, "grid too large");
+    kp.G = G;
+    kp.substeps = resolve_substeps(p);
+    kp.dts = (float)(p.dt / kp.substeps);
+    kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1) ? 1 : 0;
+    return CHEMO_OK;
+}
+
+int to_status(uint32_t bits)
+{
+    if (bits & ERR_TIMEOUT) return fail(CHEMO_ETIMEOUT, "a bounded device-side wait ran out (scan look-back)");
+    if (bits & ERR_OVERFLOW) return fail(CHEMO_EOVERFLOW, "cell-list placement overflowed");
+    if (bits & ERR_NONFINITE) return fail(CHEMO_ENONFINITE, "a non-finite position appeared");
+    if (bits & ERR_DOMAIN) return fail(CHEMO_EDOMAIN, "a particle position was outside the box");
+    if (bits & ERR_SPECIES) return fail(CHEMO_EINVAL, "a species value was >= n_species");
+    return CHEMO_OK;
+}
+
+// Bins the particles currently in U (with slots already counted) into S.
+int sort_from_u(chemo_sim *s, cudaStream_t st)
+{
+    CUDA_TRY(launch_scan(s->kp, st, nullptr));
+    CUDA_TRY(launch_scatter(s->kp, s->cur, 0, st, nullptr));
+    return CHEMO_OK;
+}
+
+// Enqueues one step on st. Counts launched kernels into *launches.
+int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
+{
+    const KP &kp = s->kp;
+    const bool grid = kp.has_grid && kp.chem_mode == 0;
+    const bool overlap = grid && kp.fused_deposit;
+    if (overlap) {
+        CUDA_TRY(cudaEventRecord(s->ev_fork, st));
+        CUDA_TRY(cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
+        CUDA_TRY(launch_pde(kp, s->cur, s->aux, launches));
+        CUDA_TRY(cudaEventRecord(s->ev_join, s->aux));
+    }
+    CUDA_TRY(launch_step_particles(kp, s->cur, st, launches));
+    if (overlap) CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
+    CUDA_TRY(launch_scan(kp, st, launches));
+    CUDA_TRY(launch_scatter(kp, s->cur, 1, st, launches));
+    if (grid && !overlap) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
+    if (grid) s->cur = overlap ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+    s->step += 1;
+    return CHEMO_OK;
+}
+
+void drop_graphs(chemo_sim *s)
+{
+    for (auto &g : s->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
+
+// Captures `k` steps starting from grid parity 0 into an executable graph.
+int capture(chemo_sim *s, int k, cudaGraphExec_t *out)
+{
+    const int cur0 = s->cur;
+    const int64_t step0 = s->step;
+    s->cur = 0;
+    CUDA_TRY(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    int st = CHEMO_OK;
+    for (int i = 0; i < k && st == CHEMO_OK; ++i) st = enqueue_step(s, s->cap, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->cap, &g);
+    s->cur = cur0;
+    s->step = step0;
+    if (st != CHEMO_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return fail(CHEMO_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(CHEMO_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    return CHEMO_OK;
+}
+
+int copy_in(chemo_sim *s, const void *src, size_t bytes, int mem_kind, cudaStream_t st, size_t offset, void **dst)
+{
+    if (mem_kind == CHEMO_MEM_DEVICE) {
+        *dst = const_cast<void *>(src);
+        return CHEMO_OK;
+    }
+    (void)s;
+    char *base = (char *)s->scratch + offset;
+    CUDA_TRY(cudaMemcpyAsync(base, src, bytes, cudaMemcpyHostToDevice, st));
+    *dst = base;
+    return CHEMO_OK;
+}
+
+int check_mem_kind(int mem_kind)
+{
+    if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE)
+        return fail(CHEMO_EINVAL, "mem_kind must be CHEMO_MEM_HOST (0) or CHEMO_MEM_DEVICE (1)");
+    return CHEMO_OK;
+}
+
+int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp, int mem_kind, cudaStream_t st)
+{
+    const int64_t n = s->kp.n;
+    const int d = s->kp.dim;
+    if (n == 0) return sort_from_u(s, st);
+    if (!pos || !sp) return fail(CHEMO_EINVAL, "pos and species are required");
+    if (mem_kind == CHEMO_MEM_HOST) {
+        for (int64_t i = 0; i < n; ++i) {
+            if (sp[i] >= s->prm.n_species) return fail(CHEMO_EINVAL, "species[%lld] = %d >= n_species", (long long)i, sp[i]);
+            for (int a = 0; a < d; ++a) {
+                const float v = pos[i * d + a];
+                if (!std::isfinite(v) || v < s->kp.lo[a] || v > s->kp.hi[a])
+                    return fail(CHEMO_EINVAL, "pos[%lld][%d] = %g is outside the box", (long long)i, a, (double)v);
+            }
+        }
+    }
+    const size_t pbytes = (size_t)n * d * sizeof(float);
+    const size_t sbytes = ((size_t)n + 255) & ~(size_t)255;
+    if (mem_kind == CHEMO_MEM_HOST) {
+        void *tmp;
+        int r = scratch(s, 2 * pbytes + sbytes + 512, &tmp);
+        if (r) return r;
+    }
+    void *dpos, *dsp, *ddisp = nullptr;
+    int r = copy_in(s, pos, pbytes, mem_kind, st, 0, &dpos);
+    if (r) return r;
+    r = copy_in(s, sp, (size_t)n, mem_kind, st, (pbytes + 255) & ~(size_t)255, &dsp);
+    if (r) return r;
+    if (disp && s->kp.dS) {
+        r = copy_in(s, disp, pbytes, mem_kind, st, ((pbytes + 255) & ~(size_t)255) + sbytes, &ddisp);
+        if (r) return r;
+    }
+    CUDA_TRY(launch_pack(s->kp, (const float *)dpos, (const uint8_t *)dsp, (const float *)ddisp, st, nullptr));
+    r = sort_from_u(s, st);
+    if (r) return r;
+    if (mem_kind == CHEMO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return CHEMO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *chemo_status_string(int status)
+{
+    switch (status) {
+    case CHEMO_OK: return "ok";
+    case CHEMO_EINVAL: return "invalid argument";
+    case CHEMO_ENOMEM: return "out of memory";
+    case CHEMO_ECUDA: return "CUDA error";
+    case CHEMO_EDOMAIN: return "particle outside the domain";
+    case CHEMO_ENONFINITE: return "non-finite value";
+    case CHEMO_EOVERFLOW: return "overflow";
+    case CHEMO_ETIMEOUT: return "device wait timed out";
+    case CHEMO_ENOTSUP: return "not supported";
+    default: return "unknown status";
+    }
+}
+
+const char *chemo_last_error(void) { return g_last_error; }
+
+void chemo_destroy(chemo_sim *s)
+{
+    if (!s) return;
+    cudaDeviceSynchronize();
+    drop_graphs(s);
+    for (void *p : s->allocs) cudaFree(p);
+    if (s->scratch) cudaFree(s->scratch);
+    if (s->aux) cudaStreamDestroy(s->aux);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+    if (s->ev_join) cudaEventDestroy(s->ev_join);
+    delete s;
+}
+
+int chemo_create(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species, int mem_kind,
+                 void *stream, chemo_sim **out)
+{
+    g_last_error[0] = 0;
+    if (!params || !out) return fail(CHEMO_EINVAL, "params and out are required");
+    *out = nullptr;
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (int r = check_params(*params)) return r;
+    if (n < 0 || n > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "n = %lld out of range [0, 2^29]", (long long)n);
+    if (n > 0 && mem_kind == CHEMO_MEM_DEVICE && !(is_device_ptr(pos) && is_device_ptr(species)))
+        return fail(CHEMO_EINVAL, "mem_kind is DEVICE but pos/species are not device pointers");
+    chemo_sim *s = new (std::nothrow) chemo_sim();
+    if (!s) return fail(CHEMO_ENOMEM, "host allocation failed");
+    s->prm = *params;
+    KP &kp = s->kp;
+    kp.n = n;
+    int r;
+    if ((r = fill_layout(*params, n, kp)) || (r = fill_grid(*params, kp))) {
+        delete s;
+        return r;
+    }
+    fill_model(*params, kp);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)std::max<int64_t>(n, 1);
+    void *p;
+#define ALLOC(field, bytes)                         \
+    if ((r = dalloc(s, &p, (bytes)))) {             \
+        chemo_destroy(s);                           \
+        return r;                                   \
+    }                                               \
+    field = decltype(field)(p);
+    ALLOC(kp.S, N * sizeof(float4));
+    ALLOC(kp.U, N * sizeof(float4));
+    ALLOC(kp.slot, N * sizeof(uint32_t));
+    kp.dS = kp.dU = nullptr;
+    if (params->track_displacement) {
+        ALLOC(kp.dS, N * sizeof(float4));
+        ALLOC(kp.dU, N * sizeof(float4));
+    }
+    const size_t slots = (size_t)kp.bin_slots;
+    ALLOC(kp.cnt, ((slots + 3) & ~(size_t)3) * sizeof(uint32_t));
+    ALLOC(kp.start, ((slots + 1 + 3) & ~(size_t)3) * sizeof(uint32_t));
+    const size_t tiles = (slots + 4095) / 4096;
+    ALLOC(kp.tiles, tiles * sizeof(unsigned long long));
+    uint32_t *ctl;
+    ALLOC(ctl, 64);
+    kp.tile_ctr = ctl;
+    kp.scan_seq = ctl + 1;
+    kp.err = ctl + 2;
+    kp.step = reinterpret_cast<unsigned long long *>(ctl + 4);
+    kp.c[0] = kp.c[1] = nullptr;
+    kp.srcg = kp.Rg = nullptr;
+    if (kp.has_grid) {
+        ALLOC(kp.c[0], (size_t)kp.G * sizeof(float));
+        ALLOC(kp.c[1], (size_t)kp.G * sizeof(float));
+        if (!kp.fused_deposit) {
+            ALLOC(kp.srcg, (size_t)kp.G * sizeof(float));
+            ALLOC(kp.Rg, (size_t)kp.G * sizeof(float));
+        }
+    }
+#undef ALLOC
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMemsetAsync(kp.cnt, 0, ((slots + 3) & ~(size_t)3) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(kp.tiles, 0, tiles * sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 64, st);
+    if (e == cudaSuccess && kp.has_grid) {
+        e = cudaMemsetAsync(kp.c[0], 0, (size_t)kp.G * sizeof(float), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(kp.c[1], 0, (size_t)kp.G * sizeof(float), st);
+        if (e == cudaSuccess && kp.srcg) e = cudaMemsetAsync(kp.srcg, 0, (size_t)kp.G * sizeof(float), st);
+        if (e == cudaSuccess && kp.Rg) e = cudaMemsetAsync(kp.Rg, 0, (size_t)kp.G * sizeof(float), st);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        chemo_destroy(s);
+        return fail(CHEMO_ECUDA, "create: %s", cudaGetErrorString(e));
+    }
+    if ((r = ingest(s, pos, species, nullptr, mem_kind, st))) {
+        chemo_destroy(s);
+        return r;
+    }
+    // launches per step: particles, scan, scatter, and the PDE substeps
+    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.substeps : 0);
+    *out = s;
+    return CHEMO_OK;
+}
+
+int chemo_write_state(chemo_sim *s, const float *pos, const uint8_t *species, const float *disp, int mem_kind,
+                      void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    return ingest(s, pos, species, disp, mem_kind, (cudaStream_t)stream);
+}
+
+int chemo_write_field(chemo_sim *s, const float *c, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !c) return fail(CHEMO_EINVAL, "sim and c are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (!s->kp.has_grid) return fail(CHEMO_EINVAL, "this simulation has no grid (chem_mode 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)s->kp.G * sizeof(float);
+    CUDA_TRY(cudaMemcpyAsync(s->kp.c[s->cur], c, bytes,
+                             mem_kind == CHEMO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    if (mem_kind == CHEMO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return CHEMO_OK;
+}
+
+int chemo_step(chemo_sim *s, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    return enqueue_step(s, (cudaStream_t)stream, nullptr);
+}
+
+int chemo_step_n(chemo_sim *s, int64_t nsteps, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (nsteps < 0) return fail(CHEMO_EINVAL, "nsteps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    int64_t left = nsteps;
+    if (left >= 2 && s->cur != 0) {
+        if (int r = enqueue_step(s, st, nullptr)) return r;
+        --left;
+    }
+    static const int sizes[2] = {2, 16};
+    for (int gi = 1; gi >= 0; --gi) {
+        const int k = sizes[gi];
+        if (left < k) continue;
+        if (!s->graph[gi])
+            if (int r = capture(s, k, &s->graph[gi])) return r;
+        while (left >= k) {
+            CUDA_TRY(cudaGraphLaunch(s->graph[gi], st));
+            s->step += k;
+            left -= k;
+        }
+    }
+    while (left > 0) {
+        if (int r = enqueue_step(s, st, nullptr)) return r;
+        --left;
+    }
+    return CHEMO_OK;
+}
+
+int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *disp_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (disp_out && !s->kp.dS) return fail(CHEMO_EINVAL, "displacement is not tracked (track_displacement = 0)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = s->kp.n;
+    const size_t pbytes = (size_t)n * s->kp.dim * sizeof(float);
+    const size_t pb = (pbytes + 255) & ~(size_t)255;
+    if (mem_kind == CHEMO_MEM_DEVICE) {
+        CUDA_TRY(launch_unsort(s->kp, pos_out, species_out, disp_out, st));
+    } else {
+        void *tmp;
+        if (int r = scratch(s, 2 * pb + (size_t)n + 256, &tmp)) return r;
+        char *b = (char *)tmp;
+        float *dp = pos_out ? (float *)b : nullptr;
+        float *dd = disp_out ? (float *)(b + pb) : nullptr;
+        uint8_t *ds = species_out ? (uint8_t *)(b + 2 * pb) : nullptr;
+        CUDA_TRY(launch_unsort(s->kp, dp, ds, dd, st));
+        if (pos_out && n) CUDA_TRY(cudaMemcpyAsync(pos_out, dp, pbytes, cudaMemcpyDeviceToHost, st));
+        if (disp_out && n) CUDA_TRY(cudaMemcpyAsync(disp_out, dd, pbytes, cudaMemcpyDeviceToHost, st));
+        if (species_out && n) CUDA_TRY(cudaMemcpyAsync(species_out, ds, (size_t)n, cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return chemo_check(s, stream);
+    }
+    return CHEMO_OK;
+}
+
+int chemo_read_field(chemo_sim *s, float *c_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !c_out) return fail(CHEMO_EINVAL, "sim and c_out are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (!s->kp.has_grid) return fail(CHEMO_EINVAL, "this simulation has no grid (chem_mode 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaMemcpyAsync(c_out, s->kp.c[s->cur], (size_t)s->kp.G * sizeof(float),
+                             mem_kind == CHEMO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    if (mem_kind == CHEMO_MEM_HOST) {
+        CUDA_TRY(cudaStreamSynchronize(st));
+        return chemo_check(s, stream);
+    }
+    return CHEMO_OK;
+}
+
+int chemo_gradient(chemo_sim *s, int64_t nsteps, int32_t ckpt_every, const float *dL_dpos_final,
+                   const float *dL_dc_final, float *dL_dparams, float *dL_dpos0, int mem_kind, void *stream)
+{
+    (void)s; (void)nsteps; (void)ckpt_every; (void)dL_dpos_final; (void)dL_dc_final;
+    (void)dL_dparams; (void)dL_dpos0; (void)mem_kind; (void)stream;
+    return fail(CHEMO_ENOTSUP, "chemo_gradient (adjoint) is not available in this build");
+}
+
+int chemo_set_params(chemo_sim *s, const chemo_params *p)
+{
+    g_last_error[0] = 0;
+    if (!s || !p) return fail(CHEMO_EINVAL, "sim and params are required");
+    if (int r = check_params(*p)) return r;
+    const chemo_params &o = s->prm;
+    bool same = p->dim == o.dim && p->boundary == o.boundary && p->n_species == o.n_species &&
+                p->chem_mode == o.chem_mode && p->pde_bc == o.pde_bc && p->track_displacement == o.track_displacement;
+    for (int a = 0; a < 3; ++a) same = same && p->lo[a] == o.lo[a] && p->hi[a] == o.hi[a] && p->grid[a] == o.grid[a];
+    if (!same) return fail(CHEMO_EINVAL, "chemo_set_params cannot change geometry, species count or modes");
+    KP k2 = s->kp;
+    int r;
+    if ((r = fill_layout(*p, s->kp.n, k2)) || (r = fill_grid(*p, k2))) return r;
+    if (k2.nb[0] != s->kp.nb[0] || k2.nb[1] != s->kp.nb[1] || k2.nb[2] != s->kp.nb[2] ||
+        k2.search != s->kp.search || k2.morton != s->kp.morton || k2.substeps != s->kp.substeps ||
+        k2.fused_deposit != s->kp.fused_deposit)
+        return fail(CHEMO_EINVAL, "new parameters change the cell-list layout or the PDE substeps");
+    fill_model(*p, s->kp);
+    s->prm = *p;
+    drop_graphs(s);  // graphs hold the old constants
+    return CHEMO_OK;
+}
+
+int64_t chemo_step_index(const chemo_sim *s) { return s ? s->step : -1; }
+
+int chemo_set_step_index(chemo_sim *s, int64_t step, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || step < 0) return fail(CHEMO_EINVAL, "bad sim or step");
+    k_set_u64<<<1, 1, 0, (cudaStream_t)stream>>>(s->kp.step, (unsigned long long)step);
+    CUDA_TRY(cudaGetLastError());
+    s->step = step;
+    return CHEMO_OK;
+}
+
+int chemo_check(chemo_sim *s, void *stream)
+{
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    CUDA_TRY(cudaStreamSynchronize(s->aux));
+    uint32_t bits = 0;
+    CUDA_TRY(cudaMemcpy(&bits, s->kp.err, sizeof(bits), cudaMemcpyDeviceToHost));
+    if (bits) CUDA_TRY(cudaMemset(s->kp.err, 0, sizeof(uint32_t)));
+    return to_status(bits);
+}
+
+int chemo_get_info(const chemo_sim *s, chemo_info *info)
+{
+    if (!s || !info) return fail(CHEMO_EINVAL, "sim and info are required");
+    const KP &kp = s->kp;
+    info->n = kp.n;
+    info->dim = kp.dim;
+    info->search_mode = kp.search;
+    for (int a = 0; a < 3; ++a) {
+        info->nbins[a] = kp.nb[a];
+        info->bin_side[a] = a < kp.dim ? kp.L[a] / kp.nb[a] : 0.f;
+    }
+    info->bin_slots = kp.bin_slots;
+    info->morton = kp.morton;
+    info->pde_substeps = kp.has_grid ? kp.substeps : 0;
+    info->grid_nodes = kp.G;
+    info->device_bytes = s->bytes;
+    info->launches_per_step = s->launches_per_step;
+    return CHEMO_OK;
+}
+
+int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (n < 0 || (n > 0 && (!ctr || !out))) return fail(CHEMO_EINVAL, "bad arguments");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mem_kind == CHEMO_MEM_DEVICE) {
+        CUDA_TRY(launch_philox(seed, ctr, out, n, st));
+        return CHEMO_OK;
+    }
+    const size_t bytes = (size_t)n * 16;
+    void *d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, 2 * bytes + 32));
+    uint32_t *dc = (uint32_t *)d, *dout = (uint32_t *)((char *)d + bytes);
+    cudaError_t e = cudaMemcpyAsync(dc, ctr, bytes, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_philox(seed, dc, dout, n, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CHEMO_ECUDA, "philox: %s", cudaGetErrorString(e));
+    return CHEMO_OK;
+}
+
+// Stage entry points: results land in device scratch, then go to the caller.
+static int stage_out(chemo_sim *s, void *dst, const void *src, size_t bytes, int mem_kind, cudaStream_t st)
+{
+    if (!dst || bytes == 0) return CHEMO_OK;
+    CUDA_TRY(cudaMemcpyAsync(dst, src, bytes,
+                             mem_kind == CHEMO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    (void)s;
+    return CHEMO_OK;
+}
+
+static int finish(chemo_sim *s, int mem_kind, void *stream)
+{
+    if (mem_kind == CHEMO_MEM_HOST) {
+        CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+        return chemo_check(s, stream);
+    }
+    return CHEMO_OK;
+}
+
+int chemo_stage_bins(chemo_sim *s, int32_t *cells_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !cells_out) return fail(CHEMO_EINVAL, "sim and cells_out are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(int32_t);
+    void *tmp;
+    if (int r = scratch(s, bytes + 256, &tmp)) return r;
+    CUDA_TRY(launch_stage_bins(s->kp, (int32_t *)tmp, st));
+    if (int r = stage_out(s, cells_out, tmp, bytes, mem_kind, st)) return r;
+    return finish(s, mem_kind, stream);
+}
+
+int chemo_stage_sort(chemo_sim *s, uint32_t *ids_out, uint32_t *bin_start_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)s->kp.n * sizeof(uint32_t);
+    void *tmp;
+    if (int r = scratch(s, bytes + 256, &tmp)) return r;
+    if (ids_out) {
+        CUDA_TRY(launch_stage_sort(s->kp, (uint32_t *)tmp, st));
+        if (int r = stage_out(s, ids_out, tmp, bytes, mem_kind, st)) return r;
+    }
+    if (bin_start_out)
+        if (int r = stage_out(s, bin_start_out, s->kp.start, ((size_t)s->kp.bin_slots + 1) * sizeof(uint32_t), mem_kind, st))
+            return r;
+    return finish(s, mem_kind, stream);
+}
+
+int chemo_stage_forces(chemo_sim *s, float *F_out, int32_t *count_out, uint64_t *idsum_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !F_out) return fail(CHEMO_EINVAL, "sim and F_out are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t n = s->kp.n;
+    const size_t fb = ((size_t)n * s->kp.dim * sizeof(float) + 255) & ~(size_t)255;
+    const size_t cb = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
+    const size_t ib = (size_t)n * sizeof(uint64_t);
+    void *tmp;
+    if (int r = scratch(s, fb + cb + ib + 256, &tmp)) return r;
+    char *b = (char *)tmp;
+    CUDA_TRY(launch_stage_forces(s->kp, (float *)b, (int32_t *)(b + fb), (unsigned long long *)(b + fb + cb), st));
+    if (int r = stage_out(s, F_out, b, (size_t)n * s->kp.dim * sizeof(float), mem_kind, st)) return r;
+    if (int r = stage_out(s, count_out, b + fb, (size_t)n * sizeof(int32_t), mem_kind, st)) return r;
+    if (int r = stage_out(s, idsum_out, b + fb + cb, ib, mem_kind, st)) return r;
+    return finish(s, mem_kind, stream);
+}
+
+int chemo_stage_drift(chemo_sim *s, float *drift_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !drift_out) return fail(CHEMO_EINVAL, "sim and drift_out are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(float);
+    void *tmp;
+    if (int r = scratch(s, bytes + 256, &tmp)) return r;
+    CUDA_TRY(launch_stage_drift(s->kp, s->cur, (float *)tmp, st));
+    if (int r = stage_out(s, drift_out, tmp, bytes, mem_kind, st)) return r;
+    return finish(s, mem_kind, stream);
+}
+
+int chemo_stage_deposit(chemo_sim *s, float *S_out, float *R_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (!s->kp.has_grid) return fail(CHEMO_EINVAL, "this simulation has no grid (chem_mode 1)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t gb = ((size_t)s->kp.G * sizeof(float) + 255) & ~(size_t)255;
+    void *tmp;
+    if (int r = scratch(s, 2 * gb, &tmp)) return r;
+    float *dS = (float *)tmp, *dR = (float *)((char *)tmp + gb);
+    CUDA_TRY(cudaMemsetAsync(tmp, 0, 2 * gb, st));
+    CUDA_TRY(launch_stage_deposit(s->kp, dS, dR, st));
+    if (int r = stage_out(s, S_out, dS, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
+    if (int r = stage_out(s, R_out, dR, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
+    return finish(s, mem_kind, stream);
+}
+
+}  // extern "C"

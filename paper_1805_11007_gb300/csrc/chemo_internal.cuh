@@ -1,0 +1,260 @@
+// chemo_internal.cuh -- device-side definitions shared by the kernels and the
+// engine of the GB300 chemotaxis step (arXiv:1805.11007). Not part of the
+// public ABI (include/chemo.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace chemo {
+
+constexpr int MAXS = 8;
+constexpr uint32_t ID_BITS = 29;                 // particle id in the low 29 bits of .w
+constexpr uint32_t ID_MASK = (1u << ID_BITS) - 1u;
+constexpr uint32_t SP_SHIFT = ID_BITS;           // species in the top 3 bits
+
+// Latched device error bits (OR-ed into KP::err).
+enum : uint32_t {
+    ERR_NONFINITE = 1u,
+    ERR_DOMAIN = 2u,
+    ERR_OVERFLOW = 4u,
+    ERR_TIMEOUT = 8u,
+    ERR_SPECIES = 16u,
+};
+
+// Philox stream tags (third counter word).
+constexpr uint32_t TAG_MOVE = 0u;
+constexpr uint32_t TAG_REACT = 2u;
+
+// Kernel parameter block, passed by value to every kernel.
+struct KP {
+    // particles and cell list
+    int64_t n;
+    int dim, periodic, morton, search;  // search 1: 3^d bins >= r_c, 2: 2^d bins >= 2 r_c
+    int pairs;                          // 0: no pair interaction (inter = 0 or zero range)
+    float lo[3], hi[3], L[3], halfL[3];
+    int nb[3];
+    float inv_b[3];
+    int mbits;                          // Morton bits per axis
+    int64_t bin_slots;
+    // species tables (index s * MAXS + t)
+    int ns;
+    float rc2[MAXS * MAXS];      // r_c,st^2
+    float inv_eps[MAXS * MAXS];  // 1/eps_st
+    float amp_f[MAXS * MAXS];    // inter/eps_st
+    float shift[MAXS * MAXS];    // exp(-cutoff_factor) when force shifted, else 0
+    float noise[MAXS];           // sqrt(2 D_s dt)
+    float chem[MAXS];            // chi * chemotactic_s
+    float src[MAXS];             // k_s dt / h^d
+    float cons[MAXS];            // kappa_s / h^d
+    float rk0[MAXS], rkc[MAXS];  // switching rates
+    int rto[MAXS];
+    int reactions;
+    float dt;
+    double dt_d;                 // dt in double (switching decision)
+    uint32_t seed_lo, seed_hi;
+    int chem_mode;               // 0 grid, 1 fixed gradient
+    float fixed_g[3];
+    // grid
+    int has_grid;
+    int g[3];
+    int64_t G;
+    float inv_h[3], inv_2h[3], inv_h2[3];
+    int pde_bc;                  // 0 Neumann, 1 Dirichlet, 2 periodic
+    float Dc, gamma;
+    int substeps;
+    float dts;
+    int fused_deposit;           // 1: deposit straight into c^{n+1} (one substep)
+    // buffers
+    float4 *S, *U;               // sorted state, unsorted next state
+    uint32_t *slot;              // rank of each U entry inside its bin
+    float4 *dS, *dU;             // unwrapped displacement (optional)
+    uint32_t *cnt, *start;       // bin counts, bin offsets (bin_slots + 1)
+    unsigned long long *tiles;   // scan tile status
+    uint32_t *tile_ctr;          // dynamic tile counter of the scan
+    uint32_t *scan_seq;          // scan epoch counter
+    float *c[2];                 // chemical ping-pong buffers
+    float *srcg, *Rg;            // source and consumption grids (substeps > 1)
+    uint32_t *err;               // latched error bits
+    unsigned long long *step;    // absolute index of the step being computed
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), written from the
+// published definition: ten rounds of the 4x32 Philox S-box, Weyl key bumps.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Words of cell `id` at step `step` on stream `tag`: counter
+// (id, step lo, tag, step hi), key (seed lo, seed hi).
+__device__ __forceinline__ uint4 cell_words(const KP &kp, uint32_t id, unsigned long long step,
+                                            uint32_t tag)
+{
+    return philox4x32_10(make_uint4(id, (uint32_t)step, tag, (uint32_t)(step >> 32)), kp.seed_lo,
+                         kp.seed_hi);
+}
+
+// u = (w + 1/2) 2^-32 in single precision (never 0).
+__device__ __forceinline__ float word_uniform(uint32_t w)
+{
+    return fmaf((float)w, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+}
+
+// Box-Muller transform of the uniform pair (u(a), u(b)): two N(0,1) draws.
+__device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
+{
+    const float r = sqrtf(-2.0f * logf(word_uniform(a)));
+    float s, c;
+    sincospif(2.0f * word_uniform(b), &s, &c);
+    return make_float2(r * c, r * s);
+}
+
+// ---------------------------------------------------------------------------
+// Cell list: FP32 bin rule (no contraction) and bin keys.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bin_axis(float x, float lo, float inv_b, int nb)
+{
+    const float t = __fmul_rn(__fsub_rn(x, lo), inv_b);
+    int c = __float2int_rd(t);
+    c = c < 0 ? 0 : c;
+    return c > nb - 1 ? nb - 1 : c;
+}
+
+__device__ __forceinline__ uint32_t spread2(uint32_t v)  // 16 bits -> even bits
+{
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
+{
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t bin_key(const KP &kp, int cx, int cy, int cz)
+{
+    if (kp.morton) {
+        if (kp.dim == 2) return spread2((uint32_t)cx) | (spread2((uint32_t)cy) << 1);
+        return spread3((uint32_t)cx) | (spread3((uint32_t)cy) << 1) | (spread3((uint32_t)cz) << 2);
+    }
+    return (uint32_t)cx + (uint32_t)kp.nb[0] * ((uint32_t)cy + (uint32_t)kp.nb[1] * (uint32_t)cz);
+}
+
+__device__ __forceinline__ void cell_of(const KP &kp, float4 p, int &cx, int &cy, int &cz)
+{
+    cx = bin_axis(p.x, kp.lo[0], kp.inv_b[0], kp.nb[0]);
+    cy = bin_axis(p.y, kp.lo[1], kp.inv_b[1], kp.nb[1]);
+    cz = kp.dim == 3 ? bin_axis(p.z, kp.lo[2], kp.inv_b[2], kp.nb[2]) : 0;
+}
+
+__device__ __forceinline__ uint32_t key_of(const KP &kp, float4 p)
+{
+    int cx, cy, cz;
+    cell_of(kp, p, cx, cy, cz);
+    return bin_key(kp, cx, cy, cz);
+}
+
+// ---------------------------------------------------------------------------
+// Grid helpers. Nodes at lo + k h; C-order index x + gx (y + gy z).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t gidx(const KP &kp, int x, int y, int z)
+{
+    return (int64_t)x + (int64_t)kp.g[0] * ((int64_t)y + (int64_t)kp.g[1] * (int64_t)z);
+}
+
+// Neighbour node index with the ghost rule: mirror (walls) or wrap (periodic).
+__device__ __forceinline__ int gnbr(const KP &kp, int a, int k)
+{
+    const int N = kp.g[a];
+    if (kp.pde_bc == 2) return k < 0 ? k + N : (k >= N ? k - N : k);
+    if (k < 0) return -k;
+    if (k > N - 1) return 2 * (N - 1) - k;
+    return k;
+}
+
+// Grid cell containing x along axis a and the offset in it. The cell
+// coordinate t = (x - lo)/h is carried as t_hi + err with err the exact FMA
+// residual of the product, so the offset keeps ~2^-24 relative accuracy
+// instead of the ~2^-24 N absolute error of a rounded product.
+__device__ __forceinline__ void gcell(const KP &kp, int a, float x, int &k0, int &k1, float &f)
+{
+    const int N = kp.g[a];
+    const float rel = x - kp.lo[a];
+    const float th = __fmul_rn(rel, kp.inv_h[a]);
+    const float err = fmaf(rel, kp.inv_h[a], -th);
+    const float fl = floorf(th);
+    int k = (int)fl;
+    float fr = (th - fl) + err;
+    if (fr < 0.f) {
+        fr += 1.f;
+        k -= 1;
+    } else if (fr >= 1.f) {
+        fr -= 1.f;
+        k += 1;
+    }
+    if (kp.pde_bc == 2) {
+        k = k % N;
+        if (k < 0) k += N;
+        k0 = k;
+        k1 = k + 1 == N ? 0 : k + 1;
+        f = fr;
+    } else {
+        if (k < 0) {
+            f = (th - 0.f) + err;   // outside the first cell (x < lo): extrapolate in cell 0
+            k = 0;
+        } else if (k > N - 2) {
+            f = (th - (float)(N - 2)) + err;  // x at (or past) the last node: cell N-2
+            k = N - 2;
+        } else {
+            f = fr;
+        }
+        k0 = k;
+        k1 = k + 1;
+    }
+}
+
+__device__ __forceinline__ void set_err(const KP &kp, uint32_t bits) { atomicOr(kp.err, bits); }
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (kernels.cu). All launch on `st` and return the launch
+// status; counts of launched kernels are added to *launches when non-NULL.
+// ---------------------------------------------------------------------------
+cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches);
+cudaError_t launch_pack(const KP &kp, const float *pos, const uint8_t *sp, const float *disp,
+                        cudaStream_t st, int *launches);
+cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches);
+cudaError_t launch_scatter(const KP &kp, int cur, int advance_step, cudaStream_t st, int *launches);
+cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches);
+cudaError_t launch_unsort(const KP &kp, float *pos, uint8_t *sp, float *disp, cudaStream_t st);
+cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, cudaStream_t st);
+cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st);
+cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, cudaStream_t st);
+cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned long long *idsum,
+                                cudaStream_t st);
+cudaError_t launch_stage_drift(const KP &kp, int cur, float *drift, cudaStream_t st);
+cudaError_t launch_stage_deposit(const KP &kp, float *S, float *R, cudaStream_t st);
+cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);
+
+}  // namespace chemo

@@ -1,0 +1,86 @@
+"""Helpers of the GPU parity tests: run the CUDA library through its C ABI
+and the FP64 oracle on the same seeded inputs, and compare element by element.
+
+Tolerances (single step, FP32 GPU against FP64 oracle):
+  * pair force, per particle: |F_gpu - F_ref| <= 1e-5 * sum_j |f_ij| plus the
+    magnitude of the pairs within 1e-6 r_c^2 of the cutoff (either
+    classification is correct there), plus 1e-30 absolute;
+  * positions: 1e-5 L per component (minimum image when periodic), plus
+    dt times the borderline force magnitude;
+  * chemical field and deposit: 1e-5 * max |value| elementwise;
+  * drift: 1e-5 * max |drift| elementwise.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from oracle import chemo_oracle as orc
+from paper_1805_11007_gb300 import chemo
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def make_sim(p, pos, sp, c0=None):
+    sim = chemo.chemo_create(p, dev(pos), dev(sp))
+    if c0 is not None:
+        chemo.chemo_write_field(sim, dev(c0))
+    return sim
+
+
+def gpu_forces(sim):
+    n, d = sim.n, sim.dim
+    F = torch.zeros((n, d), dtype=torch.float32, device="cuda")
+    cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
+    ids = torch.zeros(n, dtype=torch.int64, device="cuda")
+    chemo.chemo_stage_forces(sim, F, cnt, ids)
+    torch.cuda.synchronize()
+    chemo.chemo_check(sim)
+    return F.cpu().numpy().astype(np.float64), cnt.cpu().numpy(), ids.cpu().numpy().view(np.uint64)
+
+
+def min_image(d, p):
+    d = np.array(d, dtype=np.float64)
+    if p.get("boundary", 0) == 1:
+        L = np.array(p["hi"][: d.shape[1]]) - np.array(p["lo"][: d.shape[1]])
+        d -= L * np.round(d / L)
+    return d
+
+
+def assert_forces_match(p, F_gpu, cnt_gpu, ids_gpu, pos, sp):
+    F, ex = orc.pair_forces(p, pos.astype(np.float64), sp, method=1, extras=True)
+    border = ex["border"] > 0
+    ok = ~border
+    np.testing.assert_array_equal(cnt_gpu[ok], ex["count"][ok])
+    np.testing.assert_array_equal(ids_gpu[ok], ex["idsum"][ok])
+    err = np.linalg.norm(F_gpu - F, axis=1)
+    tol = 1e-5 * ex["fabs"] + ex["border"] + 1e-30
+    bad = np.where(err > tol)[0]
+    assert bad.size == 0, "force mismatch at %s: err %s tol %s" % (bad[:5], err[bad[:5]], tol[bad[:5]])
+    return ex
+
+
+def assert_step_matches(p, pos0, sp0, c0, pos_g, sp_g, c_g, disp_g=None, step_index=0):
+    pos_r, sp_r, c_r, disp_r = orc.step(p, pos0.astype(np.float64), sp0,
+                                        None if c0 is None else c0.astype(np.float64), step_index=step_index,
+                                        disp=None if disp_g is None else np.zeros(pos0.shape))
+    _, ex = orc.pair_forces(p, pos0.astype(np.float64), sp0, method=1, extras=True)
+    L = float(max(np.array(p["hi"][: p["dim"]]) - np.array(p["lo"][: p["dim"]])))
+    d = np.abs(min_image(pos_g.astype(np.float64) - pos_r, p))
+    tol = 1e-5 * L + p["dt"] * ex["border"][:, None]
+    bad = np.argwhere(d > tol)
+    assert bad.size == 0, "position mismatch at %s: %s" % (bad[:5], d[tuple(bad[:5].T)])
+    if p.get("reactions", 0):
+        np.testing.assert_array_equal(sp_g, sp_r)
+    else:
+        np.testing.assert_array_equal(sp_g, sp0)
+    if c_g is not None:
+        scale = max(np.abs(c_r).max(), 1e-30)
+        dc = np.abs(c_g.astype(np.float64) - c_r) / scale
+        assert dc.max() <= 1e-5, "field mismatch: max rel %g at %s" % (dc.max(), np.unravel_index(dc.argmax(), dc.shape))
+    if disp_g is not None:
+        dd = np.abs(disp_g.astype(np.float64) - disp_r)
+        assert dd.max() <= 1e-5 * L + p["dt"] * ex["border"].max()
+    return pos_r, sp_r, c_r

@@ -1,0 +1,102 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/chemo.h declares, its struct layouts match the ctypes
+binding, and parameter validation rejects bad input before touching a GPU."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_1805_11007_gb300 import build as gb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "chemo.h")
+
+
+@pytest.fixture(scope="module")
+def chemo():
+    gb.build()
+    from paper_1805_11007_gb300 import chemo as c
+    return c
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chemo_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_function_is_exported(chemo):
+    names = _declared()
+    assert len(names) >= 20
+    out = subprocess.run(["nm", "-D", "--defined-only", gb.LIB], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r" T (chemo_[a-z_0-9]+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    L = chemo.lib()
+    for n in names:
+        assert hasattr(L, n)
+
+
+def test_struct_layouts_match_ctypes(chemo, tmp_path):
+    prog = tmp_path / "layout.c"
+    fields_p = [f for f, _ in chemo.chemo_params._fields_]
+    fields_i = [f for f, _ in chemo.chemo_info._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chemo.h"', "int main(void){",
+             'printf("%zu %zu\\n", sizeof(chemo_params), sizeof(chemo_info));']
+    for f in fields_p:
+        lines.append('printf("p %s %%zu\\n", offsetof(chemo_params, %s));' % (f, f))
+    for f in fields_i:
+        lines.append('printf("i %s %%zu\\n", offsetof(chemo_info, %s));' % (f, f))
+    lines.append("return 0;}")
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    sp, si = map(int, out[0].split())
+    assert sp == ctypes.sizeof(chemo.chemo_params)
+    assert si == ctypes.sizeof(chemo.chemo_info)
+    for line in out[1:]:
+        if not line:
+            continue
+        kind, name, off = line.split()
+        cls = chemo.chemo_params if kind == "p" else chemo.chemo_info
+        assert getattr(cls, name).offset == int(off), name
+
+
+def test_status_strings(chemo):
+    assert chemo.chemo_status_string(0) == "ok"
+    assert "invalid" in chemo.chemo_status_string(chemo.EINVAL)
+    assert chemo.chemo_status_string(12345) == "unknown status"
+
+
+@pytest.mark.parametrize("bad", [
+    dict(dim=4), dict(n_species=0), dict(n_species=9), dict(dt=0.0), dict(grid=[2, 64, 1]),
+    dict(boundary=1, pde_bc=0), dict(boundary=0, pde_bc=2), dict(cutoff_mode=3), dict(search_mode=5),
+    dict(hi=[0.0, 1.0, 1.0]), dict(react_to=[5, 0]),
+])
+def test_invalid_parameters_rejected_on_host(chemo, bad):
+    from paper_1805_11007_gb300 import workloads as wl
+    p = wl.params("walls_grid_2d", grid=[64, 64, 1])
+    p.update(bad)
+    with pytest.raises(chemo.ChemoError) as ei:
+        chemo.chemo_create(p, np.zeros((0, p["dim"] if p["dim"] in (2, 3) else 2), np.float32),
+                           np.zeros(0, np.uint8))
+    assert ei.value.status == chemo.EINVAL
+
+
+def test_struct_size_mismatch_rejected(chemo):
+    from paper_1805_11007_gb300 import workloads as wl
+    prm = chemo.make_params(wl.params("walls_grid_2d"))
+    prm.struct_size = 12
+    out = ctypes.c_void_p()
+    st = chemo.lib().chemo_create(ctypes.byref(prm), 0, None, None, 0, None, ctypes.byref(out))
+    assert st == chemo.EINVAL
+    assert "struct_size" in chemo.chemo_last_error()
+
+
+def test_gradient_reports_not_supported_without_device(chemo):
+    st = chemo.lib().chemo_gradient(None, 1, 1, None, None, None, None, 0, None)
+    assert st == chemo.ENOTSUP

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA library (through its C ABI) against the FP64 oracle on
+identical seeded inputs, row by row of the step and for whole steps.
+
+Rows: a1 bins (bit-exact), a2 counting sort (valid permutation, bins in
+order), a3 pair force and neighbour sets, a4 gradient interpolation, a5 move
+and boundary, a6 deposit, a7 PDE; whole steps at sizes that span many tiles
+with ragged tails, the full-size 3D clump workload, and edge cases.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import chemo_oracle as orc
+from paper_1805_11007_gb300 import chemo
+from paper_1805_11007_gb300 import workloads as wl
+from parity_util import (assert_forces_match, assert_step_matches, dev, gpu_forces, make_sim)
+
+pytestmark = pytest.mark.gpu
+
+
+# ---------------------------------------------------------------------------
+# Philox: device generator == oracle generator, all four counter words
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 7, 0xDEADBEEFCAFEF00D])
+def test_device_philox_matches_oracle(seed):
+    rng = np.random.default_rng(seed & 0xFFFF)
+    ctr = rng.integers(0, 2 ** 32, size=(5003, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [1, 2, 3, 4]]
+    out = np.zeros_like(ctr)
+    chemo.chemo_philox(seed, ctr, out)
+    np.testing.assert_array_equal(out, orc.philox(ctr, seed))
+
+
+# ---------------------------------------------------------------------------
+# a1 / a2: bins and counting sort
+# ---------------------------------------------------------------------------
+def _morton(cells, dim):
+    key = np.zeros(cells.shape[0], dtype=np.uint64)
+    for b in range(16 if dim == 2 else 10):
+        for a in range(dim):
+            key |= ((cells[:, a].astype(np.uint64) >> np.uint64(b)) & np.uint64(1)) << np.uint64(b * dim + a)
+    return key
+
+
+BIN_CASES = [
+    # (workload, overrides, n)
+    ("walls_grid_2d", dict(bin_side=0.0101, search_mode=1, bin_order=1), 20011),
+    ("walls_grid_2d", dict(bin_side=0.0203, search_mode=2, bin_order=2), 20011),
+    ("periodic_fixed_gradient_2d", dict(bin_side=0.0125, search_mode=1, bin_order=2), 1000),
+    ("clumps_grid_3d", dict(bin_side=0.0041, search_mode=1, bin_order=2, grid=[32, 32, 32]), 60001),
+    ("clumps_grid_3d", dict(bin_side=0.0081, search_mode=2, bin_order=1, grid=[32, 32, 32]), 60001),
+]
+
+
+@pytest.mark.parametrize("name,over,n", BIN_CASES)
+def test_bins_exact_and_sort_valid(name, over, n):
+    p, pos, sp = wl.initial_state(name, n=n, **over)
+    pos[:7, 0] = 0.0
+    if p["boundary"] == 0:
+        pos[7:14, 1] = 1.0
+    with make_sim(p, pos, sp) as sim:
+        info = chemo.chemo_get_info(sim)
+        cells = np.zeros((n, p["dim"]), np.int32)
+        chemo.chemo_stage_bins(sim, cells)
+        ref, nb = orc.bins_f32(p, p["bin_side"], pos)
+        assert tuple(info["nbins"][: p["dim"]]) == nb[: p["dim"]]
+        np.testing.assert_array_equal(cells, ref)
+        ids = np.zeros(n, np.uint32)
+        start = np.zeros(info["bin_slots"] + 1, np.uint32)
+        chemo.chemo_stage_sort(sim, ids, start)
+    assert np.array_equal(np.sort(ids), np.arange(n, dtype=np.uint32))  # permutation
+    assert start[0] == 0 and start[-1] == n and np.all(np.diff(start.astype(np.int64)) >= 0)
+    if info["morton"]:
+        key = _morton(ref, p["dim"])
+    else:
+        key = np.zeros(n, np.int64)
+        for a in reversed(range(p["dim"])):
+            key = key * nb[a] + ref[:, a]
+    k_sorted = key[ids].astype(np.int64)
+    j = np.arange(n)
+    assert np.all(start[k_sorted] <= j) and np.all(j < start[k_sorted + 1])
+
+
+# ---------------------------------------------------------------------------
+# a3: pair force and neighbour sets
+# ---------------------------------------------------------------------------
+FORCE_CASES = [
+    ("periodic_fixed_gradient_2d", dict(), 1000),
+    ("periodic_fixed_gradient_2d", dict(diameter=[0.03], search_mode=2), 3001),
+    ("walls_grid_2d", dict(diameter=[0.01, 0.02], grid=[64, 64, 1]), 30007),
+    ("walls_grid_2d", dict(diameter=[0.01, 0.02], grid=[64, 64, 1], search_mode=2, bin_order=2), 30007),
+    ("walls_grid_2d", dict(diameter=[0.01, 0.02], grid=[64, 64, 1], cutoff_mode=1, cutoff_factor=1.5,
+                           inter=2.5), 30007),
+    ("clumps_grid_3d", dict(diameter=[0.01, 0.02], grid=[16, 16, 16]), 80021),
+    ("clumps_grid_3d", dict(diameter=[0.01, 0.02], grid=[16, 16, 16], search_mode=2, bin_order=1), 80021),
+    ("clumps_grid_3d", dict(diameter=[0.02, 0.03], grid=[16, 16, 16], boundary=1, pde_bc=2), 40009),
+]
+
+
+@pytest.mark.parametrize("name,over,n", FORCE_CASES)
+def test_pair_forces_match_oracle(name, over, n):
+    p, pos, sp = wl.initial_state(name, n=n, **over)
+    with make_sim(p, pos, sp) as sim:
+        F, cnt, ids = gpu_forces(sim)
+    ex = assert_forces_match(p, F, cnt, ids, pos, sp)
+    assert ex["count"].mean() > 1.0  # real neighbourhoods
+
+
+def test_dense_cluster_single_bin():
+    # 3000 cells inside one bin: long candidate lists, heavy overlap
+    p = wl.params("walls_grid_2d", diameter=[0.02, 0.02], grid=[16, 16, 1])
+    rng = np.random.default_rng(0)
+    pos = (0.5 + 0.004 * rng.random((3000, 2))).astype(np.float32)
+    sp = wl.half_species(3000, 2)
+    with make_sim(p, pos, sp) as sim:
+        F, cnt, ids = gpu_forces(sim)
+    assert_forces_match(p, F, cnt, ids, pos, sp)
+
+
+# ---------------------------------------------------------------------------
+# a4: gradient interpolation
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,over,n", [
+    ("walls_grid_2d", dict(grid=[97, 65, 1]), 20011),
+    ("clumps_grid_3d", dict(grid=[33, 29, 31]), 30011),
+    ("walls_grid_2d", dict(grid=[64, 48, 1], boundary=1, pde_bc=2, diameter=[0.004, 0.004]), 20011),
+])
+def test_drift_matches_oracle(name, over, n):
+    p, pos, sp = wl.initial_state(name, n=n, chi=1.7, **over)
+    pos[:5, 0] = p["lo"][0]
+    c0 = wl.random_field(p, seed=11)
+    with make_sim(p, pos, sp, c0) as sim:
+        d = torch.zeros((n, p["dim"]), dtype=torch.float32, device="cuda")
+        chemo.chemo_stage_drift(sim, d)
+        d = d.cpu().numpy().astype(np.float64)
+    ref = orc.drift(p, pos.astype(np.float64), sp, c0.astype(np.float64))
+    scale = np.abs(ref).max()
+    assert scale > 0
+    assert np.abs(d - ref).max() <= 1e-5 * scale
+
+
+# ---------------------------------------------------------------------------
+# a6: deposit
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("name,over,n", [
+    ("walls_grid_2d", dict(grid=[129, 97, 1], consume=[0.0, 0.3]), 40009),
+    ("clumps_grid_3d", dict(grid=[40, 36, 33], consume=[0.0, 0.3]), 50021),
+    ("walls_grid_2d", dict(grid=[64, 64, 1], boundary=1, pde_bc=2, diameter=[0.004, 0.004]), 20011),
+])
+def test_deposit_matches_oracle(name, over, n):
+    p, pos, sp = wl.initial_state(name, n=n, **over)
+    pos[:5, 0] = p["lo"][0]
+    if p["boundary"] == 0:
+        pos[5:10, 1] = p["hi"][1]
+    shape = orc.grid_shape(p)
+    with make_sim(p, pos, sp) as sim:
+        S = np.zeros(shape, np.float32)
+        R = np.zeros(shape, np.float32)
+        chemo.chemo_stage_deposit(sim, S, R)
+    Sr, Rr = orc.deposit(p, pos.astype(np.float64), sp)
+    assert np.abs(S - Sr).max() <= 1e-5 * np.abs(Sr).max()
+    if np.abs(Rr).max() > 0:
+        assert np.abs(R - Rr).max() <= 1e-5 * np.abs(Rr).max()
+
+
+# ---------------------------------------------------------------------------
+# a5 + a7: whole steps
+# ---------------------------------------------------------------------------
+STEP_CASES = [
+    # fixed gradient, periodic, displacement tracking (the MSD set-up)
+    ("periodic_fixed_gradient_2d", dict(), 1000, 0),
+    # grid with one fused substep (PDE concurrent with the particle kernel)
+    ("walls_grid_2d", dict(grid=[128, 128, 1]), 20011, 3),
+    # many substeps (separate source grid)
+    ("walls_grid_2d", dict(grid=[512, 512, 1]), 20011, 0),
+    # consumption, fused and not fused
+    ("walls_grid_2d", dict(grid=[128, 128, 1], consume=[0.0, 0.5]), 20011, 0),
+    ("walls_grid_2d", dict(grid=[256, 256, 1], consume=[0.0, 0.5]), 20011, 0),
+    # Dirichlet walls (held), periodic grid
+    ("walls_grid_2d", dict(grid=[96, 80, 1], pde_bc=1), 12007, 0),
+    ("walls_grid_2d", dict(grid=[96, 80, 1], boundary=1, pde_bc=2, diameter=[0.004, 0.008]), 12007, 0),
+    # 3D, clumps, 7-point stencil
+    ("clumps_grid_3d", dict(grid=[48, 48, 48], diameter=[0.01, 0.02]), 60013, 0),
+    ("clumps_grid_3d", dict(grid=[40, 44, 36], diameter=[0.01, 0.02], search_mode=2), 60013, 5),
+    # large steps that reflect more than once
+    ("walls_grid_2d", dict(grid=[64, 64, 1], D=[3000.0, 2000.0], dt=1e-4), 5003, 0),
+]
+
+
+@pytest.mark.parametrize("name,over,n,step0", STEP_CASES)
+def test_step_matches_oracle(name, over, n, step0):
+    p, pos, sp = wl.initial_state(name, n=n, **over)
+    c0 = wl.random_field(p, seed=5, scale=0.3) if p["chem_mode"] == 0 else None
+    with make_sim(p, pos, sp, c0) as sim:
+        if step0:
+            chemo.chemo_set_step_index(sim, step0)
+        chemo.chemo_step(sim)
+        assert chemo.chemo_step_index(sim) == step0 + 1
+        pos_g, sp_g, disp_g = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim) if c0 is not None else None
+    assert_step_matches(p, pos, sp, c0, pos_g, sp_g, c_g, disp_g, step_index=step0)
+
+
+def test_reactions_step_matches_oracle():
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=40009, grid=[128, 128, 1], reactions=1,
+                                  react_k0=[3000.0, 0.0], react_kc=[0.0, 2000.0], react_to=[1, 0])
+    c0 = wl.random_field(p, seed=9, scale=2.0)
+    with make_sim(p, pos, sp, c0) as sim:
+        chemo.chemo_step(sim)
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim)
+    pos_r, sp_r, c_r, _ = orc.step(p, pos, sp, c0.astype(np.float64))
+    # the switching decision compares u with (k0 + kc c(X)) dt; c(X) differs
+    # between FP32 and FP64 by rounding, so cells within 1e-6 of a tie may
+    # differ. All others must agree.
+    conc = orc.conc(p, pos.astype(np.float64), c0.astype(np.float64))
+    ctr = np.zeros((pos.shape[0], 4), np.uint32)
+    ctr[:, 0] = np.arange(pos.shape[0])
+    ctr[:, 2] = orc.TAG_REACT
+    u = (orc.philox(ctr, p["seed"])[:, 0].astype(np.float64) + 0.5) / 2 ** 32
+    k0 = np.array([np.float32(3000.0), 0.0])[sp]
+    kc = np.array([0.0, np.float32(2000.0)])[sp]
+    prop = (k0 + kc * conc) * p["dt"]
+    tie = np.abs(u - prop) <= 1e-6 * np.maximum(prop, 1e-30) + 1e-12
+    assert (sp_r != sp).sum() > 100
+    np.testing.assert_array_equal(sp_g[~tie], sp_r[~tie])
+    assert np.abs(pos_g - pos_r).max() <= 1e-5
+    assert np.abs(c_g - c_r).max() <= 1e-4 * np.abs(c_r).max()  # deposit differs only on tie cells
+
+
+def test_step_n_equals_repeated_steps_and_oracle():
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=20011, grid=[128, 128, 1])
+    c0 = wl.random_field(p, seed=5, scale=0.3)
+    k = 21  # exercises the 16-step graph, the 2-step graph and a direct step
+    with make_sim(p, pos, sp, c0) as a, make_sim(p, pos, sp, c0) as b:
+        chemo.chemo_step_n(a, k)
+        for _ in range(k):
+            chemo.chemo_step(b)
+        pa, _, _ = chemo.read_state_host(a)
+        pb, _, _ = chemo.read_state_host(b)
+        ca = chemo.read_field_host(a)
+        cb = chemo.read_field_host(b)
+        assert chemo.chemo_step_index(a) == k
+    # same kernels, same inputs; float atomics may reorder the deposit sums
+    assert np.abs(pa - pb).max() <= 1e-6
+    assert np.abs(ca - cb).max() <= 1e-5 * np.abs(ca).max()
+    pr, _, cr, _ = orc.run(p, pos, sp, c0.astype(np.float64), nsteps=k)
+    # k steps: per-step errors add up (no pair crosses the cutoff over this
+    # horizon in practice; allow k times the single-step tolerance)
+    assert np.abs(pa - pr).max() <= k * 1e-5
+    assert np.abs(ca - cr).max() <= k * 1e-5 * np.abs(cr).max()
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads, in the launch configuration the benchmark times
+# ---------------------------------------------------------------------------
+def test_full_size_clumps_3d_step():
+    p, pos, sp = wl.initial_state("clumps_grid_3d")
+    c0 = wl.random_field(p, seed=7, scale=0.05)
+    with make_sim(p, pos, sp, c0) as sim:
+        info = chemo.chemo_get_info(sim)
+        assert info["pde_substeps"] == 1
+        chemo.chemo_step_n(sim, 1)
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim)
+    orc.set_threads(max(1, orc.get_threads()))
+    assert_step_matches(p, pos, sp, c0, pos_g, sp_g, c_g)
+
+
+def test_full_size_walls_2d_step():
+    p, pos, sp = wl.initial_state("walls_grid_2d")
+    c0 = wl.random_field(p, seed=8, scale=0.1)
+    with make_sim(p, pos, sp, c0) as sim:
+        assert chemo.chemo_get_info(sim)["pde_substeps"] == 12
+        chemo.chemo_step_n(sim, 1)
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim)
+    assert_step_matches(p, pos, sp, c0, pos_g, sp_g, c_g)
+
+
+def test_full_size_deposit_conserves_mass():
+    # property at any size: the trapezoid integral of the deposited source is
+    # dt * sum_i k_{s_i}
+    p, pos, sp = wl.initial_state("clumps_grid_3d")
+    with make_sim(p, pos, sp) as sim:
+        S = torch.zeros(orc.grid_shape(p), dtype=torch.float32, device="cuda")
+        chemo.chemo_stage_deposit(sim, S, None)
+        S = S.double()
+    h = 1.0 / 255
+    w = torch.ones(256, dtype=torch.float64, device="cuda")
+    w[0] = w[-1] = 0.5
+    mass = torch.einsum("zyx,z,y,x->", S, w, w, w).item() * h ** 3
+    expect = p["dt"] * float(np.float32(0.1)) * (sp == 0).sum()
+    assert abs(mass - expect) <= 1e-5 * expect
+
+
+# ---------------------------------------------------------------------------
+# Edge cases
+# ---------------------------------------------------------------------------
+def test_empty_and_single_particle():
+    p = wl.params("walls_grid_2d", grid=[33, 33, 1])
+    with make_sim(p, np.zeros((0, 2), np.float32), np.zeros(0, np.uint8)) as sim:
+        chemo.chemo_step_n(sim, 3)
+        c = chemo.read_field_host(sim)
+        assert np.all(c == 0.0)
+        chemo.chemo_check(sim)
+    pos = np.array([[0.5, 0.5]], np.float32)
+    sp = np.array([0], np.uint8)
+    with make_sim(p, pos, sp) as sim:
+        chemo.chemo_step(sim)
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim)
+    assert_step_matches(p, pos, sp, np.zeros(orc.grid_shape(p), np.float32), pos_g, sp_g, c_g)
+
+
+def test_host_buffers_round_trip():
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=1025, grid=[33, 33, 1])
+    sim = chemo.chemo_create(p, pos, sp)  # host memory
+    try:
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        np.testing.assert_array_equal(pos_g, pos)
+        np.testing.assert_array_equal(sp_g, sp)
+        pos2 = np.ascontiguousarray(pos[::-1])
+        chemo.chemo_write_state(sim, pos2, sp)
+        pos_g, _, _ = chemo.read_state_host(sim)
+        np.testing.assert_array_equal(pos_g, pos2)
+    finally:
+        sim.close()
+
+
+def test_bad_device_input_is_latched():
+    p = wl.params("walls_grid_2d", grid=[33, 33, 1])
+    pos = np.full((10, 2), 0.5, np.float32)
+    pos[3, 0] = np.nan
+    with make_sim(p, pos, np.zeros(10, np.uint8)) as sim:
+        with pytest.raises(chemo.ChemoError) as ei:
+            chemo.chemo_check(sim)
+        assert ei.value.status == chemo.ENONFINITE
+        chemo.chemo_check(sim)  # cleared
+
+
+def test_set_params_changes_model_constants():
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=5003, grid=[64, 64, 1])
+    with make_sim(p, pos, sp) as sim:
+        q = dict(p, chi=3.0, D=[0.5, 0.25], inter=2.0)
+        chemo.chemo_set_params(sim, q)
+        chemo.chemo_step(sim)
+        pos_g, sp_g, _ = chemo.read_state_host(sim)
+        c_g = chemo.read_field_host(sim)
+        with pytest.raises(chemo.ChemoError):
+            chemo.chemo_set_params(sim, dict(p, grid=[65, 64, 1]))
+    assert_step_matches(q, pos, sp, np.zeros(orc.grid_shape(p), np.float32), pos_g, sp_g, c_g)
