@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the chemotaxis particle step on GB300.
+
+Workload (default): the 3D clump workload: unit cube with reflecting walls,
+1,000,000 cells of two species (diameters 0.002 / 0.004, D = 1 / 0.5) drawn
+from 8 Gaussian clumps (sigma 0.05), chemical on a 256^3 grid (7-point
+stencil, decay 0.1, secretion 0.1 by species 0, c0 = 0), dt = 1e-6, runs of
+200 steps. A timed step is one pass of the whole step (bin, sort, pair force,
+gradient interpolation, move, deposit, PDE). The timed region advances the
+simulation in runs of 200 steps, each started from the seeded initial state
+(the reset is inside the timed region and counted as launches).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun), every rank runs its own
+replicate (seed + rank); no data moves between ranks (weak scaling), only the
+timing barrier and the max over ranks.
+
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a self-similar sample of the same workload (fewer cells, clumps and
+grid scaled so the per-cell and per-node work is unchanged), sized so the
+whole run ends within a few minutes.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/sec at N=1M 3D (and % HBM roofline); adjoint/forward time ratio"
+UNIT = "particle-steps/s"
+WORKLOAD = "clumps_grid_3d"
+RUN_STEPS = 200
+BASE_SEED = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=200)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-steps", type=int, default=50)
+    return ap.parse_args()
+
+
+def workload_config(p, n):
+    return {
+        "workload": "%s: 3D unit cube, reflecting walls, N=%d two species (diameters %g/%g, D=%g/%g), "
+                    "8 Gaussian clumps sigma 0.05, %dx%dx%d grid (7-point, D_c=%g, gamma=%g, k_0=%g), dt=%g, "
+                    "runs of %d steps from the initial state"
+                    % (WORKLOAD, n, p["diameter"][0], p["diameter"][1], p["D"][0], p["D"][1], p["grid"][0],
+                       p["grid"][1], p["grid"][2], p["Dc"], p["gamma"], p["secrete"][0], p["dt"], RUN_STEPS),
+        "n_particles": n,
+        "grid": list(p["grid"]),
+        "dt": p["dt"],
+        "run_steps": RUN_STEPS,
+        "l2": "inputs larger than L2: c ping-pong 2 x 64 MiB + particles 40 MB per step > 126 MB L2",
+    }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# nvidia-smi clock sampler
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp,index,utilization.gpu,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.fh = None
+
+    def start(self):
+        try:
+            self.fh = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.seek(0)
+        rows = [r.split(", ") for r in self.fh.read().strip().splitlines() if r.strip()]
+        load = [r for r in rows if len(r) >= 11 and r[2].strip().isdigit() and int(r[2]) >= 50]
+        use = load if load else rows
+        mhz = [float(r[3]) for r in use if r[3].replace(".", "").isdigit()]
+        mx = [float(r[4]) for r in use if r[4].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in use:
+            for k, nm in enumerate(names):
+                if len(r) > 7 + k and r[7 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows), "samples_under_load": len(load)}
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_full(p, pos, sp, budget_s=12.0, max_steps=10):
+    """The oracle (as it stands) advancing the full workload for a few steps."""
+    import numpy as np
+    from oracle import chemo_oracle as orc
+    th = oracle_threads()
+    orc.set_threads(th)
+    c = np.zeros(orc.grid_shape(p))
+    x = pos.astype(np.float64)
+    s = sp.copy()
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        x, s, c, _ = orc.step(p, x, s, c, step_index=steps)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": pos.shape[0] * steps / el, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+            "sample": "%d full steps of the %d-cell 3D clump workload (FP64 oracle, OpenMP)" % (steps, pos.shape[0])}
+
+
+def scaled_sample(frac, seed):
+    """Self-similar sample of the clump workload: frac of the cells, clump
+    sigma and grid side scaled by frac^(1/3) so the cell density and the
+    nodes per cell are unchanged."""
+    from paper_1805_11007_gb300 import workloads as wl
+    import numpy as np
+    full = wl.WORKLOADS[WORKLOAD]
+    n = max(2048, int(full["n"] * frac))
+    lin = (n / full["n"]) ** (1.0 / 3.0)
+    g = max(8, int(round(256 * lin)))
+    p = wl.params(WORKLOAD, grid=[g, g, g], seed=seed)
+    pos = wl.clump_positions(n, 3, p["lo"], p["hi"], seed, sigma=0.05 * lin)
+    sp = wl.half_species(n, 2)
+    return p, pos, sp
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import chemo_oracle as orc
+    from paper_1805_11007_gb300 import workloads as wl
+    orc.build()
+    th = oracle_threads()
+    orc.set_threads(th)
+    # calibrate the per-cell cost on a 1/64 sample, then size the sample so
+    # warmup + steps take about 150 s
+    p, pos, sp = scaled_sample(1.0 / 64.0, BASE_SEED)
+    c = np.zeros(orc.grid_shape(p))
+    t0 = time.perf_counter()
+    orc.step(p, pos, sp, c)
+    per_cell = (time.perf_counter() - t0) / pos.shape[0]
+    budget = 150.0
+    n_target = budget / max(1, args.steps + args.warmup) / max(per_cell, 1e-12)
+    frac = min(1.0, max(2048.0, n_target) / wl.WORKLOADS[WORKLOAD]["n"])
+    p, pos, sp = scaled_sample(frac, BASE_SEED)
+    x = pos.astype(np.float64)
+    s = sp.copy()
+    c = np.zeros(orc.grid_shape(p))
+    step = 0
+    for _ in range(args.warmup):
+        x, s, c, _ = orc.step(p, x, s, c, step_index=step)
+        step += 1
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        x, s, c, _ = orc.step(p, x, s, c, step_index=step)
+        step += 1
+    el = time.perf_counter() - t0
+    n = pos.shape[0]
+    value = n * args.steps / el
+    sample = ("self-similar sample of the clump workload: %d cells, clump sigma %.4f, %d^3 grid (per-cell and "
+              "per-node work of the full workload); FP64 oracle on %d host threads" %
+              (n, 0.05 * (n / 1e6) ** (1 / 3), p["grid"][0], orc.get_threads()))
+    full_p = wl.params(WORKLOAD)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(workload_config(full_p, 1_000_000), sample=sample),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_1805_11007_gb300 import build as gb
+    gb.build()
+    from paper_1805_11007_gb300 import chemo
+    from paper_1805_11007_gb300 import workloads as wl
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    p, pos, sp = wl.initial_state(WORKLOAD, seed=BASE_SEED + rank)
+    n = pos.shape[0]
+    devc = torch.device("cuda", local)
+    pos0 = torch.from_numpy(pos).to(devc)
+    sp0 = torch.from_numpy(sp).to(devc)
+    zero_c = torch.zeros(chemo.grid_shape(p), dtype=torch.float32, device=devc)
+    stream = torch.cuda.current_stream()
+    sim = chemo.chemo_create(p, pos0, sp0, stream=stream)
+    info = chemo.chemo_get_info(sim)
+    per_step = info["launches_per_step"]
+    reset_launches = 3  # pack, scan, scatter
+
+    state = {"in_run": 0, "resets": 0}
+
+    def reset():
+        chemo.chemo_write_state(sim, pos0, sp0, stream=stream)
+        chemo.chemo_write_field(sim, zero_c, stream=stream)
+        chemo.chemo_set_step_index(sim, 0, stream=stream)
+        state["in_run"] = 0
+        state["resets"] += 1
+
+    def advance(k):
+        while k > 0:
+            if state["in_run"] == RUN_STEPS:
+                reset()
+            m = min(k, RUN_STEPS - state["in_run"])
+            chemo.chemo_step_n(sim, m, stream=stream)
+            state["in_run"] += m
+            k -= m
+
+    # pair interactions per step on the initial state (in-cutoff, directed)
+    cnt = torch.zeros(n, dtype=torch.int32, device=devc)
+    F = torch.zeros((n, 3), dtype=torch.float32, device=devc)
+    chemo.chemo_stage_forces(sim, F, cnt, None, stream=stream)
+    pairs_per_step = int(cnt.sum().item())
+    del F, cnt
+
+    reset()
+    advance(args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    resets0 = state["resets"]
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    advance(args.steps)
+    ev1.record(stream)
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    clock_rec = clocks.stop()
+    resets_in = state["resets"] - resets0
+    chemo.chemo_check(sim, stream=stream)
+    t_local = torch.tensor([ms], dtype=torch.float64, device=devc)
+    if dist is not None:
+        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    value = n * args.steps * world / (ms_max * 1e-3)
+    ms_per_step = ms_max / args.steps
+
+    # per-kernel device times (same kernels, streams and overlap as a step)
+    reset()
+    prof = chemo.chemo_profile_steps(sim, min(args.profile_steps, RUN_STEPS), stream=stream)
+    state["in_run"] = min(args.profile_steps, RUN_STEPS)
+    G = int(np.prod(p["grid"]))
+    s = info["pde_substeps"]
+    hbm, peak_kind = measured_peaks()
+    bytes_per = {
+        # algorithmic bytes per launch: state read + write (16 + 16 B) and the
+        # bin slot (4 B) per cell; read + write of c per node per substep
+        "k_step": 36.0 * n,
+        "k_pde": 8.0 * G * s,
+        "k_scan": 8.0 * info["bin_slots"] + 4.0,
+        "k_scatter": 36.0 * n,
+    }
+    kern = {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter")}
+    dom = max(kern, key=kern.get)
+    achieved = bytes_per[dom] / (kern[dom] * 1e-3) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "traffic": None, "kernel_ms": kern, "step_ms_profiled": prof["step"]}
+    floor_bytes = 42.0 * n + 8.0 * G * s
+    step_floor = {"bytes_per_step": floor_bytes, "achieved_GBps": floor_bytes / (ms_per_step * 1e-3) / 1e9,
+                  "frac": floor_bytes / (ms_per_step * 1e-3) / 1e9 / hbm}
+
+    # end to end through the C ABI with host buffers: every step uploads the
+    # state from pinned host memory, steps, and reads the positions back
+    e2e = None
+    if not args.no_e2e:
+        pos_h = torch.from_numpy(pos.copy()).pin_memory()
+        sp_h = torch.from_numpy(sp.copy()).pin_memory()
+        reset()
+        k_e2e = min(args.steps, RUN_STEPS)
+        for _ in range(3):
+            chemo.chemo_write_state(sim, pos_h, sp_h, stream=stream)
+            chemo.chemo_step(sim, stream=stream)
+            chemo.chemo_read_state(sim, pos_h, sp_h, stream=stream)
+        pos_h.copy_(torch.from_numpy(pos))
+        sp_h.copy_(torch.from_numpy(sp))
+        reset()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            chemo.chemo_write_state(sim, pos_h, sp_h, stream=stream)
+            chemo.chemo_step(sim, stream=stream)
+            chemo.chemo_read_state(sim, pos_h, sp_h, stream=stream)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        tt = torch.tensor([el], dtype=torch.float64, device=devc)
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e = {"value": n * k_e2e * world / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(pos_h.numel() * 4 + sp_h.numel()),
+               "d2h_bytes_per_step": int(pos_h.numel() * 4 + sp_h.numel()), "steps": k_e2e,
+               "how": "per step: chemo_write_state from pinned host (positions + species), chemo_step, "
+                      "chemo_read_state to pinned host; the chemical grid stays on the device"}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_full(p, pos, sp)
+        except Exception as exc:  # the baseline must not sink the GPU line
+            cpu = {"value": None, "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+                   "sample": "failed: %s" % exc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(p, n), parallelism="replicas x%d (independent seeds)" % world),
+            "roofline": roofline, "step_floor": step_floor, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(args.steps * per_step + resets_in * reset_launches),
+            "clocks": clock_rec,
+            "pair_interactions_per_s": pairs_per_step / (ms_per_step * 1e-3),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

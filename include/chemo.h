@@ -187,6 +187,15 @@ int chemo_check(chemo_sim *sim, void *stream);
 /* Fills *info. */
 int chemo_get_info(const chemo_sim *sim, chemo_info *info);
 
+/* Measurement: advances nsteps steps exactly like chemo_step (same kernels,
+ * same streams, the PDE still overlapped with the particle kernel), with a
+ * CUDA event pair around every kernel on the stream it runs on. Returns in
+ * kernel_ms[CHEMO_PROF_SLOTS] the mean device time per step of each kernel
+ * class (particle step, PDE (all substeps), scan, scatter + deposit) and, in
+ * the last slot, the mean time of a whole step. Synchronises `stream`. */
+#define CHEMO_PROF_SLOTS 5
+int chemo_profile_steps(chemo_sim *sim, int64_t nsteps, float *kernel_ms, void *stream);
+
 /* Releases every resource of sim (NULL is ignored). Synchronises the device
  * work of the simulation first. */
 void chemo_destroy(chemo_sim *sim);

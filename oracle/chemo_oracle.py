@@ -197,7 +197,8 @@ def bins_f32(params: dict, bin_side: float, pos_f32) -> tuple[np.ndarray, tuple]
     pos = np.ascontiguousarray(np.asarray(pos_f32, dtype=np.float32).reshape(-1, p.dim))
     cells = np.zeros(pos.shape, dtype=np.int32)
     nb = np.zeros(3, dtype=np.int32)
-    lib().orc_bins_f32(ctypes.byref(p), float(bin_side), pos.shape[0], _ptr(pos), _ptr(cells), _ptr(nb))
+    # the bin side is a single-precision parameter of the GPU library
+    lib().orc_bins_f32(ctypes.byref(p), _f32(bin_side), pos.shape[0], _ptr(pos), _ptr(cells), _ptr(nb))
     return cells, tuple(int(v) for v in nb)
 
 

@@ -165,6 +165,7 @@ def _declare(L):
         "chemo_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "chemo_last_error": ([], ctypes.c_char_p),
         "chemo_philox": ([ctypes.c_uint64, vp, vp, i64, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_profile_steps": ([vp, i64, vp, vp], ctypes.c_int),
         "chemo_stage_bins": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_sort": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_forces": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
@@ -344,6 +345,17 @@ def chemo_get_info(sim: Sim) -> dict:
     _check(lib().chemo_get_info(_h(sim), ctypes.byref(info)), "chemo_get_info")
     return {name: (list(getattr(info, name)) if hasattr(getattr(info, name), "__len__") else getattr(info, name))
             for name, _ in chemo_info._fields_}
+
+
+PROF_SLOTS = 5
+PROF_NAMES = ("k_step", "k_pde", "k_scan", "k_scatter", "step")
+
+
+def chemo_profile_steps(sim: Sim, nsteps: int, stream=None) -> dict:
+    """Mean device ms per step of each kernel class and of a whole step."""
+    out = (ctypes.c_float * PROF_SLOTS)()
+    _check(lib().chemo_profile_steps(_h(sim), int(nsteps), out, _stream(stream)), "chemo_profile_steps")
+    return {PROF_NAMES[i]: float(out[i]) for i in range(PROF_SLOTS)}
 
 
 def chemo_destroy(sim: Sim):

@@ -206,6 +206,13 @@ void fill_model(const chemo_params &p, KP &kp)
         kp.rkc[s] = in ? p.react_kc[s] : 0.f;
         kp.rto[s] = in ? p.react_to[s] : s;
     }
+    // fixed-point quantum of the pair-force sum: 2^-40 of the largest pair
+    // force magnitude inter/eps (terms never exceed it)
+    double fmax = 0.0;
+    for (int i = 0; i < MAXS * MAXS; ++i) fmax = std::max(fmax, (double)std::fabs(kp.amp_f[i]));
+    if (!(fmax > 0.0)) fmax = 1.0;
+    kp.fq = (float)std::ldexp(fmax, -40);
+    kp.fq_inv = (float)(1.0 / (double)kp.fq);
     kp.reactions = p.reactions ? 1 : 0;
     kp.dt = (float)p.dt;
     kp.dt_d = p.dt;
@@ -419,16 +426,8 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
     const int d = s->kp.dim;
     if (n == 0) return sort_from_u(s, st);
     if (!pos || !sp) return fail(CHEMO_EINVAL, "pos and species are required");
-    if (mem_kind == CHEMO_MEM_HOST) {
-        for (int64_t i = 0; i < n; ++i) {
-            if (sp[i] >= s->prm.n_species) return fail(CHEMO_EINVAL, "species[%lld] = %d >= n_species", (long long)i, sp[i]);
-            for (int a = 0; a < d; ++a) {
-                const float v = pos[i * d + a];
-                if (!std::isfinite(v) || v < s->kp.lo[a] || v > s->kp.hi[a])
-                    return fail(CHEMO_EINVAL, "pos[%lld][%d] = %g is outside the box", (long long)i, a, (double)v);
-            }
-        }
-    }
+    // positions and species are validated by the pack kernel on the device;
+    // bad entries are clamped and latched (reported by chemo_check)
     const size_t pbytes = (size_t)n * d * sizeof(float);
     const size_t sbytes = ((size_t)n + 255) & ~(size_t)255;
     if (mem_kind == CHEMO_MEM_HOST) {
@@ -755,6 +754,74 @@ int chemo_get_info(const chemo_sim *s, chemo_info *info)
     info->device_bytes = s->bytes;
     info->launches_per_step = s->launches_per_step;
     return CHEMO_OK;
+}
+
+int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || !kernel_ms || nsteps <= 0) return fail(CHEMO_EINVAL, "bad arguments");
+    cudaStream_t st = (cudaStream_t)stream;
+    const KP &kp = s->kp;
+    const bool grid = kp.has_grid && kp.chem_mode == 0;
+    const bool overlap = grid && kp.fused_deposit;
+    // event pairs per step: particle, pde, scan, scatter, whole step
+    std::vector<cudaEvent_t> ev((size_t)nsteps * 10, nullptr);
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto &x : ev)
+                if (x) cudaEventDestroy(x);
+            return fail(CHEMO_ECUDA, "cudaEventCreate failed");
+        }
+    int r = CHEMO_OK;
+    for (int64_t k = 0; k < nsteps && r == CHEMO_OK; ++k) {
+        cudaEvent_t *e = &ev[(size_t)k * 10];
+        cudaError_t err = cudaEventRecord(e[8], st);
+        if (overlap) {
+            if (err == cudaSuccess) err = cudaEventRecord(s->ev_fork, st);
+            if (err == cudaSuccess) err = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
+            if (err == cudaSuccess) err = cudaEventRecord(e[2], s->aux);
+            if (err == cudaSuccess) err = launch_pde(kp, s->cur, s->aux, nullptr);
+            if (err == cudaSuccess) err = cudaEventRecord(e[3], s->aux);
+            if (err == cudaSuccess) err = cudaEventRecord(s->ev_join, s->aux);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e[0], st);
+        if (err == cudaSuccess) err = launch_step_particles(kp, s->cur, st, nullptr);
+        if (err == cudaSuccess) err = cudaEventRecord(e[1], st);
+        if (overlap && err == cudaSuccess) err = cudaStreamWaitEvent(st, s->ev_join, 0);
+        if (err == cudaSuccess) err = cudaEventRecord(e[4], st);
+        if (err == cudaSuccess) err = launch_scan(kp, st, nullptr);
+        if (err == cudaSuccess) err = cudaEventRecord(e[5], st);
+        if (err == cudaSuccess) err = launch_scatter(kp, s->cur, 1, st, nullptr);
+        if (err == cudaSuccess) err = cudaEventRecord(e[6], st);
+        if (grid && !overlap) {
+            if (err == cudaSuccess) err = cudaEventRecord(e[2], st);
+            if (err == cudaSuccess) err = launch_pde(kp, s->cur, st, nullptr);
+            if (err == cudaSuccess) err = cudaEventRecord(e[3], st);
+        }
+        if (err == cudaSuccess) err = cudaEventRecord(e[9], st);
+        if (err != cudaSuccess) r = fail(CHEMO_ECUDA, "profile: %s", cudaGetErrorString(err));
+        if (grid) s->cur = overlap ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+        s->step += 1;
+    }
+    if (r == CHEMO_OK) {
+        cudaError_t err = cudaStreamSynchronize(st);
+        if (err != cudaSuccess) r = fail(CHEMO_ECUDA, "profile sync: %s", cudaGetErrorString(err));
+    }
+    if (r == CHEMO_OK) {
+        double acc[CHEMO_PROF_SLOTS] = {0, 0, 0, 0, 0};
+        const int pairs[CHEMO_PROF_SLOTS][2] = {{0, 1}, {2, 3}, {4, 5}, {5, 6}, {8, 9}};
+        for (int64_t k = 0; k < nsteps; ++k) {
+            cudaEvent_t *e = &ev[(size_t)k * 10];
+            for (int q = 0; q < CHEMO_PROF_SLOTS; ++q) {
+                if (q == 1 && !grid) continue;
+                float ms = 0.f;
+                if (cudaEventElapsedTime(&ms, e[pairs[q][0]], e[pairs[q][1]]) == cudaSuccess) acc[q] += ms;
+            }
+        }
+        for (int q = 0; q < CHEMO_PROF_SLOTS; ++q) kernel_ms[q] = (float)(acc[q] / (double)nsteps);
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    return r;
 }
 
 int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, int mem_kind, void *stream)

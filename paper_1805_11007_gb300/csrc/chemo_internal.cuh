@@ -43,6 +43,7 @@ struct KP {
     float inv_eps[MAXS * MAXS];  // 1/eps_st
     float amp_f[MAXS * MAXS];    // inter/eps_st
     float shift[MAXS * MAXS];    // exp(-cutoff_factor) when force shifted, else 0
+    float fq, fq_inv;            // fixed-point quantum of the force sum and its inverse
     float noise[MAXS];           // sqrt(2 D_s dt)
     float chem[MAXS];            // chi * chemotactic_s
     float src[MAXS];             // k_s dt / h^d

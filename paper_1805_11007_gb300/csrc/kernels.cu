@@ -44,11 +44,19 @@ __device__ __forceinline__ void load_tables(const KP &kp, SmemTables &t)
 // ---------------------------------------------------------------------------
 // Pair force (Sect. 3.2): F_i = sum_{j != i, 0 < r < r_c,ij}
 //   (inter/eps_ij) (exp(-r/eps_ij) - shift) (X_i - X_j)/r
-// over the particles of a contiguous range of the sorted array.
+// over the particles of a contiguous range of the sorted array. Each pair
+// term is rounded once to a 64-bit fixed-point value (quantum
+// max(inter/eps) 2^-40, far below FP32 resolution) and summed exactly, so the
+// force does not depend on the order of the particles inside a bin (which
+// the atomic slots of the counting sort leave unspecified).
 // ---------------------------------------------------------------------------
+struct FAcc {
+    long long x, y, z;
+};
+
 template <int DIM, bool PERIODIC, bool STATS>
 __device__ __forceinline__ void accum_range(const KP &kp, const SmemTables &t, uint32_t q0, uint32_t q1,
-                                            uint32_t self, float4 me, int sp, float3 &F, int &count,
+                                            uint32_t self, float4 me, int sp, FAcc &F, int &count,
                                             unsigned long long &idsum)
 {
     const float4 *__restrict__ S = kp.S;
@@ -75,10 +83,10 @@ __device__ __forceinline__ void accum_range(const KP &kp, const SmemTables &t, u
             const float rinv = rsqrtf(r2);
             const float r = r2 * rinv;
             const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
-            const float s = f * rinv;
-            F.x = fmaf(s, dx, F.x);
-            F.y = fmaf(s, dy, F.y);
-            if (DIM == 3) F.z = fmaf(s, dz, F.z);
+            const float sq = (f * rinv) * kp.fq_inv;
+            F.x += __float2ll_rn(sq * dx);
+            F.y += __float2ll_rn(sq * dy);
+            if (DIM == 3) F.z += __float2ll_rn(sq * dz);
             if (STATS) {
                 count += 1;
                 idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
@@ -94,7 +102,7 @@ template <int DIM, bool PERIODIC, bool STATS>
 __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, uint32_t self, float4 me,
                                              int sp, int &count, unsigned long long &idsum)
 {
-    float3 F = make_float3(0.f, 0.f, 0.f);
+    FAcc F = {0ll, 0ll, 0ll};
     int c[3], lo[3], hi[3];
     const float pc[3] = {me.x, me.y, me.z};
 #pragma unroll
@@ -160,7 +168,8 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
             }
         }
     }
-    return F;
+    return make_float3(__ll2float_rn(F.x) * kp.fq, __ll2float_rn(F.y) * kp.fq,
+                       DIM == 3 ? __ll2float_rn(F.z) * kp.fq : 0.f);
 }
 
 // ---------------------------------------------------------------------------

@@ -103,7 +103,7 @@ def test_pair_forces_match_oracle(name, over, n):
     with make_sim(p, pos, sp) as sim:
         F, cnt, ids = gpu_forces(sim)
     ex = assert_forces_match(p, F, cnt, ids, pos, sp)
-    assert ex["count"].mean() > 1.0  # real neighbourhoods
+    assert ex["count"].sum() > 0.3 * n  # real neighbourhoods
 
 
 def test_dense_cluster_single_bin():
