@@ -8,7 +8,7 @@
  * regular grid. One step (chemo_step) advances both by dt:
  *
  *   a1  bin each cell into a cell list (Sect. 2.2, 3.1: neighbourhood search)
- *   a2  counting-sort the cells by bin (Z-order) and build the bin offsets
+ *   a2  counting-sort the cells by bin (row-major) and build the bin offsets
  *   a3  sum the finite-range soft repulsion over neighbouring bins
  *       (Sect. 3.2 interaction loop; pair term of Eq. (1a)/(1b))
  *   a4  interpolate the central-difference gradient of c^n to each cell
@@ -102,7 +102,10 @@ typedef struct chemo_params {
     float bin_side;              /* cell-list bin side (0 = automatic) */
     int32_t search_mode;         /* 0 automatic, 1 3^d bins of side >= r_c,
                                     2 2^d bins of side >= 2 r_c */
-    int32_t bin_order;           /* 0 automatic, 1 row-major (x fastest), 2 Z-order */
+    int32_t bin_order;           /* 0 or 1: row-major bins, x fastest (2, Z-order: ENOTSUP) */
+    int32_t pde_overlap;         /* 0 automatic, 1 run the PDE after the particle kernels,
+                                    2 run it concurrently with the particle kernel (one
+                                    substep only) */
 } chemo_params;
 
 /* Layout facts of a simulation (read-only). */
@@ -111,9 +114,10 @@ typedef struct chemo_info {
     int32_t dim;
     int32_t search_mode;         /* 1 or 2, as resolved */
     int32_t nbins[3];            /* bins per axis */
-    int64_t bin_slots;           /* entries of the bin table (Morton padded) */
+    int64_t bin_slots;           /* entries of the bin table: pitch * nbins[1] * nbins[2] */
     float bin_side[3];
-    int32_t morton;              /* 1 if bins are stored in Z-order */
+    int32_t bin_pitch;           /* bins per stored row (nbins[0] rounded up to 8); bin
+                                    (x, y, z) has key x + pitch (y + nbins[1] z) */
     int32_t pde_substeps;        /* as resolved */
     int64_t grid_nodes;
     int64_t device_bytes;        /* device memory held by the simulation */

@@ -64,6 +64,7 @@ class chemo_params(ctypes.Structure):
         ("bin_side", ctypes.c_float),
         ("search_mode", ctypes.c_int32),
         ("bin_order", ctypes.c_int32),
+        ("pde_overlap", ctypes.c_int32),
     ]
 
 
@@ -75,7 +76,7 @@ class chemo_info(ctypes.Structure):
         ("nbins", ctypes.c_int32 * 3),
         ("bin_slots", ctypes.c_int64),
         ("bin_side", ctypes.c_float * 3),
-        ("morton", ctypes.c_int32),
+        ("bin_pitch", ctypes.c_int32),
         ("pde_substeps", ctypes.c_int32),
         ("grid_nodes", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
@@ -125,6 +126,7 @@ def make_params(d: dict) -> chemo_params:
     p.bin_side = float(d.get("bin_side", 0.0))
     p.search_mode = int(d.get("search_mode", 0))
     p.bin_order = int(d.get("bin_order", 0))
+    p.pde_overlap = int(d.get("pde_overlap", 0))
     return p
 
 

@@ -46,13 +46,15 @@ __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v;
 struct chemo_sim {
     chemo_params prm{};
     KP kp{};
+    uint32_t *cnt8[2] = {nullptr, nullptr};  // packed bin counts, double buffered
+    int cntp = 0;                // cnt8[cntp] describes the sorted state
     int cur = 0;                 // c[cur] holds c^n
     int64_t step = 0;            // host mirror of the next step index
     int launches_per_step = 0;
     cudaStream_t aux = nullptr;  // second stream for the PDE
     cudaStream_t cap = nullptr;  // capture stream for graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // 2-step and 16-step replays
+    cudaGraphExec_t graph[2][2][2] = {};  // [2-step, 16-step][grid parity][count parity]
     std::vector<void *> allocs;
     int64_t bytes = 0;
     void *scratch = nullptr;     // staging for host transfers and stage outputs
@@ -149,6 +151,7 @@ int check_params(const chemo_params &p)
     if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
     if (p.search_mode < 0 || p.search_mode > 2) return fail(CHEMO_EINVAL, "search_mode must be 0, 1 or 2");
     if (p.bin_order < 0 || p.bin_order > 2) return fail(CHEMO_EINVAL, "bin_order must be 0, 1 or 2");
+    if (p.pde_overlap < 0 || p.pde_overlap > 2) return fail(CHEMO_EINVAL, "pde_overlap must be 0, 1 or 2");
     if (p.chem_mode == 0) {
         if (p.pde_bc < 0 || p.pde_bc > 2) return fail(CHEMO_EINVAL, "pde_bc must be 0, 1 or 2");
         if ((p.pde_bc == 2) != (p.boundary == 1))
@@ -206,6 +209,16 @@ void fill_model(const chemo_params &p, KP &kp)
         kp.rkc[s] = in ? p.react_kc[s] : 0.f;
         kp.rto[s] = in ? p.react_to[s] : s;
     }
+    // search radius per species: its largest cutoff against any species, with
+    // a 1e-3 relative margin over FP32 rounding of the bin-relative position
+    for (int s = 0; s < MAXS; ++s) {
+        double m = 0.0;
+        if (s < p.n_species)
+            for (int t = 0; t < p.n_species; ++t)
+                m = std::max(m, (double)p.cutoff_factor * 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]));
+        const double r = m * (1.0 + 1e-3);
+        kp.rsp2[s] = (float)(r * r);
+    }
     // fixed-point quantum of the pair-force sum: 2^-40 of the largest pair
     // force magnitude inter/eps (terms never exceed it)
     double fmax = 0.0;
@@ -237,6 +250,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         kp.halfL[a] = 0.5f * kp.L[a];
         kp.nb[a] = 1;
         kp.inv_b[a] = 0.f;
+        kp.bside[a] = 0.f;
     }
     const double rc = max_cutoff(p);
     const bool pairs = rc > 0.0 && p.inter != 0.f;
@@ -259,7 +273,6 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
                                 : std::pow(vol * (double)(1 << p.dim) / (double)std::max<int64_t>(n, 1), 1.0 / p.dim);
     }
     int64_t total = 1;
-    int maxnb = 1;
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
         double m = std::floor(L / bmin);
@@ -268,8 +281,8 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         if (m > 65535.0) return fail(CHEMO_EINVAL, "axis %d needs %g bins: cutoff too small for the box", a, m);
         kp.nb[a] = (int)m;
         kp.inv_b[a] = (float)((double)kp.nb[a] / L);
+        kp.bside[a] = (float)(L / kp.nb[a]);
         total *= kp.nb[a];
-        maxnb = std::max(maxnb, kp.nb[a]);
     }
     if (pairs && kp.periodic) {
         for (int a = 0; a < p.dim; ++a) {
@@ -280,19 +293,14 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
                 return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= 2 r_c; need >= 2", a, kp.nb[a]);
         }
     }
-    if (total > (int64_t)1 << 31) return fail(CHEMO_EINVAL, "cell list would need %lld bins", (long long)total);
-    int bits = 0;
-    while ((1 << bits) < maxnb) ++bits;
-    const int64_t mslots = (int64_t)1 << (bits * p.dim);
-    bool morton;
-    if (p.bin_order == 1) morton = false;
-    else if (p.bin_order == 2) morton = true;
-    else morton = mslots <= 2 * total;
-    if (morton && ((p.dim == 3 && bits > 10) || (p.dim == 2 && bits > 15) || mslots > ((int64_t)1 << 31)))
-        return fail(CHEMO_EINVAL, "Z-order bin table too large (%d bits per axis)", bits);
-    kp.morton = morton ? 1 : 0;
-    kp.mbits = bits;
-    kp.bin_slots = morton ? mslots : total;
+    if (p.bin_order == 2) return fail(CHEMO_ENOTSUP, "Z-order bin storage is not supported; bins are row-major");
+    // row-major bins, rows padded to a multiple of 8 so that a group of 8
+    // bins never straddles two rows
+    kp.px = (kp.nb[0] + 7) & ~7;
+    const int64_t slots = (int64_t)kp.px * (p.dim >= 2 ? kp.nb[1] : 1) * (p.dim == 3 ? kp.nb[2] : 1);
+    if (slots > ((int64_t)1 << 31)) return fail(CHEMO_EINVAL, "cell list would need %lld bins", (long long)slots);
+    kp.bin_slots = slots;
+    kp.ngroups = slots / 8;
     kp.search = search;
     return CHEMO_OK;
 }
@@ -324,6 +332,7 @@ int fill_grid(const chemo_params &p, KP &kp)
     kp.substeps = resolve_substeps(p);
     kp.dts = (float)(p.dt / kp.substeps);
     kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1) ? 1 : 0;
+    kp.overlap = kp.fused_deposit && p.pde_overlap != 1;
     return CHEMO_OK;
 }
 
@@ -337,20 +346,32 @@ int to_status(uint32_t bits)
     return CHEMO_OK;
 }
 
-// Bins the particles currently in U (with slots already counted) into S.
-int sort_from_u(chemo_sim *s, cudaStream_t st)
+// Kernel parameters with the count buffers of the current parity.
+KP view(const chemo_sim *s)
 {
-    CUDA_TRY(launch_scan(s->kp, st, nullptr));
-    CUDA_TRY(launch_scatter(s->kp, s->cur, 0, st, nullptr));
+    KP k = s->kp;
+    k.cnt_cur = s->cnt8[s->cntp];
+    k.cnt_nxt = s->cnt8[s->cntp ^ 1];
+    return k;
+}
+
+// Bins the particles currently in U (with slots already counted into the
+// next count buffer) into S.
+int sort_from_u(chemo_sim *s, const KP &k, cudaStream_t st)
+{
+    CUDA_TRY(launch_scan(k, st, nullptr));
+    CUDA_TRY(launch_scatter(k, s->cur, 0, st, nullptr));
+    s->cntp ^= 1;
     return CHEMO_OK;
 }
 
 // Enqueues one step on st. Counts launched kernels into *launches.
 int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
 {
-    const KP &kp = s->kp;
+    const KP kp = view(s);
     const bool grid = kp.has_grid && kp.chem_mode == 0;
-    const bool overlap = grid && kp.fused_deposit;
+    const bool overlap = grid && kp.overlap;
+    if (grid && kp.fused_deposit && !overlap) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
     if (overlap) {
         CUDA_TRY(cudaEventRecord(s->ev_fork, st));
         CUDA_TRY(cudaStreamWaitEvent(s->aux, s->ev_fork, 0));
@@ -361,33 +382,37 @@ int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
     if (overlap) CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
     CUDA_TRY(launch_scan(kp, st, launches));
     CUDA_TRY(launch_scatter(kp, s->cur, 1, st, launches));
-    if (grid && !overlap) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
-    if (grid) s->cur = overlap ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+    if (grid && !kp.fused_deposit) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
+    if (grid) s->cur = kp.fused_deposit ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+    s->cntp ^= 1;
     s->step += 1;
     return CHEMO_OK;
 }
 
 void drop_graphs(chemo_sim *s)
 {
-    for (auto &g : s->graph)
-        if (g) {
-            cudaGraphExecDestroy(g);
-            g = nullptr;
-        }
+    for (auto &a : s->graph)
+        for (auto &b : a)
+            for (auto &g : b)
+                if (g) {
+                    cudaGraphExecDestroy(g);
+                    g = nullptr;
+                }
 }
 
-// Captures `k` steps starting from grid parity 0 into an executable graph.
+// Captures `k` steps starting from the current buffer parities into an
+// executable graph (the parities are restored afterwards).
 int capture(chemo_sim *s, int k, cudaGraphExec_t *out)
 {
-    const int cur0 = s->cur;
+    const int cur0 = s->cur, cntp0 = s->cntp;
     const int64_t step0 = s->step;
-    s->cur = 0;
     CUDA_TRY(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     int st = CHEMO_OK;
     for (int i = 0; i < k && st == CHEMO_OK; ++i) st = enqueue_step(s, s->cap, nullptr);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(s->cap, &g);
     s->cur = cur0;
+    s->cntp = cntp0;
     s->step = step0;
     if (st != CHEMO_OK) {
         if (g) cudaGraphDestroy(g);
@@ -424,7 +449,7 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
 {
     const int64_t n = s->kp.n;
     const int d = s->kp.dim;
-    if (n == 0) return sort_from_u(s, st);
+    if (n == 0) return sort_from_u(s, view(s), st);
     if (!pos || !sp) return fail(CHEMO_EINVAL, "pos and species are required");
     // positions and species are validated by the pack kernel on the device;
     // bad entries are clamped and latched (reported by chemo_check)
@@ -444,8 +469,9 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
         r = copy_in(s, disp, pbytes, mem_kind, st, ((pbytes + 255) & ~(size_t)255) + sbytes, &ddisp);
         if (r) return r;
     }
-    CUDA_TRY(launch_pack(s->kp, (const float *)dpos, (const uint8_t *)dsp, (const float *)ddisp, st, nullptr));
-    r = sort_from_u(s, st);
+    const KP k = view(s);
+    CUDA_TRY(launch_pack(k, (const float *)dpos, (const uint8_t *)dsp, (const float *)ddisp, st, nullptr));
+    r = sort_from_u(s, k, st);
     if (r) return r;
     if (mem_kind == CHEMO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
     return CHEMO_OK;
@@ -526,10 +552,13 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
         ALLOC(kp.dS, N * sizeof(float4));
         ALLOC(kp.dU, N * sizeof(float4));
     }
-    const size_t slots = (size_t)kp.bin_slots;
-    ALLOC(kp.cnt, ((slots + 3) & ~(size_t)3) * sizeof(uint32_t));
-    ALLOC(kp.start, ((slots + 1 + 3) & ~(size_t)3) * sizeof(uint32_t));
-    const size_t tiles = (slots + 4095) / 4096;
+    const size_t slots = (size_t)kp.bin_slots;  // a multiple of 8
+    const size_t cwords = slots / 2;  // 16-bit counts
+    ALLOC(s->cnt8[0], cwords * sizeof(uint32_t));
+    ALLOC(s->cnt8[1], cwords * sizeof(uint32_t));
+    ALLOC(kp.gstart, (((size_t)kp.ngroups + 1 + 3) & ~(size_t)3) * sizeof(uint32_t));
+    kp.cnt_cur = kp.cnt_nxt = nullptr;
+    const size_t tiles = ((size_t)kp.ngroups + 2047) / 2048;
     ALLOC(kp.tiles, tiles * sizeof(unsigned long long));
     uint32_t *ctl;
     ALLOC(ctl, 64);
@@ -549,7 +578,8 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     }
 #undef ALLOC
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMemsetAsync(kp.cnt, 0, ((slots + 3) & ~(size_t)3) * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->cnt8[0], 0, cwords * sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->cnt8[1], 0, cwords * sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(kp.tiles, 0, tiles * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 64, st);
     if (e == cudaSuccess && kp.has_grid) {
@@ -613,18 +643,29 @@ int chemo_step_n(chemo_sim *s, int64_t nsteps, void *stream)
     if (nsteps < 0) return fail(CHEMO_EINVAL, "nsteps < 0");
     cudaStream_t st = (cudaStream_t)stream;
     int64_t left = nsteps;
-    if (left >= 2 && s->cur != 0) {
-        if (int r = enqueue_step(s, st, nullptr)) return r;
-        --left;
-    }
+    // graphs of an even number of steps leave both buffer parities unchanged
     static const int sizes[2] = {2, 16};
     for (int gi = 1; gi >= 0; --gi) {
         const int k = sizes[gi];
         if (left < k) continue;
-        if (!s->graph[gi])
-            if (int r = capture(s, k, &s->graph[gi])) return r;
+        cudaGraphExec_t &g = s->graph[gi][s->cur][s->cntp];
+        if (!g) {
+            // capture this size for every buffer parity at once, so that later
+            // calls (after a chemo_write_state, for instance) never capture
+            const int cur0 = s->cur, cntp0 = s->cntp;
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    if (s->graph[gi][a][b]) continue;
+                    s->cur = a;
+                    s->cntp = b;
+                    const int r = capture(s, k, &s->graph[gi][a][b]);
+                    s->cur = cur0;
+                    s->cntp = cntp0;
+                    if (r) return r;
+                }
+        }
         while (left >= k) {
-            CUDA_TRY(cudaGraphLaunch(s->graph[gi], st));
+            CUDA_TRY(cudaGraphLaunch(g, st));
             s->step += k;
             left -= k;
         }
@@ -647,7 +688,7 @@ int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *
     const size_t pbytes = (size_t)n * s->kp.dim * sizeof(float);
     const size_t pb = (pbytes + 255) & ~(size_t)255;
     if (mem_kind == CHEMO_MEM_DEVICE) {
-        CUDA_TRY(launch_unsort(s->kp, pos_out, species_out, disp_out, st));
+        CUDA_TRY(launch_unsort(view(s), pos_out, species_out, disp_out, st));
     } else {
         void *tmp;
         if (int r = scratch(s, 2 * pb + (size_t)n + 256, &tmp)) return r;
@@ -655,7 +696,7 @@ int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *
         float *dp = pos_out ? (float *)b : nullptr;
         float *dd = disp_out ? (float *)(b + pb) : nullptr;
         uint8_t *ds = species_out ? (uint8_t *)(b + 2 * pb) : nullptr;
-        CUDA_TRY(launch_unsort(s->kp, dp, ds, dd, st));
+        CUDA_TRY(launch_unsort(view(s), dp, ds, dd, st));
         if (pos_out && n) CUDA_TRY(cudaMemcpyAsync(pos_out, dp, pbytes, cudaMemcpyDeviceToHost, st));
         if (disp_out && n) CUDA_TRY(cudaMemcpyAsync(disp_out, dd, pbytes, cudaMemcpyDeviceToHost, st));
         if (species_out && n) CUDA_TRY(cudaMemcpyAsync(species_out, ds, (size_t)n, cudaMemcpyDeviceToHost, st));
@@ -703,8 +744,8 @@ int chemo_set_params(chemo_sim *s, const chemo_params *p)
     int r;
     if ((r = fill_layout(*p, s->kp.n, k2)) || (r = fill_grid(*p, k2))) return r;
     if (k2.nb[0] != s->kp.nb[0] || k2.nb[1] != s->kp.nb[1] || k2.nb[2] != s->kp.nb[2] ||
-        k2.search != s->kp.search || k2.morton != s->kp.morton || k2.substeps != s->kp.substeps ||
-        k2.fused_deposit != s->kp.fused_deposit)
+        k2.search != s->kp.search || k2.px != s->kp.px || k2.substeps != s->kp.substeps ||
+        k2.fused_deposit != s->kp.fused_deposit || k2.overlap != s->kp.overlap)
         return fail(CHEMO_EINVAL, "new parameters change the cell-list layout or the PDE substeps");
     fill_model(*p, s->kp);
     s->prm = *p;
@@ -748,7 +789,7 @@ int chemo_get_info(const chemo_sim *s, chemo_info *info)
         info->bin_side[a] = a < kp.dim ? kp.L[a] / kp.nb[a] : 0.f;
     }
     info->bin_slots = kp.bin_slots;
-    info->morton = kp.morton;
+    info->bin_pitch = kp.px;
     info->pde_substeps = kp.has_grid ? kp.substeps : 0;
     info->grid_nodes = kp.G;
     info->device_bytes = s->bytes;
@@ -761,9 +802,9 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     g_last_error[0] = 0;
     if (!s || !kernel_ms || nsteps <= 0) return fail(CHEMO_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    const KP &kp = s->kp;
-    const bool grid = kp.has_grid && kp.chem_mode == 0;
-    const bool overlap = grid && kp.fused_deposit;
+    const bool grid = s->kp.has_grid && s->kp.chem_mode == 0;
+    const bool overlap = grid && s->kp.overlap;
+    const bool fused = grid && s->kp.fused_deposit;
     // event pairs per step: particle, pde, scan, scatter, whole step
     std::vector<cudaEvent_t> ev((size_t)nsteps * 10, nullptr);
     for (auto &e : ev)
@@ -774,8 +815,14 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         }
     int r = CHEMO_OK;
     for (int64_t k = 0; k < nsteps && r == CHEMO_OK; ++k) {
+        const KP kp = view(s);
         cudaEvent_t *e = &ev[(size_t)k * 10];
         cudaError_t err = cudaEventRecord(e[8], st);
+        if (fused && !overlap) {
+            if (err == cudaSuccess) err = cudaEventRecord(e[2], st);
+            if (err == cudaSuccess) err = launch_pde(kp, s->cur, st, nullptr);
+            if (err == cudaSuccess) err = cudaEventRecord(e[3], st);
+        }
         if (overlap) {
             if (err == cudaSuccess) err = cudaEventRecord(s->ev_fork, st);
             if (err == cudaSuccess) err = cudaStreamWaitEvent(s->aux, s->ev_fork, 0);
@@ -793,14 +840,15 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         if (err == cudaSuccess) err = cudaEventRecord(e[5], st);
         if (err == cudaSuccess) err = launch_scatter(kp, s->cur, 1, st, nullptr);
         if (err == cudaSuccess) err = cudaEventRecord(e[6], st);
-        if (grid && !overlap) {
+        if (grid && !fused) {
             if (err == cudaSuccess) err = cudaEventRecord(e[2], st);
             if (err == cudaSuccess) err = launch_pde(kp, s->cur, st, nullptr);
             if (err == cudaSuccess) err = cudaEventRecord(e[3], st);
         }
         if (err == cudaSuccess) err = cudaEventRecord(e[9], st);
         if (err != cudaSuccess) r = fail(CHEMO_ECUDA, "profile: %s", cudaGetErrorString(err));
-        if (grid) s->cur = overlap ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+        if (grid) s->cur = fused ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+        s->cntp ^= 1;
         s->step += 1;
     }
     if (r == CHEMO_OK) {
@@ -875,7 +923,7 @@ int chemo_stage_bins(chemo_sim *s, int32_t *cells_out, int mem_kind, void *strea
     const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(int32_t);
     void *tmp;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
-    CUDA_TRY(launch_stage_bins(s->kp, (int32_t *)tmp, st));
+    CUDA_TRY(launch_stage_bins(view(s), (int32_t *)tmp, st));
     if (int r = stage_out(s, cells_out, tmp, bytes, mem_kind, st)) return r;
     return finish(s, mem_kind, stream);
 }
@@ -890,12 +938,17 @@ int chemo_stage_sort(chemo_sim *s, uint32_t *ids_out, uint32_t *bin_start_out, i
     void *tmp;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
     if (ids_out) {
-        CUDA_TRY(launch_stage_sort(s->kp, (uint32_t *)tmp, st));
+        CUDA_TRY(launch_stage_sort(view(s), (uint32_t *)tmp, nullptr, st));
         if (int r = stage_out(s, ids_out, tmp, bytes, mem_kind, st)) return r;
     }
-    if (bin_start_out)
-        if (int r = stage_out(s, bin_start_out, s->kp.start, ((size_t)s->kp.bin_slots + 1) * sizeof(uint32_t), mem_kind, st))
-            return r;
+    if (bin_start_out) {
+        const size_t sb = ((size_t)s->kp.bin_slots + 1) * sizeof(uint32_t);
+        void *t2;
+        if (mem_kind == CHEMO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));  // ids copied out before reuse
+        if (int r = scratch(s, sb + 256, &t2)) return r;
+        CUDA_TRY(launch_stage_sort(view(s), nullptr, (uint32_t *)t2, st));
+        if (int r = stage_out(s, bin_start_out, t2, sb, mem_kind, st)) return r;
+    }
     return finish(s, mem_kind, stream);
 }
 
@@ -912,7 +965,7 @@ int chemo_stage_forces(chemo_sim *s, float *F_out, int32_t *count_out, uint64_t 
     void *tmp;
     if (int r = scratch(s, fb + cb + ib + 256, &tmp)) return r;
     char *b = (char *)tmp;
-    CUDA_TRY(launch_stage_forces(s->kp, (float *)b, (int32_t *)(b + fb), (unsigned long long *)(b + fb + cb), st));
+    CUDA_TRY(launch_stage_forces(view(s), (float *)b, (int32_t *)(b + fb), (unsigned long long *)(b + fb + cb), st));
     if (int r = stage_out(s, F_out, b, (size_t)n * s->kp.dim * sizeof(float), mem_kind, st)) return r;
     if (int r = stage_out(s, count_out, b + fb, (size_t)n * sizeof(int32_t), mem_kind, st)) return r;
     if (int r = stage_out(s, idsum_out, b + fb + cb, ib, mem_kind, st)) return r;
@@ -928,7 +981,7 @@ int chemo_stage_drift(chemo_sim *s, float *drift_out, int mem_kind, void *stream
     const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(float);
     void *tmp;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
-    CUDA_TRY(launch_stage_drift(s->kp, s->cur, (float *)tmp, st));
+    CUDA_TRY(launch_stage_drift(view(s), s->cur, (float *)tmp, st));
     if (int r = stage_out(s, drift_out, tmp, bytes, mem_kind, st)) return r;
     return finish(s, mem_kind, stream);
 }
@@ -945,7 +998,7 @@ int chemo_stage_deposit(chemo_sim *s, float *S_out, float *R_out, int mem_kind, 
     if (int r = scratch(s, 2 * gb, &tmp)) return r;
     float *dS = (float *)tmp, *dR = (float *)((char *)tmp + gb);
     CUDA_TRY(cudaMemsetAsync(tmp, 0, 2 * gb, st));
-    CUDA_TRY(launch_stage_deposit(s->kp, dS, dR, st));
+    CUDA_TRY(launch_stage_deposit(view(s), dS, dR, st));
     if (int r = stage_out(s, S_out, dS, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
     if (int r = stage_out(s, R_out, dR, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
     return finish(s, mem_kind, stream);

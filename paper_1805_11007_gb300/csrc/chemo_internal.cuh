@@ -30,13 +30,14 @@ constexpr uint32_t TAG_REACT = 2u;
 struct KP {
     // particles and cell list
     int64_t n;
-    int dim, periodic, morton, search;  // search 1: 3^d bins >= r_c, 2: 2^d bins >= 2 r_c
-    int pairs;                          // 0: no pair interaction (inter = 0 or zero range)
+    int dim, periodic, search;  // search 1: 3^d bins >= r_c, 2: 2^d bins >= 2 r_c
+    int pairs;                  // 0: no pair interaction (inter = 0 or zero range)
     float lo[3], hi[3], L[3], halfL[3];
-    int nb[3];
-    float inv_b[3];
-    int mbits;                          // Morton bits per axis
-    int64_t bin_slots;
+    int nb[3];                  // bins per axis
+    float inv_b[3], bside[3];   // nb/L and L/nb per axis
+    int px;                     // row pitch of the bin table (nb[0] rounded up to 8)
+    int64_t bin_slots;          // px * nb[1] * nb[2]; bins are row-major, x fastest
+    int64_t ngroups;            // bin_slots / 8: groups of 8 bins of one row
     // species tables (index s * MAXS + t)
     int ns;
     float rc2[MAXS * MAXS];      // r_c,st^2
@@ -44,6 +45,7 @@ struct KP {
     float amp_f[MAXS * MAXS];    // inter/eps_st
     float shift[MAXS * MAXS];    // exp(-cutoff_factor) when force shifted, else 0
     float fq, fq_inv;            // fixed-point quantum of the force sum and its inverse
+    float rsp2[MAXS];            // squared search radius of each species (max cutoff, small margin)
     float noise[MAXS];           // sqrt(2 D_s dt)
     float chem[MAXS];            // chi * chemotactic_s
     float src[MAXS];             // k_s dt / h^d
@@ -66,11 +68,16 @@ struct KP {
     int substeps;
     float dts;
     int fused_deposit;           // 1: deposit straight into c^{n+1} (one substep)
+    int overlap;                 // 1: PDE concurrent with the particle kernel (second stream)
     // buffers
     float4 *S, *U;               // sorted state, unsorted next state
     uint32_t *slot;              // rank of each U entry inside its bin
     float4 *dS, *dU;             // unwrapped displacement (optional)
-    uint32_t *cnt, *start;       // bin counts, bin offsets (bin_slots + 1)
+    // Cell list, two levels: packed 16-bit counts per bin (2 per word) and the
+    // offset of every group of 8 bins. cnt_cur describes the sorted state S;
+    // cnt_nxt collects the bins of the state being written to U.
+    uint32_t *cnt_cur, *cnt_nxt;
+    uint32_t *gstart;            // group offsets (ngroups + 1) of the state last scanned
     unsigned long long *tiles;   // scan tile status
     uint32_t *tile_ctr;          // dynamic tile counter of the scan
     uint32_t *scan_seq;          // scan epoch counter
@@ -134,33 +141,39 @@ __device__ __forceinline__ int bin_axis(float x, float lo, float inv_b, int nb)
     return c > nb - 1 ? nb - 1 : c;
 }
 
-__device__ __forceinline__ uint32_t spread2(uint32_t v)  // 16 bits -> even bits
-{
-    v &= 0xFFFFu;
-    v = (v | (v << 8)) & 0x00FF00FFu;
-    v = (v | (v << 4)) & 0x0F0F0F0Fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
-}
-
-__device__ __forceinline__ uint32_t spread3(uint32_t v)  // 10 bits -> every third bit
-{
-    v &= 0x3FFu;
-    v = (v | (v << 16)) & 0x030000FFu;
-    v = (v | (v << 8)) & 0x0300F00Fu;
-    v = (v | (v << 4)) & 0x030C30C3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
 __device__ __forceinline__ uint32_t bin_key(const KP &kp, int cx, int cy, int cz)
 {
-    if (kp.morton) {
-        if (kp.dim == 2) return spread2((uint32_t)cx) | (spread2((uint32_t)cy) << 1);
-        return spread3((uint32_t)cx) | (spread3((uint32_t)cy) << 1) | (spread3((uint32_t)cz) << 2);
+    return (uint32_t)cx + (uint32_t)kp.px * ((uint32_t)cy + (uint32_t)kp.nb[1] * (uint32_t)cz);
+}
+
+// Offset of bin k in the sorted arrays: its group's offset plus the counts of
+// the bins before it in the group (16-bit counts, 2 per word, 8 per group).
+__device__ __forceinline__ uint32_t bin_start(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ gstart,
+                                              uint32_t k)
+{
+    const uint32_t g = k >> 3, r = k & 7u;
+    uint32_t s = __ldg(&gstart[g]);
+    if (r) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(cnt) + g);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (uint32_t i = 0; i < 4; ++i) {
+            if (2 * i < r) s += ws[i] & 0xFFFFu;
+            if (2 * i + 1 < r) s += ws[i] >> 16;
+        }
     }
-    return (uint32_t)cx + (uint32_t)kp.nb[0] * ((uint32_t)cy + (uint32_t)kp.nb[1] * (uint32_t)cz);
+    return s;
+}
+
+// Counts particle key k into the packed counts; returns its slot in the bin
+// (the count before it). A bin holds at most 65535 particles.
+__device__ __forceinline__ uint32_t count_bin(uint32_t *cnt, uint32_t k, uint32_t *err)
+{
+    const uint32_t sh = (k & 1u) * 16u;
+    const uint32_t old = atomicAdd(&cnt[k >> 1], 1u << sh);
+    const uint32_t slot = (old >> sh) & 0xFFFFu;
+    if (slot == 0xFFFFu) atomicOr(err, 4u /* ERR_OVERFLOW */);
+    return slot;
 }
 
 __device__ __forceinline__ void cell_of(const KP &kp, float4 p, int &cx, int &cy, int &cz)
@@ -251,7 +264,7 @@ cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches);
 cudaError_t launch_unsort(const KP &kp, float *pos, uint8_t *sp, float *disp, cudaStream_t st);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, cudaStream_t st);
 cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st);
-cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, cudaStream_t st);
+cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, uint32_t *bin_starts, cudaStream_t st);
 cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned long long *idsum,
                                 cudaStream_t st);
 cudaError_t launch_stage_drift(const KP &kp, int cur, float *drift, cudaStream_t st);

@@ -14,6 +14,8 @@
 //              look-back with bounded waits); clears the counts.
 //   k_scatter  stable placement of the moved cells by bin (counting sort) and
 //              the cloud-in-cell deposit of their secretion (Sect. 2.3).
+#include <cmath>
+
 #include "chemo_internal.cuh"
 
 namespace chemo {
@@ -43,9 +45,8 @@ __device__ __forceinline__ void load_tables(const KP &kp, SmemTables &t)
 
 // ---------------------------------------------------------------------------
 // Pair force (Sect. 3.2): F_i = sum_{j != i, 0 < r < r_c,ij}
-//   (inter/eps_ij) (exp(-r/eps_ij) - shift) (X_i - X_j)/r
-// over the particles of a contiguous range of the sorted array. Each pair
-// term is rounded once to a 64-bit fixed-point value (quantum
+//   (inter/eps_ij) (exp(-r/eps_ij) - shift) (X_i - X_j)/r.
+// Each pair term is rounded once to a 64-bit fixed-point value (quantum
 // max(inter/eps) 2^-40, far below FP32 resolution) and summed exactly, so the
 // force does not depend on the order of the particles inside a bin (which
 // the atomic slots of the counting sort leave unspecified).
@@ -54,75 +55,88 @@ struct FAcc {
     long long x, y, z;
 };
 
-template <int DIM, bool PERIODIC, bool STATS>
-__device__ __forceinline__ void accum_range(const KP &kp, const SmemTables &t, uint32_t q0, uint32_t q1,
-                                            uint32_t self, float4 me, int sp, FAcc &F, int &count,
-                                            unsigned long long &idsum)
+// ---------------------------------------------------------------------------
+// Search window. Bins are stored row-major (x fastest), so the bins of one
+// x-row of the window are one contiguous range of the sorted array: the
+// window is at most 3^(d-1) ranges (twice that when a periodic row wraps).
+// Rows (and the end bins of a row) that lie farther from the particle than
+// its species' largest cutoff are skipped. Each thread stages its ranges in
+// shared memory and walks all of them in one flattened loop (the warp waits
+// for its longest candidate list only, not for the longest bin of every
+// row). Candidates inside the cutoff are listed in shared memory and their
+// forces evaluated in a second, mostly converged loop.
+// ---------------------------------------------------------------------------
+constexpr int LIST_CAP = 16;
+
+template <int DIM, bool PERIODIC>
+struct RowCap {
+    static constexpr int value = (DIM == 3 ? 9 : 3) * (PERIODIC ? 2 : 1);
+};
+
+template <int DIM, bool PERIODIC>
+__device__ __forceinline__ void pair_delta(const KP &kp, float4 me, float4 o, float &dx, float &dy, float &dz, float &r2)
 {
-    const float4 *__restrict__ S = kp.S;
-    const int row = sp * MAXS;
-    q1 = min(q1, (uint32_t)kp.n);  // bin offsets are trusted only up to n
-    for (uint32_t q = q0; q < q1; ++q) {
-        const float4 o = __ldg(&S[q]);
-        float dx = me.x - o.x, dy = me.y - o.y, dz = DIM == 3 ? me.z - o.z : 0.f;
-        if (PERIODIC) {
-            // minimum image; the shifted coordinate is subtracted first so
-            // the difference of two nearby points is formed exactly
-            if (dx > kp.halfL[0]) dx = (me.x - kp.L[0]) - o.x;
-            else if (dx < -kp.halfL[0]) dx = me.x - (o.x - kp.L[0]);
-            if (dy > kp.halfL[1]) dy = (me.y - kp.L[1]) - o.y;
-            else if (dy < -kp.halfL[1]) dy = me.y - (o.y - kp.L[1]);
-            if (DIM == 3) {
-                if (dz > kp.halfL[2]) dz = (me.z - kp.L[2]) - o.z;
-                else if (dz < -kp.halfL[2]) dz = me.z - (o.z - kp.L[2]);
-            }
-        }
-        const float r2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
-        const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
-        if (r2 < t.rc2[st] && r2 > 0.f && q != self) {
-            const float rinv = rsqrtf(r2);
-            const float r = r2 * rinv;
-            const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
-            const float sq = (f * rinv) * kp.fq_inv;
-            F.x += __float2ll_rn(sq * dx);
-            F.y += __float2ll_rn(sq * dy);
-            if (DIM == 3) F.z += __float2ll_rn(sq * dz);
-            if (STATS) {
-                count += 1;
-                idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
-            }
+    dx = me.x - o.x;
+    dy = me.y - o.y;
+    dz = DIM == 3 ? me.z - o.z : 0.f;
+    if (PERIODIC) {
+        // minimum image; the shifted coordinate is subtracted first so the
+        // difference of two nearby points is formed exactly
+        if (dx > kp.halfL[0]) dx = (me.x - kp.L[0]) - o.x;
+        else if (dx < -kp.halfL[0]) dx = me.x - (o.x - kp.L[0]);
+        if (dy > kp.halfL[1]) dy = (me.y - kp.L[1]) - o.y;
+        else if (dy < -kp.halfL[1]) dy = me.y - (o.y - kp.L[1]);
+        if (DIM == 3) {
+            if (dz > kp.halfL[2]) dz = (me.z - kp.L[2]) - o.z;
+            else if (dz < -kp.halfL[2]) dz = me.z - (o.z - kp.L[2]);
         }
     }
+    r2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
 }
 
-// Neighbouring bins of a particle: 3^d bins around its own (search 1) or
-// the 2^d bins on the sides it is closest to (search 2). In row-major order
-// the bins of one x-row form one contiguous range of the sorted array.
-template <int DIM, bool PERIODIC, bool STATS>
-__device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, uint32_t self, float4 me,
-                                             int sp, int &count, unsigned long long &idsum)
+template <int DIM>
+__device__ __forceinline__ void pair_term(const KP &kp, const SmemTables &t, int st, float dx, float dy, float dz,
+                                          float r2, FAcc &F)
 {
-    FAcc F = {0ll, 0ll, 0ll};
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
+    const float sq = (f * rinv) * kp.fq_inv;
+    F.x += __float2ll_rn(sq * dx);
+    F.y += __float2ll_rn(sq * dy);
+    if (DIM == 3) F.z += __float2ll_rn(sq * dz);
+}
+
+// Distance (squared) from a particle at offset f in [0,1] (bin units) of its
+// bin to the neighbouring bin at offset o in {-1, 0, +1}, bin side b.
+__device__ __forceinline__ float gap2(int o, float f, float b)
+{
+    const float d = o < 0 ? f * b : (o > 0 ? (1.f - f) * b : 0.f);
+    return d * d;
+}
+
+template <int DIM, bool PERIODIC, bool STATS>
+__device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, uint32_t self, float4 me, int sp,
+                                             int &count, unsigned long long &idsum, unsigned char *smem_extra)
+{
+    uint2 *rng = reinterpret_cast<uint2 *>(smem_extra) + threadIdx.x;
+    uint32_t *lst = reinterpret_cast<uint32_t *>(smem_extra + (size_t)TPB * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) +
+                    threadIdx.x;
     int c[3], lo[3], hi[3];
+    float f[3];
     const float pc[3] = {me.x, me.y, me.z};
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= DIM) {
-            c[a] = 0;
-            lo[a] = 0;
-            hi[a] = 0;
+            c[a] = lo[a] = hi[a] = 0;
+            f[a] = 0.f;
             continue;
         }
         c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+        f[a] = fminf(fmaxf(__fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a], 0.f), 1.f);
         if (kp.search == 2) {
-            const float tt = __fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a];
-            if (tt < 0.5f) {
-                lo[a] = c[a] - 1;
-                hi[a] = c[a];
-            } else {
-                lo[a] = c[a];
-                hi[a] = c[a] + 1;
-            }
+            lo[a] = f[a] < 0.5f ? c[a] - 1 : c[a];
+            hi[a] = lo[a] + 1;
         } else {
             lo[a] = c[a] - 1;
             hi[a] = c[a] + 1;
@@ -132,44 +146,80 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
             hi[a] = min(hi[a], kp.nb[a] - 1);
         }
     }
+    const float rs2 = kp.rsp2[sp];
+    const uint32_t *__restrict__ cnt = kp.cnt_cur;
+    const uint32_t *__restrict__ gst = kp.gstart;
+    const uint32_t n = (uint32_t)kp.n;
+    int nr = 0;
     for (int z = lo[2]; z <= hi[2]; ++z) {
+        const float gz = DIM == 3 ? gap2(z - c[2], f[2], kp.bside[2]) : 0.f;
         int zz = z;
         if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
         for (int y = lo[1]; y <= hi[1]; ++y) {
+            const float gyz = gz + gap2(y - c[1], f[1], kp.bside[1]);
+            if (gyz >= rs2) continue;  // the whole row is out of reach
             int yy = y;
             if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
-            if (!kp.morton) {
-                int x0 = lo[0], x1 = hi[0];
-                if (PERIODIC && x0 < 0) {  // wrapped cell on the left, then the rest
-                    const uint32_t k = bin_key(kp, kp.nb[0] - 1, yy, zz);
-                    accum_range<DIM, PERIODIC, STATS>(kp, t, kp.start[k], kp.start[k + 1], self, me, sp, F,
-                                                      count, idsum);
-                    x0 = 0;
-                }
-                if (PERIODIC && x1 >= kp.nb[0]) {
-                    const uint32_t k = bin_key(kp, 0, yy, zz);
-                    accum_range<DIM, PERIODIC, STATS>(kp, t, kp.start[k], kp.start[k + 1], self, me, sp, F,
-                                                      count, idsum);
-                    x1 = kp.nb[0] - 1;
-                }
-                if (x0 <= x1) {
-                    const uint32_t k0 = bin_key(kp, x0, yy, zz), k1 = bin_key(kp, x1, yy, zz);
-                    accum_range<DIM, PERIODIC, STATS>(kp, t, kp.start[k0], kp.start[k1 + 1], self, me, sp, F,
-                                                      count, idsum);
-                }
-            } else {
-                for (int x = lo[0]; x <= hi[0]; ++x) {
-                    int xx = x;
-                    if (PERIODIC) xx = x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x);
-                    const uint32_t k = bin_key(kp, xx, yy, zz);
-                    accum_range<DIM, PERIODIC, STATS>(kp, t, kp.start[k], kp.start[k + 1], self, me, sp, F,
-                                                      count, idsum);
-                }
+            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+            int x0 = lo[0], x1 = hi[0];
+            if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
+            if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
+            if (PERIODIC && x0 < 0) {
+                const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
+                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
+                x0 = 0;
+            }
+            if (PERIODIC && x1 >= kp.nb[0]) {
+                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
+                x1 = kp.nb[0] - 1;
+            }
+            if (x0 <= x1)
+                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk + x0), bin_start(cnt, gst, rowk + x1 + 1));
+        }
+    }
+    const float4 *__restrict__ S = kp.S;
+    const int row = sp * MAXS;
+    FAcc F = {0ll, 0ll, 0ll};
+    int nl = 0;
+    int r = 0;
+    uint32_t q = 0, qe = 0;
+    for (;;) {
+        while (q >= qe && r < nr) {
+            const uint2 g = rng[r++ * TPB];
+            q = g.x;
+            qe = min(g.y, n);  // offsets are trusted only up to n
+        }
+        if (q >= qe) break;
+        const float4 o = __ldg(&S[q]);
+        float dx, dy, dz, r2;
+        pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+        const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+        if (r2 < t.rc2[st] && r2 > 0.f && q != self) {
+            if (nl < LIST_CAP) lst[nl++ * TPB] = q;
+            else pair_term<DIM>(kp, t, st, dx, dy, dz, r2, F);
+            if (STATS) {
+                count += 1;
+                idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
             }
         }
+        ++q;
+    }
+    for (int i = 0; i < nl; ++i) {
+        const float4 o = __ldg(&S[lst[i * TPB]]);
+        float dx, dy, dz, r2;
+        pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+        pair_term<DIM>(kp, t, row + (int)(__float_as_uint(o.w) >> SP_SHIFT), dx, dy, dz, r2, F);
     }
     return make_float3(__ll2float_rn(F.x) * kp.fq, __ll2float_rn(F.y) * kp.fq,
                        DIM == 3 ? __ll2float_rn(F.z) * kp.fq : 0.f);
+}
+
+// Dynamic shared memory of the kernels that evaluate pair forces.
+template <int DIM, bool PERIODIC>
+constexpr size_t pair_smem()
+{
+    return sizeof(SmemTables) + (size_t)TPB * RowCap<DIM, PERIODIC>::value * sizeof(uint2) +
+           (size_t)TPB * LIST_CAP * sizeof(uint32_t);
 }
 
 // ---------------------------------------------------------------------------
@@ -180,36 +230,46 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
 template <int DIM>
 __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restrict__ c, float4 p, float &cval)
 {
-    int i[2], j[2], k[2] = {0, 0};
+    int i0, i1, j0, j1, k0 = 0, k1 = 0;
     float fx, fy, fz = 0.f;
-    gcell(kp, 0, p.x, i[0], i[1], fx);
-    gcell(kp, 1, p.y, j[0], j[1], fy);
-    if (DIM == 3) gcell(kp, 2, p.z, k[0], k[1], fz);
-    const int im = gnbr(kp, 0, i[0] - 1), ip = gnbr(kp, 0, i[1] + 1);
-    const int jm = gnbr(kp, 1, j[0] - 1), jp = gnbr(kp, 1, j[1] + 1);
+    gcell(kp, 0, p.x, i0, i1, fx);
+    gcell(kp, 1, p.y, j0, j1, fy);
+    if (DIM == 3) gcell(kp, 2, p.z, k0, k1, fz);
+    const int64_t gx = kp.g[0], plane = (int64_t)kp.g[0] * kp.g[1];
+    // base node (i0, j0, k0) and offsets to the other nodes used
+    const int64_t b = (int64_t)i0 + gx * ((int64_t)j0 + (int64_t)kp.g[1] * k0);
+    const int64_t ox[4] = {gnbr(kp, 0, i0 - 1) - i0, 0, i1 - i0, gnbr(kp, 0, i1 + 1) - i0};
+    const int64_t oy[4] = {(gnbr(kp, 1, j0 - 1) - j0) * gx, 0, (j1 - j0) * gx, (gnbr(kp, 1, j1 + 1) - j0) * gx};
+    int64_t oz[4] = {0, 0, 0, 0};
+    if (DIM == 3) {
+        oz[0] = (gnbr(kp, 2, k0 - 1) - k0) * plane;
+        oz[2] = (k1 - k0) * plane;
+        oz[3] = (gnbr(kp, 2, k1 + 1) - k0) * plane;
+    }
     constexpr int NZ = DIM == 3 ? 2 : 1;
     // corners C[bz][by][bx] and the nodes one beyond them along each axis
     float C[NZ][2][2], XM[NZ][2], XP[NZ][2], YM[NZ][2], YP[NZ][2], ZM[2][2], ZP[2][2];
 #pragma unroll
     for (int bz = 0; bz < NZ; ++bz) {
+        const int64_t z = oz[1 + bz];  // plane k0 (offset 0) or k1
 #pragma unroll
-        for (int b = 0; b < 2; ++b) {
-            C[bz][b][0] = __ldg(&c[gidx(kp, i[0], j[b], k[bz])]);
-            C[bz][b][1] = __ldg(&c[gidx(kp, i[1], j[b], k[bz])]);
-            XM[bz][b] = __ldg(&c[gidx(kp, im, j[b], k[bz])]);
-            XP[bz][b] = __ldg(&c[gidx(kp, ip, j[b], k[bz])]);
-            YM[bz][b] = __ldg(&c[gidx(kp, i[b], jm, k[bz])]);
-            YP[bz][b] = __ldg(&c[gidx(kp, i[b], jp, k[bz])]);
+        for (int bb = 0; bb < 2; ++bb) {
+            const int64_t yb = oy[1 + bb], xb = ox[1 + bb];
+            C[bz][bb][0] = __ldg(&c[b + z + yb]);
+            C[bz][bb][1] = __ldg(&c[b + z + yb + ox[2]]);
+            XM[bz][bb] = __ldg(&c[b + z + yb + ox[0]]);
+            XP[bz][bb] = __ldg(&c[b + z + yb + ox[3]]);
+            YM[bz][bb] = __ldg(&c[b + z + oy[0] + xb]);
+            YP[bz][bb] = __ldg(&c[b + z + oy[3] + xb]);
         }
     }
     if (DIM == 3) {
-        const int km = gnbr(kp, 2, k[0] - 1), kq = gnbr(kp, 2, k[1] + 1);
 #pragma unroll
         for (int by = 0; by < 2; ++by)
 #pragma unroll
             for (int bx = 0; bx < 2; ++bx) {
-                ZM[by][bx] = __ldg(&c[gidx(kp, i[bx], j[by], km)]);
-                ZP[by][bx] = __ldg(&c[gidx(kp, i[bx], j[by], kq)]);
+                ZM[by][bx] = __ldg(&c[b + oz[0] + oy[1 + by] + ox[1 + bx]]);
+                ZP[by][bx] = __ldg(&c[b + oz[3] + oy[1 + by] + ox[1 + bx]]);
             }
     }
     const float wx[2] = {1.f - fx, fx}, wy[2] = {1.f - fy, fy}, wz[2] = {1.f - fz, fz};
@@ -223,13 +283,13 @@ __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restr
             for (int bx = 0; bx < 2; ++bx) {
                 const float w = wx[bx] * wy[by] * (DIM == 3 ? wz[bz] : 1.f);
                 // central difference at the corner node: c(k+1) - c(k-1)
-                const float gx = bx ? XP[bz][by] - C[bz][by][0] : C[bz][by][1] - XM[bz][by];
-                const float gy = by ? YP[bz][bx] - C[bz][0][bx] : C[bz][1][bx] - YM[bz][bx];
-                g.x = fmaf(w, gx, g.x);
-                g.y = fmaf(w, gy, g.y);
+                const float gxv = bx ? XP[bz][by] - C[bz][by][0] : C[bz][by][1] - XM[bz][by];
+                const float gyv = by ? YP[bz][bx] - C[bz][0][bx] : C[bz][1][bx] - YM[bz][bx];
+                g.x = fmaf(w, gxv, g.x);
+                g.y = fmaf(w, gyv, g.y);
                 if (DIM == 3) {
-                    const float gz = bz ? ZP[by][bx] - C[0][by][bx] : C[NZ - 1][by][bx] - ZM[by][bx];
-                    g.z = fmaf(w, gz, g.z);
+                    const float gzv = bz ? ZP[by][bx] - C[0][by][bx] : C[NZ - 1][by][bx] - ZM[by][bx];
+                    g.z = fmaf(w, gzv, g.z);
                 }
                 cval = fmaf(w, C[bz][by][bx], cval);
             }
@@ -263,9 +323,10 @@ __device__ __forceinline__ float wrap_axis(float x, float lo, float hi, float L)
 // k_step: the particle part of one step.
 // ---------------------------------------------------------------------------
 template <int DIM, bool PERIODIC>
-__global__ void __launch_bounds__(TPB) k_step(KP kp, int cur)
+__global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
 {
-    __shared__ SmemTables t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
     load_tables(kp, t);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -279,7 +340,9 @@ __global__ void __launch_bounds__(TPB) k_step(KP kp, int cur)
     int cnt_unused = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs) F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, cnt_unused, ids_unused);
+    if (kp.pairs)
+        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, cnt_unused, ids_unused,
+                                             smem + sizeof(SmemTables));
 
     float3 dr = make_float3(0.f, 0.f, 0.f);
     float conc = 0.f;
@@ -348,7 +411,7 @@ __global__ void __launch_bounds__(TPB) k_step(KP kp, int cur)
     }
     const float4 nu = make_float4(xb, yb, zb, __uint_as_float(id | ((uint32_t)sp << SP_SHIFT)));
     kp.U[j] = nu;
-    kp.slot[j] = atomicAdd(&kp.cnt[key_of(kp, nu)], 1u);
+    kp.slot[j] = count_bin(kp.cnt_nxt, key_of(kp, nu), kp.err);
 }
 
 // ---------------------------------------------------------------------------
@@ -389,20 +452,21 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
         }
         kp.dU[i] = d;
     }
-    kp.slot[i] = atomicAdd(&kp.cnt[key_of(kp, u)], 1u);
+    kp.slot[i] = count_bin(kp.cnt_nxt, key_of(kp, u), kp.err);
 }
 
 // ---------------------------------------------------------------------------
-// k_scan: exclusive scan of cnt[0, bin_slots) into start[0, bin_slots]
-// (start[bin_slots] = n), clearing cnt. Single pass with decoupled look-back
-// (Merrill & Garland, 2016): tiles are claimed in order from an atomic
-// counter, each publishes its aggregate, then its inclusive prefix once its
-// predecessors' are known. Waits are bounded; a wait that runs out latches
-// ERR_TIMEOUT and proceeds.
+// k_scan: offsets of the groups of 8 bins of the state just counted
+// (cnt_nxt): gstart[g] = sum of the counts of all earlier groups,
+// gstart[ngroups] = n. Single pass with decoupled look-back (Merrill &
+// Garland, 2016): tiles are claimed in order from an atomic counter, each
+// publishes its aggregate, then its inclusive prefix once its predecessors'
+// are known. Waits are bounded; a wait that runs out latches ERR_TIMEOUT and
+// proceeds. The kernel also clears cnt_cur (the counts of the state the
+// particle kernel has finished reading), which the next step counts into.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_ITEMS = 4;                       // per thread per round
-constexpr int SCAN_ROUNDS = 4;
-constexpr int SCAN_TILE = TPB * SCAN_ITEMS * SCAN_ROUNDS;  // 4096 bins
+constexpr int SCAN_ITEMS = 8;                       // consecutive groups per thread
+constexpr int SCAN_TILE = TPB * SCAN_ITEMS;         // 2048 groups
 constexpr unsigned long long ST_AGG = 1ull, ST_INC = 2ull;
 constexpr int ST_VAL_BITS = 38;
 constexpr unsigned long long ST_VAL_MASK = (1ull << ST_VAL_BITS) - 1ull;
@@ -437,10 +501,10 @@ __device__ __forceinline__ uint32_t block_exscan(uint32_t v, uint32_t &total, ui
     }
     __syncthreads();
     total = warp_sums[TPB / 32 - 1];
-    const uint32_t before = wid ? warp_sums[wid - 1] : 0u;
-    __syncthreads();
-    return before + x - v;
+    return (wid ? warp_sums[wid - 1] : 0u) + x - v;
 }
+
+__device__ __forceinline__ uint32_t halfsum(uint32_t w) { return (w & 0xFFFFu) + (w >> 16); }
 
 __global__ void __launch_bounds__(TPB) k_scan(KP kp)
 {
@@ -455,29 +519,27 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
         return;
     }
     const uint32_t epoch = (*(volatile uint32_t *)kp.scan_seq % 0xFFFFFFu) + 1u;
-    const int64_t B = kp.bin_slots;
-    const int64_t base = (int64_t)tile * SCAN_TILE;
+    const int64_t NG = kp.ngroups;
+    const int64_t g0 = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
 
-    uint32_t v[SCAN_ROUNDS][SCAN_ITEMS];
-    uint32_t tsum[SCAN_ROUNDS];
+    uint32_t v[SCAN_ITEMS];
+    const uint4 *src = reinterpret_cast<const uint4 *>(kp.cnt_nxt);  // one uint4 per group
+    uint4 *clr = reinterpret_cast<uint4 *>(kp.cnt_cur);
 #pragma unroll
-    for (int r = 0; r < SCAN_ROUNDS; ++r) {
-        const int64_t i0 = base + (int64_t)r * TPB * SCAN_ITEMS + (int64_t)threadIdx.x * SCAN_ITEMS;
-        if (i0 + SCAN_ITEMS <= B) {
-            const uint4 q = *reinterpret_cast<const uint4 *>(&kp.cnt[i0]);
-            v[r][0] = q.x; v[r][1] = q.y; v[r][2] = q.z; v[r][3] = q.w;
-        } else {
-#pragma unroll
-            for (int k = 0; k < SCAN_ITEMS; ++k) v[r][k] = (i0 + k < B) ? kp.cnt[i0 + k] : 0u;
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const int64_t g = g0 + i;
+        v[i] = 0u;
+        if (g < NG) {
+            const uint4 q = __ldcs(src + g);
+            v[i] = halfsum(q.x) + halfsum(q.y) + halfsum(q.z) + halfsum(q.w);
+            clr[g] = make_uint4(0u, 0u, 0u, 0u);
         }
-        tsum[r] = v[r][0] + v[r][1] + v[r][2] + v[r][3];
     }
-    uint32_t rpre[SCAN_ROUNDS], rtot[SCAN_ROUNDS];
+    uint32_t tsum = 0;
 #pragma unroll
-    for (int r = 0; r < SCAN_ROUNDS; ++r) rpre[r] = block_exscan(tsum[r], rtot[r], s_warp);
-    uint32_t tile_total = 0;
-#pragma unroll
-    for (int r = 0; r < SCAN_ROUNDS; ++r) tile_total += rtot[r];
+    for (int i = 0; i < SCAN_ITEMS; ++i) tsum += v[i];
+    uint32_t tile_total;
+    const uint32_t tpre = block_exscan(tsum, tile_total, s_warp);
 
     // publish and look back
     if (threadIdx.x < 32) {
@@ -520,40 +582,29 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
         }
         if (timed_out) set_err(kp, ERR_TIMEOUT);
         if (lane == 0) {
-            if (tile != 0) {
-                __threadfence();
-                atomicExch(&kp.tiles[tile], st_pack(epoch, ST_INC, excl + tile_total));
-            }
+            if (tile != 0) atomicExch(&kp.tiles[tile], st_pack(epoch, ST_INC, excl + tile_total));
             s_prefix = excl;
         }
     }
     __syncthreads();
-    const uint32_t tile_prefix = (uint32_t)s_prefix;
-    uint32_t off = tile_prefix;
+    uint32_t run = (uint32_t)s_prefix + tpre;
+    uint32_t out[SCAN_ITEMS];
 #pragma unroll
-    for (int r = 0; r < SCAN_ROUNDS; ++r) {
-        const int64_t i0 = base + (int64_t)r * TPB * SCAN_ITEMS + (int64_t)threadIdx.x * SCAN_ITEMS;
-        uint32_t run = off + rpre[r];
-        uint32_t out[SCAN_ITEMS];
-#pragma unroll
-        for (int k = 0; k < SCAN_ITEMS; ++k) {
-            out[k] = run;
-            run += v[r][k];
-        }
-        if (i0 + SCAN_ITEMS <= B) {
-            *reinterpret_cast<uint4 *>(&kp.start[i0]) = make_uint4(out[0], out[1], out[2], out[3]);
-            *reinterpret_cast<uint4 *>(&kp.cnt[i0]) = make_uint4(0u, 0u, 0u, 0u);
-        } else {
-#pragma unroll
-            for (int k = 0; k < SCAN_ITEMS; ++k)
-                if (i0 + k < B) {
-                    kp.start[i0 + k] = out[k];
-                    kp.cnt[i0 + k] = 0u;
-                }
-        }
-        off += rtot[r];
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        out[i] = run;
+        run += v[i];
     }
-    if (base + SCAN_TILE >= B && base < B && threadIdx.x == 0) kp.start[B] = tile_prefix + tile_total;
+    if (g0 + SCAN_ITEMS <= NG) {
+        uint4 *dst = reinterpret_cast<uint4 *>(kp.gstart + g0);
+#pragma unroll
+        for (int r = 0; r < SCAN_ITEMS / 4; ++r) dst[r] = make_uint4(out[4 * r], out[4 * r + 1], out[4 * r + 2], out[4 * r + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i)
+            if (g0 + i < NG) kp.gstart[g0 + i] = out[i];
+    }
+    const int64_t base = (int64_t)tile * SCAN_TILE;
+    if (base + SCAN_TILE >= NG && base < NG && threadIdx.x == 0) kp.gstart[NG] = (uint32_t)s_prefix + tile_total;
 }
 
 // ---------------------------------------------------------------------------
@@ -610,7 +661,7 @@ __global__ void __launch_bounds__(TPB) k_scatter(KP kp, int cur, int advance)
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (j >= kp.n) return;
     const float4 u = kp.U[j];
-    const uint32_t dst = kp.start[key_of(kp, u)] + kp.slot[j];
+    const uint32_t dst = bin_start(kp.cnt_nxt, kp.gstart, key_of(kp, u)) + kp.slot[j];
     if ((int64_t)dst >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
         return;
@@ -677,6 +728,123 @@ __global__ void __launch_bounds__(128) k_pde(KP kp, const float *__restrict__ ci
 }
 
 // ---------------------------------------------------------------------------
+// k_pde_stream: the same substep as k_pde, streamed. Each thread owns four
+// consecutive x nodes (one float4) of a row and marches along the last axis
+// (z in 3D, y in 2D), keeping the previous / current / next planes in
+// registers; x neighbours come from the adjacent lanes (shuffles) and, in 3D,
+// the y neighbours from the rows beside it (cache hits). One DRAM read and one
+// write per node. Needs gx % 4 == 0.
+// ---------------------------------------------------------------------------
+template <int BC>
+__device__ __forceinline__ int ghost(int k, int N)  // ghost rule along one axis
+{
+    if (BC == 2) return k < 0 ? k + N : (k >= N ? k - N : k);
+    return k < 0 ? -k : (k > N - 1 ? 2 * (N - 1) - k : k);
+}
+
+__device__ __forceinline__ float4 f4_axpy(float a, float4 x, float4 y)
+{
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+
+template <int DIM, int BC>
+__global__ void __launch_bounds__(256) k_pde_stream(KP kp, const float *__restrict__ cin, float *__restrict__ cout,
+                                                    int use_src, int last, int chunk)
+{
+    const int gx = kp.g[0], gy = kp.g[1], gz = DIM == 3 ? kp.g[2] : 1;
+    const int nq = gx >> 2;
+    const int lane = threadIdx.x;
+    const int q = blockIdx.x * 32 + lane;
+    const int qq = q < nq ? q : nq - 1;
+    int y, s0, ns;
+    if (DIM == 3) {
+        y = blockIdx.y * blockDim.y + threadIdx.y;
+        ns = gz;
+        s0 = blockIdx.z * chunk;
+    } else {
+        y = 0;
+        ns = gy;
+        s0 = (blockIdx.z * blockDim.y + threadIdx.y) * chunk;
+    }
+    const bool active = q < nq && (DIM == 2 || y < gy);
+    const int yy = DIM == 3 ? min(y, gy - 1) : 0;
+    const int s1 = min(s0 + chunk, ns);
+    if (s0 >= ns) return;  // whole warp (s0 depends on warp / block only)
+    const int64_t sstride = DIM == 3 ? (int64_t)gx * gy : (int64_t)gx;
+    const int64_t rowbase = (DIM == 3 ? (int64_t)yy * gx : 0) + 4 * (int64_t)qq;
+    int64_t oym = 0, oyp = 0;
+    if (DIM == 3) {
+        oym = (int64_t)(ghost<BC>(yy - 1, gy) - yy) * gx;
+        oyp = (int64_t)(ghost<BC>(yy + 1, gy) - yy) * gx;
+    }
+    const float ihx = kp.inv_h2[0], ihy = kp.inv_h2[1], ihz = kp.inv_h2[2];
+    const float ihs = DIM == 3 ? ihz : ihy;  // stream axis
+    const float Dc = kp.Dc, gam = kp.gamma, dts = kp.dts;
+    const float inv_s = 1.f / (float)kp.substeps;
+    const bool xlo = 4 * qq == 0, xhi = 4 * qq + 4 == gx;
+    const bool ywall = DIM == 3 && (yy == 0 || yy == gy - 1);
+    auto ld = [&](int64_t i) { return __ldg(reinterpret_cast<const float4 *>(cin + i)); };
+    float4 vm = ld(rowbase + (int64_t)ghost<BC>(s0 - 1, ns) * sstride);
+    float4 v0 = ld(rowbase + (int64_t)s0 * sstride);
+    float4 vp = ld(rowbase + (int64_t)ghost<BC>(s0 + 1, ns) * sstride);
+    for (int s = s0; s < s1; ++s) {
+        const int64_t b = rowbase + (int64_t)s * sstride;
+        const float4 vq = (s + 1 < s1) ? ld(rowbase + (int64_t)ghost<BC>(s + 2, ns) * sstride) : vp;
+        float left = __shfl_up_sync(0xffffffffu, v0.w, 1);
+        float right = __shfl_down_sync(0xffffffffu, v0.x, 1);
+        if (xlo) left = BC == 2 ? __ldg(cin + b + gx - 1) : v0.y;
+        else if (lane == 0) left = __ldg(cin + b - 1);
+        if (xhi) right = BC == 2 ? __ldg(cin + b - (gx - 4)) : v0.z;
+        else if (lane == 31) right = __ldg(cin + b + 4);
+        float4 lap;
+        lap.x = (left + v0.y - 2.f * v0.x) * ihx;
+        lap.y = (v0.x + v0.z - 2.f * v0.y) * ihx;
+        lap.z = (v0.y + v0.w - 2.f * v0.z) * ihx;
+        lap.w = (v0.z + right - 2.f * v0.w) * ihx;
+        lap.x = fmaf(vm.x + vp.x - 2.f * v0.x, ihs, lap.x);
+        lap.y = fmaf(vm.y + vp.y - 2.f * v0.y, ihs, lap.y);
+        lap.z = fmaf(vm.z + vp.z - 2.f * v0.z, ihs, lap.z);
+        lap.w = fmaf(vm.w + vp.w - 2.f * v0.w, ihs, lap.w);
+        if (DIM == 3) {
+            const float4 a = ld(b + oym), c = ld(b + oyp);
+            lap.x = fmaf(a.x + c.x - 2.f * v0.x, ihy, lap.x);
+            lap.y = fmaf(a.y + c.y - 2.f * v0.y, ihy, lap.y);
+            lap.z = fmaf(a.z + c.z - 2.f * v0.z, ihy, lap.z);
+            lap.w = fmaf(a.w + c.w - 2.f * v0.w, ihy, lap.w);
+        }
+        // rhs = D_c lap - gamma c - R c
+        float4 rhs = make_float4(Dc * lap.x - gam * v0.x, Dc * lap.y - gam * v0.y, Dc * lap.z - gam * v0.z,
+                                 Dc * lap.w - gam * v0.w);
+        float4 add = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (use_src) {
+            float4 *S4 = reinterpret_cast<float4 *>(kp.srcg + b);
+            float4 *R4 = reinterpret_cast<float4 *>(kp.Rg + b);
+            const float4 Sv = *S4, Rv = *R4;
+            rhs.x -= Rv.x * v0.x;
+            rhs.y -= Rv.y * v0.y;
+            rhs.z -= Rv.z * v0.z;
+            rhs.w -= Rv.w * v0.w;
+            add = make_float4(Sv.x * inv_s, Sv.y * inv_s, Sv.z * inv_s, Sv.w * inv_s);
+            if (last && active) {
+                *S4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                *R4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        float4 out = f4_axpy(dts, rhs, make_float4(v0.x + add.x, v0.y + add.y, v0.z + add.z, v0.w + add.w));
+        if (BC == 1) {  // Dirichlet: wall nodes keep their value
+            const bool swall = s == 0 || s == ns - 1;
+            if (swall || ywall) out = v0;
+            if (xlo) out.x = v0.x;
+            if (xhi) out.w = v0.w;
+        }
+        if (active) *reinterpret_cast<float4 *>(cout + b) = out;
+        vm = v0;
+        v0 = vp;
+        vp = vq;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Read-out and stage kernels.
 // ---------------------------------------------------------------------------
 __global__ void k_unsort(KP kp, float *__restrict__ pos, uint8_t *__restrict__ sp, float *__restrict__ disp)
@@ -734,11 +902,19 @@ __global__ void k_stage_sort(KP kp, uint32_t *__restrict__ ids)
     if (j < kp.n) ids[j] = __float_as_uint(kp.S[j].w) & ID_MASK;
 }
 
+// Offset of every bin (bin_slots + 1 entries) of the sorted state.
+__global__ void k_stage_starts(KP kp, uint32_t *__restrict__ out)
+{
+    const int64_t k = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (k <= kp.bin_slots) out[k] = bin_start(kp.cnt_cur, kp.gstart, (uint32_t)k);
+}
+
 template <int DIM, bool PERIODIC>
-__global__ void __launch_bounds__(TPB) k_stage_forces(KP kp, float *__restrict__ F_out, int32_t *__restrict__ count,
+__global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restrict__ F_out, int32_t *__restrict__ count,
                                                       unsigned long long *__restrict__ idsum)
 {
-    __shared__ SmemTables t;
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
     load_tables(kp, t);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -753,7 +929,9 @@ __global__ void __launch_bounds__(TPB) k_stage_forces(KP kp, float *__restrict__
     int cnt = 0;
     unsigned long long ids = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs) F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), cnt, ids);
+    if (kp.pairs)
+        F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), cnt, ids,
+                                            smem + sizeof(SmemTables));
     F_out[id * DIM + 0] = F.x;
     F_out[id * DIM + 1] = F.y;
     if (DIM == 3) F_out[id * DIM + 2] = F.z;
@@ -808,16 +986,45 @@ __global__ void k_fill(float *p, float v, int64_t n)
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
+// Pair kernels may need more than the default 48 KB of dynamic shared memory.
+// The pair kernels run 4 blocks per SM (register bound). Ask for just the
+// shared memory those blocks need and leave the rest of the SM's 256 KB to
+// L1, which caches the candidate positions.
+template <typename K>
+static void allow_smem(K kernel, size_t bytes)
+{
+    if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const double need = 4.0 * (double)(bytes + 1024) / (228.0 * 1024.0);
+    const int pct = (int)std::ceil(100.0 * need);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
+}
+
+static void pair_kernel_attributes()
+{
+    static bool done = false;
+    if (done) return;
+    allow_smem(k_step<2, false>, pair_smem<2, false>());
+    allow_smem(k_step<2, true>, pair_smem<2, true>());
+    allow_smem(k_step<3, false>, pair_smem<3, false>());
+    allow_smem(k_step<3, true>, pair_smem<3, true>());
+    allow_smem(k_stage_forces<2, false>, pair_smem<2, false>());
+    allow_smem(k_stage_forces<2, true>, pair_smem<2, true>());
+    allow_smem(k_stage_forces<3, false>, pair_smem<3, false>());
+    allow_smem(k_stage_forces<3, true>, pair_smem<3, true>());
+    done = true;
+}
+
 cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (kp.n == 0) return cudaSuccess;
+    pair_kernel_attributes();
     const unsigned nb = blocks_for(kp.n);
     if (kp.dim == 2) {
-        if (kp.periodic) k_step<2, true><<<nb, TPB, 0, st>>>(kp, cur);
-        else k_step<2, false><<<nb, TPB, 0, st>>>(kp, cur);
+        if (kp.periodic) k_step<2, true><<<nb, TPB, pair_smem<2, true>(), st>>>(kp, cur);
+        else k_step<2, false><<<nb, TPB, pair_smem<2, false>(), st>>>(kp, cur);
     } else {
-        if (kp.periodic) k_step<3, true><<<nb, TPB, 0, st>>>(kp, cur);
-        else k_step<3, false><<<nb, TPB, 0, st>>>(kp, cur);
+        if (kp.periodic) k_step<3, true><<<nb, TPB, pair_smem<3, true>(), st>>>(kp, cur);
+        else k_step<3, false><<<nb, TPB, pair_smem<3, false>(), st>>>(kp, cur);
     }
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -834,7 +1041,7 @@ cudaError_t launch_pack(const KP &kp, const float *pos, const uint8_t *sp, const
 
 cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches)
 {
-    const unsigned tiles = (unsigned)((kp.bin_slots + SCAN_TILE - 1) / SCAN_TILE);
+    const unsigned tiles = (unsigned)((kp.ngroups + SCAN_TILE - 1) / SCAN_TILE);
     k_scan<<<tiles, TPB, 0, st>>>(kp);
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -849,17 +1056,50 @@ cudaError_t launch_scatter(const KP &kp, int cur, int advance, cudaStream_t st, 
     return cudaGetLastError();
 }
 
+template <int DIM>
+static void pde_stream_launch(const KP &kp, const float *cin, float *cout, int use_src, int last, cudaStream_t st)
+{
+    const int nq = kp.g[0] / 4;
+    const int bx = (nq + 31) / 32;
+    const dim3 block(32, 8);
+    if (DIM == 3) {
+        // aim at about four blocks per SM; chunks of at least 8 planes
+        const int by = (kp.g[1] + 7) / 8;
+        int chunk = 8;
+        while (chunk < kp.g[2] && (int64_t)bx * by * ((kp.g[2] + 2 * chunk - 1) / (2 * chunk)) >= 608) chunk *= 2;
+        const dim3 grid(bx, by, (kp.g[2] + chunk - 1) / chunk);
+        if (kp.pde_bc == 0) k_pde_stream<3, 0><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+        else if (kp.pde_bc == 1) k_pde_stream<3, 1><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+        else k_pde_stream<3, 2><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+    } else {
+        int chunk = 4;
+        while (chunk < kp.g[1] && (int64_t)bx * 8 * ((kp.g[1] + 2 * chunk - 1) / (2 * chunk)) >= 2432) chunk *= 2;
+        const int warps = (kp.g[1] + chunk - 1) / chunk;
+        const dim3 grid(bx, 1, (warps + 7) / 8);
+        if (kp.pde_bc == 0) k_pde_stream<2, 0><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+        else if (kp.pde_bc == 1) k_pde_stream<2, 1><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+        else k_pde_stream<2, 2><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
+    }
+}
+
 cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (!kp.has_grid || kp.chem_mode != 0) return cudaSuccess;
+    const bool stream = kp.g[0] % 4 == 0 && kp.g[0] >= 8;
     const dim3 grid((kp.g[0] + 127) / 128, kp.g[1], kp.dim == 3 ? kp.g[2] : 1);
     const int s = kp.substeps;
     const int use_src = kp.fused_deposit ? 0 : 1;
     int c = cur;
     for (int m = 0; m < s; ++m) {
         const int last = m == s - 1;
-        if (kp.dim == 2) k_pde<2><<<grid, 128, 0, st>>>(kp, kp.c[c], kp.c[c ^ 1], use_src, last);
-        else k_pde<3><<<grid, 128, 0, st>>>(kp, kp.c[c], kp.c[c ^ 1], use_src, last);
+        if (stream) {
+            if (kp.dim == 2) pde_stream_launch<2>(kp, kp.c[c], kp.c[c ^ 1], use_src, last, st);
+            else pde_stream_launch<3>(kp, kp.c[c], kp.c[c ^ 1], use_src, last, st);
+        } else if (kp.dim == 2) {
+            k_pde<2><<<grid, 128, 0, st>>>(kp, kp.c[c], kp.c[c ^ 1], use_src, last);
+        } else {
+            k_pde<3><<<grid, 128, 0, st>>>(kp, kp.c[c], kp.c[c ^ 1], use_src, last);
+        }
         c ^= 1;
         if (launches) ++*launches;
     }
@@ -888,23 +1128,24 @@ cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, cudaStream_t st)
+cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, uint32_t *bin_starts, cudaStream_t st)
 {
-    if (kp.n == 0) return cudaSuccess;
-    k_stage_sort<<<blocks_for(kp.n), TPB, 0, st>>>(kp, ids);
+    if (ids && kp.n > 0) k_stage_sort<<<blocks_for(kp.n), TPB, 0, st>>>(kp, ids);
+    if (bin_starts) k_stage_starts<<<blocks_for(kp.bin_slots + 1), TPB, 0, st>>>(kp, bin_starts);
     return cudaGetLastError();
 }
 
 cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned long long *idsum, cudaStream_t st)
 {
     if (kp.n == 0) return cudaSuccess;
+    pair_kernel_attributes();
     const unsigned nb = blocks_for(kp.n);
     if (kp.dim == 2) {
-        if (kp.periodic) k_stage_forces<2, true><<<nb, TPB, 0, st>>>(kp, F, count, idsum);
-        else k_stage_forces<2, false><<<nb, TPB, 0, st>>>(kp, F, count, idsum);
+        if (kp.periodic) k_stage_forces<2, true><<<nb, TPB, pair_smem<2, true>(), st>>>(kp, F, count, idsum);
+        else k_stage_forces<2, false><<<nb, TPB, pair_smem<2, false>(), st>>>(kp, F, count, idsum);
     } else {
-        if (kp.periodic) k_stage_forces<3, true><<<nb, TPB, 0, st>>>(kp, F, count, idsum);
-        else k_stage_forces<3, false><<<nb, TPB, 0, st>>>(kp, F, count, idsum);
+        if (kp.periodic) k_stage_forces<3, true><<<nb, TPB, pair_smem<3, true>(), st>>>(kp, F, count, idsum);
+        else k_stage_forces<3, false><<<nb, TPB, pair_smem<3, false>(), st>>>(kp, F, count, idsum);
     }
     return cudaGetLastError();
 }
