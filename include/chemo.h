@@ -245,6 +245,33 @@ int chemo_stage_drift(chemo_sim *sim, float *drift_out, int mem_kind, void *stre
  * h^d) (grid_nodes each, C-order; either may be NULL). */
 int chemo_stage_deposit(chemo_sim *sim, float *S_out, float *R_out, int mem_kind, void *stream);
 
+/* ---------------------------------------------------------------------- */
+/* Pair forces without device allocation.                                  */
+/* ---------------------------------------------------------------------- */
+
+/* Row a3 (the pair force F_i, n x dim float32 by particle index) of a
+ * caller's particle set, computed without allocating any device memory. The
+ * paper has no counterpart; this entry point exists for callers that cannot
+ * call cudaMalloc where they need forces: applications that give the library
+ * a fixed device-memory budget at start-up, real-time loops in which an
+ * allocation (which can synchronise the device) would break the timing, and
+ * plug-ins running inside another framework's memory manager.
+ *
+ * pos (n x dim float32), species (n uint8) and F_out must be device memory;
+ * params as for chemo_create (only the geometry, species and force fields
+ * matter). The cell list is built in one static device array owned by the
+ * library (about 3.4 MB, held on every GPU that loads the library until the
+ * process exits), so: n <= 65536 and the cell list may use at most 262144
+ * bins, else CHEMO_EINVAL with a message naming the limit. All calls share
+ * the array and it keeps the last call's contents; calls whose kernels
+ * overlap on the GPU (different streams without ordering) race on it. The
+ * first call on a device looks up the array's device address, with that
+ * device current; make that first call before any stream capture. The call
+ * is asynchronous on `stream`; device-side input errors (non-finite
+ * positions, species out of range) are not reported. */
+int chemo_forces_noalloc(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species,
+                         float *F_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

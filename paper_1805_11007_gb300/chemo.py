@@ -173,6 +173,7 @@ def _declare(L):
         "chemo_stage_forces": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_drift": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_deposit": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_forces_noalloc": ([PP, i64, vp, vp, vp, vp], ctypes.c_int),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -407,6 +408,19 @@ def chemo_stage_deposit(sim: Sim, S_out=None, R_out=None, stream=None):
     sp, k1, _a = _buf(S_out, np.float32)
     rp, k2, _b = _buf(R_out, np.float32)
     _check(lib().chemo_stage_deposit(_h(sim), sp, rp, _kind(k1, k2), _stream(stream)), "chemo_stage_deposit")
+
+
+def chemo_forces_noalloc(params: dict, pos, species, F_out, stream=None):
+    """Pair forces of a particle set (all CUDA tensors) without any device
+    allocation (see include/chemo.h for the limits)."""
+    pp, k1, _a = _buf(pos, np.float32)
+    sp, k2, _b = _buf(species, np.uint8)
+    fp, k3, _c = _buf(F_out, np.float32)
+    if _kind(k1, k2, k3) != MEM_DEVICE:
+        raise ValueError("chemo_forces_noalloc takes device buffers only")
+    prm = make_params(params)
+    n = int(pos.shape[0])
+    _check(lib().chemo_forces_noalloc(ctypes.byref(prm), n, pp, sp, fp, _stream(stream)), "chemo_forces_noalloc")
 
 
 # ---------------------------------------------------------------------------

@@ -479,6 +479,25 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
 
 }  // namespace
 
+// Parameter block of a particle set that is binned and searched only
+// (no grid, no buffers): validation, cell-list layout and model constants.
+int chemo_internal_build_kp(const chemo_params *params, int64_t n, KP *out)
+{
+    g_last_error[0] = 0;
+    if (!params || !out) return fail(CHEMO_EINVAL, "params and out are required");
+    if (int r = check_params(*params)) return r;
+    if (n < 0 || n > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "n = %lld out of range", (long long)n);
+    KP kp{};
+    kp.n = n;
+    if (int r = fill_layout(*params, n, kp)) return r;
+    if (int r = fill_grid(*params, kp)) return r;
+    fill_model(*params, kp);
+    *out = kp;
+    return CHEMO_OK;
+}
+
+int chemo_internal_fail(int status, const char *msg) { return fail(status, "%s", msg); }
+
 extern "C" {
 
 const char *chemo_status_string(int status)

@@ -272,3 +272,13 @@ cudaError_t launch_stage_deposit(const KP &kp, float *S, float *R, cudaStream_t 
 cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);
 
 }  // namespace chemo
+
+struct chemo_params;
+// Validated parameter block (layout and constants, no buffers) of n
+// particles; sets the thread's last-error message on failure (chemo_capi.cu).
+int chemo_internal_build_kp(const chemo_params *params, int64_t n, chemo::KP *out);
+int chemo_internal_fail(int status, const char *msg);
+
+namespace chemo {
+
+}  // namespace chemo
