@@ -219,12 +219,13 @@ void fill_model(const chemo_params &p, KP &kp)
         const double r = m * (1.0 + 1e-3);
         kp.rsp2[s] = (float)(r * r);
     }
-    // fixed-point quantum of the pair-force sum: 2^-40 of the largest pair
-    // force magnitude inter/eps (terms never exceed it)
+    // fixed-point quantum of the pair-force sum: 2^-25 of the largest pair
+    // force magnitude inter/eps (terms never exceed it, so 16 of them fit an
+    // int32)
     double fmax = 0.0;
     for (int i = 0; i < MAXS * MAXS; ++i) fmax = std::max(fmax, (double)std::fabs(kp.amp_f[i]));
     if (!(fmax > 0.0)) fmax = 1.0;
-    kp.fq = (float)std::ldexp(fmax, -40);
+    kp.fq = (float)std::ldexp(fmax, -25);
     kp.fq_inv = (float)(1.0 / (double)kp.fq);
     kp.reactions = p.reactions ? 1 : 0;
     kp.dt = (float)p.dt;
@@ -289,8 +290,8 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
             if (search == 1 && kp.nb[a] < 3)
                 return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= r_c; need >= 3 (box too small "
                                           "for the cutoff; try search_mode 2)", a, kp.nb[a]);
-            if (search == 2 && kp.nb[a] < 2)
-                return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= 2 r_c; need >= 2", a, kp.nb[a]);
+            if (search == 2 && kp.nb[a] < 3)
+                return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= 2 r_c; need >= 3", a, kp.nb[a]);
         }
     }
     if (p.bin_order == 2) return fail(CHEMO_ENOTSUP, "Z-order bin storage is not supported; bins are row-major");

@@ -59,14 +59,24 @@ struct FAcc {
 // Search window. Bins are stored row-major (x fastest), so the bins of one
 // x-row of the window are one contiguous range of the sorted array: the
 // window is at most 3^(d-1) ranges (twice that when a periodic row wraps).
-// Rows (and the end bins of a row) that lie farther from the particle than
-// its species' largest cutoff are skipped. Each thread stages its ranges in
+// Rows (and the end bins of a row) farther from the particle than its
+// species' largest cutoff are skipped. Each thread stages its ranges in
 // shared memory and walks all of them in one flattened loop (the warp waits
-// for its longest candidate list only, not for the longest bin of every
-// row). Candidates inside the cutoff are listed in shared memory and their
-// forces evaluated in a second, mostly converged loop.
+// for its longest candidate list only, not for the longest bin of every row).
+// Candidates inside the cutoff are listed in shared memory; whenever one lane
+// of the warp has filled its list, the whole warp evaluates its lists
+// together (a mostly converged loop), and once more at the end.
+//
+// Pair terms are quantised to 32-bit fixed point (quantum 2^-25 of the
+// largest pair force, far below FP32 resolution of the sum's tolerance) and
+// summed exactly: in int32 over one list (at most LIST_CAP terms, no
+// overflow), then in int64. The force is then independent of the order of
+// the particles inside a bin (which the atomic slots of the counting sort
+// leave unspecified), and no 64-bit conversion runs per pair (those use the
+// narrow FP64 pipe).
 // ---------------------------------------------------------------------------
-constexpr int LIST_CAP = 16;
+constexpr int LIST_CAP = 24;  // flushed once a lane holds more than LIST_CAP - UNROLL
+constexpr int UNROLL = 8;     // candidates per lane between two warp votes
 
 template <int DIM, bool PERIODIC>
 struct RowCap {
@@ -94,19 +104,6 @@ __device__ __forceinline__ void pair_delta(const KP &kp, float4 me, float4 o, fl
     r2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
 }
 
-template <int DIM>
-__device__ __forceinline__ void pair_term(const KP &kp, const SmemTables &t, int st, float dx, float dy, float dz,
-                                          float r2, FAcc &F)
-{
-    const float rinv = rsqrtf(r2);
-    const float r = r2 * rinv;
-    const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
-    const float sq = (f * rinv) * kp.fq_inv;
-    F.x += __float2ll_rn(sq * dx);
-    F.y += __float2ll_rn(sq * dy);
-    if (DIM == 3) F.z += __float2ll_rn(sq * dz);
-}
-
 // Distance (squared) from a particle at offset f in [0,1] (bin units) of its
 // bin to the neighbouring bin at offset o in {-1, 0, +1}, bin side b.
 __device__ __forceinline__ float gap2(int o, float f, float b)
@@ -115,23 +112,48 @@ __device__ __forceinline__ float gap2(int o, float f, float b)
     return d * d;
 }
 
+// Evaluates the listed neighbours of every lane (lanes with an empty list
+// idle) and adds them to F. All lanes of the warp call it.
+template <int DIM, bool PERIODIC>
+__device__ __forceinline__ void flush_list(const KP &kp, const SmemTables &t, const uint32_t *lst, int nl, float4 me,
+                                           int row, FAcc &F)
+{
+    const int m = __reduce_max_sync(0xffffffffu, nl);
+    int ax = 0, ay = 0, az = 0;
+    for (int i = 0; i < m; ++i) {
+        if (i < nl) {
+            const float4 o = __ldg(&kp.S[lst[i * TPB]]);
+            float dx, dy, dz, r2;
+            pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+            const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
+            const float sq = (f * rinv) * kp.fq_inv;
+            ax += __float2int_rn(sq * dx);
+            ay += __float2int_rn(sq * dy);
+            if (DIM == 3) az += __float2int_rn(sq * dz);
+        }
+    }
+    F.x += ax;
+    F.y += ay;
+    F.z += az;
+}
+
+// Pair force of the particle `me` (sorted index `self`) of every valid lane.
+// Must be called by all 32 lanes of the warp (`valid` false for padding lanes).
 template <int DIM, bool PERIODIC, bool STATS>
 __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, uint32_t self, float4 me, int sp,
-                                             int &count, unsigned long long &idsum, unsigned char *smem_extra)
+                                             bool valid, int &count, unsigned long long &idsum, unsigned char *smem_extra)
 {
     uint2 *rng = reinterpret_cast<uint2 *>(smem_extra) + threadIdx.x;
     uint32_t *lst = reinterpret_cast<uint32_t *>(smem_extra + (size_t)TPB * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) +
                     threadIdx.x;
-    int c[3], lo[3], hi[3];
-    float f[3];
+    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
     const float pc[3] = {me.x, me.y, me.z};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        if (a >= DIM) {
-            c[a] = lo[a] = hi[a] = 0;
-            f[a] = 0.f;
-            continue;
-        }
+    for (int a = 0; a < DIM; ++a) {
         c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
         f[a] = fminf(fmaxf(__fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a], 0.f), 1.f);
         if (kp.search == 2) {
@@ -151,70 +173,94 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
     const uint32_t *__restrict__ gst = kp.gstart;
     const uint32_t n = (uint32_t)kp.n;
     int nr = 0;
-    for (int z = lo[2]; z <= hi[2]; ++z) {
-        const float gz = DIM == 3 ? gap2(z - c[2], f[2], kp.bside[2]) : 0.f;
-        int zz = z;
-        if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
-        for (int y = lo[1]; y <= hi[1]; ++y) {
-            const float gyz = gz + gap2(y - c[1], f[1], kp.bside[1]);
-            if (gyz >= rs2) continue;  // the whole row is out of reach
-            int yy = y;
-            if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
-            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
-            int x0 = lo[0], x1 = hi[0];
-            if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
-            if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
-            if (PERIODIC && x0 < 0) {
-                const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
-                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
-                x0 = 0;
+    if (valid) {
+        for (int z = lo[2]; z <= hi[2]; ++z) {
+            const float gz = DIM == 3 ? gap2(z - c[2], f[2], kp.bside[2]) : 0.f;
+            int zz = z;
+            if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
+            for (int y = lo[1]; y <= hi[1]; ++y) {
+                const float gyz = gz + gap2(y - c[1], f[1], kp.bside[1]);
+                if (gyz >= rs2) continue;  // the whole row is out of reach
+                int yy = y;
+                if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+                int x0 = lo[0], x1 = hi[0];
+                if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
+                if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
+                if (PERIODIC && x0 < 0) {
+                    const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
+                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
+                    x0 = 0;
+                }
+                if (PERIODIC && x1 >= kp.nb[0]) {
+                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
+                    x1 = kp.nb[0] - 1;
+                }
+                if (x0 <= x1)
+                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk + x0), bin_start(cnt, gst, rowk + x1 + 1));
             }
-            if (PERIODIC && x1 >= kp.nb[0]) {
-                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
-                x1 = kp.nb[0] - 1;
-            }
-            if (x0 <= x1)
-                rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk + x0), bin_start(cnt, gst, rowk + x1 + 1));
         }
     }
     const float4 *__restrict__ S = kp.S;
     const int row = sp * MAXS;
+    // squared cutoffs against species 0 and 1 in registers (systems of up to
+    // two species, the model of the paper); more species read the table
+    const bool two = kp.ns <= 2;
+    const float rc2_0 = t.rc2[row], rc2_1 = t.rc2[row + 1];
     FAcc F = {0ll, 0ll, 0ll};
     int nl = 0;
     int r = 0;
     uint32_t q = 0, qe = 0;
-    for (;;) {
-        while (q >= qe && r < nr) {
-            const uint2 g = rng[r++ * TPB];
-            q = g.x;
-            qe = min(g.y, n);  // offsets are trusted only up to n
-        }
-        if (q >= qe) break;
-        const float4 o = __ldg(&S[q]);
-        float dx, dy, dz, r2;
-        pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
-        const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
-        if (r2 < t.rc2[st] && r2 > 0.f && q != self) {
-            if (nl < LIST_CAP) lst[nl++ * TPB] = q;
-            else pair_term<DIM>(kp, t, st, dx, dy, dz, r2, F);
-            if (STATS) {
-                count += 1;
-                idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
+    while (q >= qe && r < nr) {
+        const uint2 g = rng[r++ * TPB];
+        q = g.x;
+        qe = min(g.y, n);  // offsets are trusted only up to n
+    }
+    bool more = q < qe;
+    while (__any_sync(0xffffffffu, more)) {
+        if (more) {
+            // a chunk of up to UNROLL candidates from one range; the next
+            // candidate is loaded while the current one is tested
+            const uint32_t m = min((uint32_t)UNROLL, qe - q);
+            float4 o = __ldg(&S[q]);
+            for (uint32_t u = 0; u < m; ++u) {
+                const uint32_t qq = q + u;
+                const float4 on = u + 1 < m ? __ldg(&S[qq + 1]) : o;
+                float dx, dy, dz, r2;
+                pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
+                const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
+                if (r2 < rc2 && r2 > 0.f && qq != self) {
+                    lst[nl++ * TPB] = qq;
+                    if (STATS) {
+                        count += 1;
+                        idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
+                    }
+                }
+                o = on;
+            }
+            q += m;
+            if (q >= qe) {
+                while (q >= qe && r < nr) {
+                    const uint2 g = rng[r++ * TPB];
+                    q = g.x;
+                    qe = min(g.y, n);
+                }
+                more = q < qe;
             }
         }
-        ++q;
+        if (__any_sync(0xffffffffu, nl > LIST_CAP - UNROLL)) {
+            flush_list<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
+            nl = 0;
+        }
     }
-    for (int i = 0; i < nl; ++i) {
-        const float4 o = __ldg(&S[lst[i * TPB]]);
-        float dx, dy, dz, r2;
-        pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
-        pair_term<DIM>(kp, t, row + (int)(__float_as_uint(o.w) >> SP_SHIFT), dx, dy, dz, r2, F);
-    }
+    flush_list<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
     return make_float3(__ll2float_rn(F.x) * kp.fq, __ll2float_rn(F.y) * kp.fq,
                        DIM == 3 ? __ll2float_rn(F.z) * kp.fq : 0.f);
 }
 
-// Dynamic shared memory of the kernels that evaluate pair forces.
+// Dynamic shared memory of the kernels that evaluate pair forces: species
+// tables, staged row ranges and the neighbour lists.
 template <int DIM, bool PERIODIC>
 constexpr size_t pair_smem()
 {
@@ -330,9 +376,8 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     load_tables(kp, t);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (j >= kp.n) return;
-    const unsigned long long step = *kp.step;
-    const float4 me = kp.S[j];
+    const bool valid = j < kp.n;
+    const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
     const uint32_t id = w & ID_MASK;
     int sp = (int)(w >> SP_SHIFT);
@@ -340,9 +385,11 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     int cnt_unused = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs)
-        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, cnt_unused, ids_unused,
+    if (kp.pairs)  // warp-synchronous: every lane takes part
+        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, cnt_unused, ids_unused,
                                              smem + sizeof(SmemTables));
+    if (!valid) return;
+    const unsigned long long step = *kp.step;
 
     float3 dr = make_float3(0.f, 0.f, 0.f);
     float conc = 0.f;
@@ -918,20 +965,21 @@ __global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restric
     load_tables(kp, t);
     __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (j >= kp.n) return;
-    const float4 me = kp.S[j];
+    const bool valid = j < kp.n;
+    const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
     const int64_t id = w & ID_MASK;
+    int cnt = 0;
+    unsigned long long ids = 0ull;
+    float3 F = make_float3(0.f, 0.f, 0.f);
+    if (kp.pairs)  // warp-synchronous: every lane takes part
+        F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), valid, cnt, ids,
+                                            smem + sizeof(SmemTables));
+    if (!valid) return;
     if (id >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
         return;
     }
-    int cnt = 0;
-    unsigned long long ids = 0ull;
-    float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs)
-        F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), cnt, ids,
-                                            smem + sizeof(SmemTables));
     F_out[id * DIM + 0] = F.x;
     F_out[id * DIM + 1] = F.y;
     if (DIM == 3) F_out[id * DIM + 2] = F.z;

@@ -239,8 +239,10 @@ def test_step_n_equals_repeated_steps_and_oracle():
         ca = chemo.read_field_host(a)
         cb = chemo.read_field_host(b)
         assert chemo.chemo_step_index(a) == k
-    # same kernels, same inputs; float atomics may reorder the deposit sums
-    assert np.abs(pa - pb).max() <= 1e-6
+    # same kernels, same inputs; the float atomics of the deposit make c
+    # differ in its last bits between runs (no bitwise reproducibility), so
+    # the two trajectories agree to the single-step tolerance
+    assert np.abs(pa - pb).max() <= 1e-5
     assert np.abs(ca - cb).max() <= 1e-5 * np.abs(ca).max()
     pr, _, cr, _ = orc.run(p, pos, sp, c0.astype(np.float64), nsteps=k)
     # k steps: per-step errors add up; allow k times the single-step tolerance
