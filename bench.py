@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--profile-steps", type=int, default=RUN_STEPS)
+    ap.add_argument("--no-adjoint", action="store_true")
     return ap.parse_args()
 
 
@@ -72,12 +73,26 @@ def workload_config(p, n):
 
 
 def measured_peaks():
+    """(HBM GB/s, its source, SM max MHz)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured", float(d.get("sm_max_mhz", 2070.0))
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, "fallback", 2070.0
+
+
+# FP32 operations of one in-cutoff pair interaction (Sect. 3.2 force): the
+# difference vector (3), r^2 (5), rsqrt, r, -r/eps, exp, minus the shift,
+# times inter/eps, times 1/r, the fixed-point scale, and the three components
+# (3): 20 operations, an FMA counted as 2.
+FLOP_PER_PAIR = 20.0
+# FP32 lanes of GB300: 152 SMs x 128 lanes, an FMA (2 flop) per lane per cycle.
+FP32_LANES = 152 * 128
+
+# DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
+# traffic field; None where the kernel changed after the capture.
+NCU_TRAFFIC_BYTES = {"k_step": None, "k_pde": None, "k_scan": None, "k_scatter": None}
 
 
 # ---------------------------------------------------------------------------
@@ -229,6 +244,46 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+def adjoint_ratio(chemo, wl, devc, stream):
+    """(forward + backward) / forward time of the differentiable workload:
+    forward = chemo_step_n of 200 steps; backward = chemo_record of the same
+    200 steps (checkpoints every 20) plus chemo_gradient."""
+    import torch
+    w = wl.WORKLOADS["adjoint_2d"]
+    p, pos, sp = wl.initial_state("adjoint_2d")
+    n, steps, every = pos.shape[0], w["steps"], w["ckpt_every"]
+    dpos = torch.from_numpy(pos).to(devc)
+    dsp = torch.from_numpy(sp).to(devc)
+    sim = chemo.chemo_create(p, dpos, dsp, stream=stream)
+    try:
+        g = torch.zeros((n, 2), dtype=torch.float32, device=devc)
+        g[:, 0] = 1.0 / n
+        dth = torch.zeros(2 + p["n_species"], dtype=torch.float32, device=devc)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        for rep in range(2):  # the first pass warms up graphs and allocations
+            chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+            chemo.chemo_set_step_index(sim, 0, stream=stream)
+            ev[0].record(stream)
+            chemo.chemo_step_n(sim, steps, stream=stream)
+            ev[1].record(stream)
+            chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+            chemo.chemo_set_step_index(sim, 0, stream=stream)
+            ev[2].record(stream)
+            chemo.chemo_record(sim, steps, every, stream=stream)
+            chemo.chemo_gradient(sim, g, dth, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+        fwd = ev[0].elapsed_time(ev[1])
+        both = ev[2].elapsed_time(ev[3])
+        return {"workload": "adjoint_2d: 2D walls, N=%d two species, %dx%d grid (%d PDE substeps), %d steps, "
+                            "checkpoints every %d, gradients wrt chi, inter, D_0, D_1"
+                            % (n, p["grid"][0], p["grid"][1], chemo.chemo_get_info(sim)["pde_substeps"], steps, every),
+                "forward_ms": fwd, "forward_backward_ms": both, "ratio": both / fwd,
+                "gradients_finite": bool(torch.isfinite(dth).all().item())}
+    finally:
+        sim.close()
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -286,13 +341,6 @@ def main():
             state["in_run"] += m
             k -= m
 
-    # pair interactions per step on the initial state (in-cutoff, directed)
-    cnt = torch.zeros(n, dtype=torch.int32, device=devc)
-    F = torch.zeros((n, 3), dtype=torch.float32, device=devc)
-    chemo.chemo_stage_forces(sim, F, cnt, None, stream=stream)
-    pairs_per_step = int(cnt.sum().item())
-    del F, cnt
-
     reset()
     advance(args.warmup)
     clocks = ClockSampler(local)
@@ -316,28 +364,34 @@ def main():
     value = n * args.steps * world / (ms_max * 1e-3)
     ms_per_step = ms_max / args.steps
 
-    # per-kernel device times (same kernels, streams and overlap as a step)
+    # per-kernel device times over one whole run (same kernels, streams and
+    # overlap as a step), and the in-cutoff pair interactions per step
     reset()
-    prof = chemo.chemo_profile_steps(sim, min(args.profile_steps, RUN_STEPS), stream=stream)
-    state["in_run"] = min(args.profile_steps, RUN_STEPS)
+    nprof = min(args.profile_steps, RUN_STEPS)
+    prof = chemo.chemo_profile_steps(sim, nprof, stream=stream)
+    state["in_run"] = nprof
     G = int(np.prod(p["grid"]))
     s = info["pde_substeps"]
-    hbm, peak_kind = measured_peaks()
-    bytes_per = {
-        # algorithmic bytes per launch: state read + write (16 + 16 B) and the
-        # bin slot (4 B) per cell; read + write of c per node per substep
-        "k_step": 36.0 * n,
-        "k_pde": 8.0 * G * s,
-        "k_scan": 8.0 * info["bin_slots"] + 4.0,
-        "k_scatter": 36.0 * n,
-    }
+    hbm, peak_kind, sm_mhz = measured_peaks()
+    fp32_peak = FP32_LANES * 2.0 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    pairs_per_step = prof["pairs_per_step"]
     kern = {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter")}
     dom = max(kern, key=kern.get)
-    achieved = bytes_per[dom] / (kern[dom] * 1e-3) / 1e9
-    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-                if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "traffic": None, "kernel_ms": kern, "step_ms_profiled": prof["step"]}
+    if dom == "k_step":
+        # the particle kernel is bound by the pair arithmetic, not by HBM
+        achieved = FLOP_PER_PAIR * pairs_per_step / (kern[dom] * 1e-3) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak,
+                    "peak_source": "FP32 lanes x 2 x SM max clock (%d x 2 x %.0f MHz)" % (FP32_LANES, sm_mhz)}
+    else:
+        bytes_per = {"k_pde": 8.0 * G * s, "k_scan": 36.0 * info["bin_slots"] / 8.0, "k_scatter": 36.0 * n}
+        achieved = bytes_per[dom] / (kern[dom] * 1e-3) / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                    "frac": achieved / hbm,
+                    "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                    else "fallback 6.8 TB/s"}
+    roofline.update({"traffic": NCU_TRAFFIC_BYTES.get(dom), "kernel_ms": kern, "step_ms_profiled": prof["step"],
+                     "profiled_steps": nprof, "pairs_per_step": pairs_per_step})
     floor_bytes = 42.0 * n + 8.0 * G * s
     step_floor = {"bytes_per_step": floor_bytes, "achieved_GBps": floor_bytes / (ms_per_step * 1e-3) / 1e9,
                   "frac": floor_bytes / (ms_per_step * 1e-3) / 1e9 / hbm}
@@ -375,6 +429,12 @@ def main():
                       "chemo_read_state to pinned host; the chemical grid stays on the device"}
     sim.close()
 
+    # adjoint / forward time of the differentiable workload (2D, 50k cells,
+    # 512^2 grid with 12 PDE substeps, 200 steps, checkpoints every 20)
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = adjoint_ratio(chemo, wl, devc, stream)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
@@ -392,7 +452,8 @@ def main():
             "roofline": roofline, "step_floor": step_floor, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(args.steps * per_step + resets_in * reset_launches),
             "clocks": clock_rec,
-            "pair_interactions_per_s": pairs_per_step / (ms_per_step * 1e-3),
+            "pair_interactions_per_s": pairs_per_step * world / (ms_per_step * 1e-3),
+            "adjoint": adjoint,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -164,15 +164,27 @@ int chemo_read_state(chemo_sim *sim, float *pos_out, uint8_t *species_out, float
 /* Copies the chemical field c^n out (grid_nodes float32, C-order). */
 int chemo_read_field(chemo_sim *sim, float *c_out, int mem_kind, void *stream);
 
-/* Vector-Jacobian product of nsteps steps (adjoint of chemo_step_n) with
- * checkpoints every ckpt_every steps: given dL/dpos of the final state (and
- * optionally dL/dc), returns dL/dparams = [chi, inter, D_0..D_{S-1}] and,
- * if dL_dpos0 is non-NULL, dL/dpos of the initial state. The forward noise
- * is frozen (same Philox counters). The simulation state is left at the
- * final step. Not available in this build: returns ENOTSUP. */
-int chemo_gradient(chemo_sim *sim, int64_t nsteps, int32_t ckpt_every, const float *dL_dpos_final,
-                   const float *dL_dc_final, float *dL_dparams, float *dL_dpos0, int mem_kind,
-                   void *stream);
+/* Records a run for the adjoint: advances nsteps steps exactly like
+ * chemo_step_n (same kernels, same Philox counters) while keeping checkpoints
+ * of the state and the field every `every` steps in library memory (replacing
+ * any earlier recording). The adjoint covers the model without type switching
+ * and without consumption, with Neumann or periodic fields: ENOTSUP
+ * otherwise. */
+int chemo_record(chemo_sim *sim, int64_t nsteps, int32_t every, void *stream);
+
+/* Vector-Jacobian product (adjoint) of the last recorded run: given
+ * dL/dpos of its final state (n x dim by id) and optionally dL/dc of its
+ * final field (grid_nodes, NULL = 0), returns dL_dparams = [dL/dchi,
+ * dL/dinter, dL/dD_0 .. dL/dD_{n_species-1}] and, if dL_dpos0 is non-NULL,
+ * dL/dpos of the recorded run's initial state. The noise is frozen (the same
+ * Philox counters as the forward run); each segment between checkpoints is
+ * re-run forward before its reverse sweep (Sect. 2 model: pair force Jacobian,
+ * interpolation Jacobian, reflection signs, deposit and PDE transposes). The
+ * cutoff jump and the reflection kinks are not differentiated (measure-zero
+ * events). The simulation is left at the final state of the recorded run.
+ * Synchronises `stream` when mem_kind is HOST. EINVAL if no run is recorded. */
+int chemo_gradient(chemo_sim *sim, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
+                   float *dL_dpos0, int mem_kind, void *stream);
 
 /* Replaces the model parameters of a live simulation. Geometry (dim, box,
  * grid, boundary, species count, bin layout) must not change: EINVAL. */
@@ -192,12 +204,13 @@ int chemo_check(chemo_sim *sim, void *stream);
 int chemo_get_info(const chemo_sim *sim, chemo_info *info);
 
 /* Measurement: advances nsteps steps exactly like chemo_step (same kernels,
- * same streams, the PDE still overlapped with the particle kernel), with a
- * CUDA event pair around every kernel on the stream it runs on. Returns in
- * kernel_ms[CHEMO_PROF_SLOTS] the mean device time per step of each kernel
- * class (particle step, PDE (all substeps), scan, scatter + deposit) and, in
- * the last slot, the mean time of a whole step. Synchronises `stream`. */
-#define CHEMO_PROF_SLOTS 5
+ * same streams and overlap), with a CUDA event pair around every kernel on
+ * the stream it runs on. Returns in kernel_ms[CHEMO_PROF_SLOTS]: the mean
+ * device time (ms) per step of the particle kernel, the PDE (all substeps),
+ * the scan, the scatter + deposit, and of a whole step; the last slot holds
+ * the mean number of in-cutoff pair interactions per step (each ordered
+ * pair counted once per cell). Synchronises `stream`. */
+#define CHEMO_PROF_SLOTS 6
 int chemo_profile_steps(chemo_sim *sim, int64_t nsteps, float *kernel_ms, void *stream);
 
 /* Releases every resource of sim (NULL is ignored). Synchronises the device

@@ -157,7 +157,8 @@ def _declare(L):
         "chemo_step_n": ([vp, i64, vp], ctypes.c_int),
         "chemo_read_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_read_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
-        "chemo_gradient": ([vp, i64, i32, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_record": ([vp, i64, i32, vp], ctypes.c_int),
+        "chemo_gradient": ([vp, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_set_params": ([vp, PP], ctypes.c_int),
         "chemo_step_index": ([vp], i64),
         "chemo_set_step_index": ([vp, i64, vp], ctypes.c_int),
@@ -315,14 +316,16 @@ def chemo_read_field(sim: Sim, c_out, stream=None):
     _check(lib().chemo_read_field(_h(sim), cp, k, _stream(stream)), "chemo_read_field")
 
 
-def chemo_gradient(sim: Sim, nsteps: int, ckpt_every: int, dL_dpos_final, dL_dc_final, dL_dparams, dL_dpos0=None,
-                   stream=None):
+def chemo_record(sim: Sim, nsteps: int, every: int, stream=None):
+    _check(lib().chemo_record(_h(sim), int(nsteps), int(every), _stream(stream)), "chemo_record")
+
+
+def chemo_gradient(sim: Sim, dL_dpos_final, dL_dparams, dL_dc_final=None, dL_dpos0=None, stream=None):
     a, k1, _a = _buf(dL_dpos_final, np.float32)
     b, k2, _b = _buf(dL_dc_final, np.float32)
     c, k3, _c = _buf(dL_dparams, np.float32)
     d, k4, _d = _buf(dL_dpos0, np.float32)
-    _check(lib().chemo_gradient(_h(sim), int(nsteps), int(ckpt_every), a, b, c, d, _kind(k1, k2, k3, k4),
-                                _stream(stream)), "chemo_gradient")
+    _check(lib().chemo_gradient(_h(sim), a, b, c, d, _kind(k1, k2, k3, k4), _stream(stream)), "chemo_gradient")
 
 
 def chemo_set_params(sim: Sim, params: dict):
@@ -350,12 +353,13 @@ def chemo_get_info(sim: Sim) -> dict:
             for name, _ in chemo_info._fields_}
 
 
-PROF_SLOTS = 5
-PROF_NAMES = ("k_step", "k_pde", "k_scan", "k_scatter", "step")
+PROF_SLOTS = 6
+PROF_NAMES = ("k_step", "k_pde", "k_scan", "k_scatter", "step", "pairs_per_step")
 
 
 def chemo_profile_steps(sim: Sim, nsteps: int, stream=None) -> dict:
-    """Mean device ms per step of each kernel class and of a whole step."""
+    """Mean device ms per step of each kernel class and of a whole step, and
+    the mean number of in-cutoff pair interactions per step."""
     out = (ctypes.c_float * PROF_SLOTS)()
     _check(lib().chemo_profile_steps(_h(sim), int(nsteps), out, _stream(stream)), "chemo_profile_steps")
     return {PROF_NAMES[i]: float(out[i]) for i in range(PROF_SLOTS)}

@@ -1,0 +1,571 @@
+// adjoint.cu -- recording and vector-Jacobian product (adjoint) of the
+// chemotaxis step (arXiv:1805.11007), for gradients of trajectory
+// observables with respect to chi, the interaction strength and the
+// diffusivities (parameter inference).
+//
+// One forward step maps (X^n, c^n) to (X^{n+1}, c^{n+1}):
+//   Y_i      = X_i + dt (F_i(X) + chi_s G(X_i; c^n)) + sqrt(2 D_s dt) xi_i
+//   X^{n+1}  = B(Y)                      (reflection or periodic wrap)
+//   c^{n+1}  = PDE substeps of c^n with the source S(X^{n+1})
+// with the noise xi frozen (the Philox counter is the step index). The
+// reverse sweep, for n = N-1 .. 0, given lambda_X = dL/dX^{n+1} and
+// lambda_c = dL/dc^{n+1}:
+//   1. PDE transpose: mu <- mu + dt_s (D_c Lap^T mu - gamma mu) per substep,
+//      accumulating lambda_S = sum over substeps of mu / s;
+//   2. deposit transpose: lambda_X_i += k_s dt/h^d sum_k lambda_S[k]/tau_k grad w_k(X^{n+1}_i);
+//   3. boundary: lambda_Y = J_B^T lambda_X (a sign per reflection);
+//   4. lambda_X^n = lambda_Y + dt chi_s (dG/dX)^T lambda_Y
+//                   + dt sum_j H_ij (lambda_Y_i - lambda_Y_j),
+//      H = f/r (I - d d^T) + f'(r) d d^T (pair force Jacobian, symmetric);
+//      lambda_c^n = mu^(0) + dt chi_s (dG/dc)^T lambda_Y (scatter to the nodes);
+//   5. parameters: dL/dchi += dt chemotactic_s G . lambda_Y,
+//      dL/dinter += dt (F/inter) . lambda_Y, dL/dD_s += sqrt(dt/(2 D_s)) xi . lambda_Y.
+// The cutoff jump and the reflection kinks are measure-zero events and are
+// not differentiated.
+//
+// Memory: checkpoints of (X, c) every `every` steps; each segment is re-run
+// forward to store its states before its reverse sweep.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "chemo_engine.h"
+
+using namespace chemo;
+
+namespace {
+
+constexpr int ATPB = 256;
+
+struct Tape {
+    int64_t n = 0, G = 0, nsteps = 0, every = 0, step0 = 0;
+    int nseg = 0, dim = 0, ns = 0;
+    std::vector<void *> allocs;
+    std::vector<float *> ck_pos, ck_c;  // checkpoints: positions by id (n x dim), field
+    uint8_t *species = nullptr;         // species by id
+    float *seg_pos = nullptr;           // (every + 1) x n x dim
+    float *seg_c = nullptr;             // every x G
+    float *lamX[2] = {nullptr, nullptr};  // n x dim by id
+    float *lamY = nullptr;              // n x dim by id
+    float *lamC[2] = {nullptr, nullptr};  // G
+    float *lamS = nullptr;              // G
+    float *F1 = nullptr;                // unit-strength pair force by id, n x dim
+    double *dpar = nullptr;             // 2 + MAXS accumulators
+};
+
+}  // namespace
+
+struct chemo_tape : Tape {};
+
+void chemo_tape_free(chemo_tape *t)
+{
+    if (!t) return;
+    for (void *p : t->allocs) cudaFree(p);
+    delete t;
+}
+
+namespace {
+
+int talloc(chemo_tape *t, void **p, size_t bytes)
+{
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return eng_fail(CHEMO_ENOMEM, "adjoint: cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    t->allocs.push_back(*p);
+    return CHEMO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Positions (n x dim) and species of the sorted state, by id.
+__global__ void k_gather_state(KP kp, float *__restrict__ pos, uint8_t *__restrict__ sp)
+{
+    const int64_t j = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    if (j >= kp.n) return;
+    const float4 u = kp.S[j];
+    const uint32_t w = __float_as_uint(u.w);
+    const int64_t id = w & ID_MASK;
+    if (id >= kp.n) return;
+    pos[id * kp.dim + 0] = u.x;
+    pos[id * kp.dim + 1] = u.y;
+    if (kp.dim == 3) pos[id * kp.dim + 2] = u.z;
+    if (sp) sp[id] = (uint8_t)(w >> SP_SHIFT);
+}
+
+// Transposed Laplacian along one axis at node k (N nodes, stride): with
+// mirror ghosts the wall rows are (-2, 2) so the transpose differs there.
+__device__ __forceinline__ float lapT_axis(const float *__restrict__ mu, int64_t g, int k, int N, int64_t stride,
+                                           bool periodic)
+{
+    const float m0 = mu[g];
+    if (periodic) {
+        const int64_t gl = k > 0 ? g - stride : g + (int64_t)(N - 1) * stride;
+        const int64_t gr = k < N - 1 ? g + stride : g - (int64_t)(N - 1) * stride;
+        return mu[gl] + mu[gr] - 2.f * m0;
+    }
+    const float left = k == 0 ? 0.f : (k == 1 ? 2.f * mu[g - stride] : mu[g - stride]);
+    const float right = k == N - 1 ? 0.f : (k == N - 2 ? 2.f * mu[g + stride] : mu[g + stride]);
+    return left + right - 2.f * m0;
+}
+
+// One transposed PDE substep: mu_out = mu_in + dt_s (D_c Lap^T - gamma) mu_in,
+// lamS (+)= mu_in / s.
+__global__ void k_adj_pde(KP kp, const float *__restrict__ mu_in, float *__restrict__ mu_out, float *__restrict__ lamS,
+                          float inv_s, int first)
+{
+    const int64_t g = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    if (g >= kp.G) return;
+    const int gx = kp.g[0], gy = kp.g[1];
+    const int x = (int)(g % gx);
+    const int y = (int)((g / gx) % gy);
+    const int z = kp.dim == 3 ? (int)(g / ((int64_t)gx * gy)) : 0;
+    const bool per = kp.pde_bc == 2;
+    float lap = lapT_axis(mu_in, g, x, gx, 1, per) * kp.inv_h2[0] + lapT_axis(mu_in, g, y, gy, gx, per) * kp.inv_h2[1];
+    if (kp.dim == 3) lap += lapT_axis(mu_in, g, z, kp.g[2], (int64_t)gx * gy, per) * kp.inv_h2[2];
+    const float m = mu_in[g];
+    mu_out[g] = m + kp.dts * (kp.Dc * lap - kp.gamma * m);
+    lamS[g] = (first ? 0.f : lamS[g]) + m * inv_s;
+}
+
+// Multilinear weights and their gradients at x: for each of the 2^d corners,
+// node indices, weight and d(weight)/dx_a.
+template <int DIM>
+__device__ __forceinline__ void corners(const KP &kp, const float *x, int node[8][3], float w[8], float dw[8][3])
+{
+    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < DIM; ++a) gcell(kp, a, x[a], k0[a], k1[a], f[a]);
+    for (int m = 0; m < (1 << DIM); ++m) {
+        float wt = 1.f;
+        for (int a = 0; a < 3; ++a) {
+            const int bit = (m >> a) & 1;
+            node[m][a] = a < DIM ? (bit ? k1[a] : k0[a]) : 0;
+            if (a < DIM) wt *= bit ? f[a] : 1.f - f[a];
+        }
+        w[m] = wt;
+        for (int b = 0; b < 3; ++b) {
+            float d = 0.f;
+            if (b < DIM) {
+                d = ((m >> b) & 1) ? kp.inv_h[b] : -kp.inv_h[b];
+                for (int a = 0; a < DIM; ++a)
+                    if (a != b) d *= ((m >> a) & 1) ? f[a] : 1.f - f[a];
+            }
+            dw[m][b] = d;
+        }
+    }
+}
+
+__device__ __forceinline__ int64_t nidx(const KP &kp, const int *k) { return gidx(kp, k[0], k[1], k[2]); }
+
+__device__ __forceinline__ void warp_add_double(double v, double *dst)
+{
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+}
+
+// Per-cell adjoint terms (by id). Reads X^n, X^{n+1}, c^n, lambda_X^{n+1},
+// lambda_S and the unit-strength pair force; writes lambda_Y and the local
+// part of lambda_X^n, scatters the interpolation transpose into lambda_c and
+// accumulates the parameter gradients.
+template <int DIM>
+__global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restrict__ Xn, const float *__restrict__ Xn1,
+                                                    const uint8_t *__restrict__ spec, const float *__restrict__ cn,
+                                                    const float *__restrict__ lamX1, const float *__restrict__ lamS,
+                                                    const float *__restrict__ F1, float *__restrict__ lamY,
+                                                    float *__restrict__ lamXn, float *__restrict__ lamC,
+                                                    unsigned long long step, double *dpar, int has_grid)
+{
+    const int64_t i = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    const bool valid = i < kp.n;
+    double d_chi = 0.0, d_int = 0.0, d_D[MAXS];
+    for (int s = 0; s < MAXS; ++s) d_D[s] = 0.0;
+    if (valid) {
+        const int sp = spec[i];
+        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < DIM; ++a) {
+            x0[a] = Xn[i * DIM + a];
+            x1[a] = Xn1[i * DIM + a];
+            lx[a] = lamX1[i * DIM + a];
+        }
+        // 2. deposit transpose at X^{n+1}
+        if (has_grid && kp.src[sp] != 0.f) {
+            int node[8][3];
+            float w[8], dw[8][3];
+            corners<DIM>(kp, x1, node, w, dw);
+            for (int m = 0; m < (1 << DIM); ++m) {
+                float inv_tau = 1.f;
+                if (kp.pde_bc != 2)
+                    for (int a = 0; a < DIM; ++a)
+                        if (node[m][a] == 0 || node[m][a] == kp.g[a] - 1) inv_tau *= 2.f;
+                const float l = lamS[nidx(kp, node[m])] * inv_tau * kp.src[sp];
+                for (int a = 0; a < DIM; ++a) lx[a] = fmaf(l, dw[m][a], lx[a]);
+            }
+        }
+        // forward quantities at X^n: gradient interpolation, noise, pre-boundary Y
+        const float chem = kp.chem[sp];
+        float G[3] = {0.f, 0.f, 0.f}, J[3][3] = {{0.f}};
+        int node[8][3];
+        float w[8], dw[8][3];
+        const bool interp = has_grid && kp.chem_mode == 0;
+        if (kp.chem_mode == 1) {
+            for (int a = 0; a < DIM; ++a) G[a] = kp.fixed_g[a];
+        } else if (interp) {
+            corners<DIM>(kp, x0, node, w, dw);
+            for (int m = 0; m < (1 << DIM); ++m)
+                for (int a = 0; a < DIM; ++a) {
+                    int kp1[3] = {node[m][0], node[m][1], node[m][2]}, km1[3] = {node[m][0], node[m][1], node[m][2]};
+                    kp1[a] = gnbr(kp, a, node[m][a] + 1);
+                    km1[a] = gnbr(kp, a, node[m][a] - 1);
+                    const float ga = (cn[nidx(kp, kp1)] - cn[nidx(kp, km1)]) * kp.inv_2h[a];
+                    G[a] = fmaf(w[m], ga, G[a]);
+                    for (int b = 0; b < DIM; ++b) J[a][b] = fmaf(dw[m][b], ga, J[a][b]);
+                }
+        }
+        const uint32_t id = (uint32_t)i;
+        const uint4 rw = cell_words(kp, id, step, TAG_MOVE);
+        const float2 n01 = box_muller(rw.x, rw.y);
+        const float xi[3] = {n01.x, n01.y, DIM == 3 ? box_muller(rw.z, rw.w).x : 0.f};
+        const float amp = kp.noise[sp];
+        float sgn[3] = {1.f, 1.f, 1.f};
+        for (int a = 0; a < DIM; ++a) {
+            const float Fa = kp.inter_f * F1[i * DIM + a];
+            float y = x0[a] + kp.dt * (Fa + chem * G[a]) + amp * xi[a];
+            if (!kp.periodic) {
+                for (int it = 0; it < 16 && (y < kp.lo[a] || y > kp.hi[a]); ++it) {
+                    y = y < kp.lo[a] ? 2.f * kp.lo[a] - y : 2.f * kp.hi[a] - y;
+                    sgn[a] = -sgn[a];
+                }
+            }
+        }
+        // 3. boundary, 4. local terms, 5. parameters
+        float ly[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < DIM; ++a) {
+            ly[a] = sgn[a] * lx[a];
+            lamY[i * DIM + a] = ly[a];
+        }
+        for (int b = 0; b < DIM; ++b) {
+            float t = ly[b];
+            if (interp && chem != 0.f) {
+                float s = 0.f;
+                for (int a = 0; a < DIM; ++a) s = fmaf(ly[a], J[a][b], s);
+                t = fmaf(kp.dt * chem, s, t);
+            }
+            lamXn[i * DIM + b] = t;
+        }
+        if (interp && chem != 0.f) {
+            for (int m = 0; m < (1 << DIM); ++m)
+                for (int a = 0; a < DIM; ++a) {
+                    const float coef = kp.dt * chem * w[m] * ly[a] * kp.inv_2h[a];
+                    if (coef == 0.f) continue;
+                    int kp1[3] = {node[m][0], node[m][1], node[m][2]}, km1[3] = {node[m][0], node[m][1], node[m][2]};
+                    kp1[a] = gnbr(kp, a, node[m][a] + 1);
+                    km1[a] = gnbr(kp, a, node[m][a] - 1);
+                    atomicAdd(&lamC[nidx(kp, kp1)], coef);
+                    atomicAdd(&lamC[nidx(kp, km1)], -coef);
+                }
+        }
+        double gl = 0.0, fl = 0.0, xl = 0.0;
+        for (int a = 0; a < DIM; ++a) {
+            gl += (double)G[a] * ly[a];
+            fl += (double)F1[i * DIM + a] * ly[a];
+            xl += (double)xi[a] * ly[a];
+        }
+        d_chi = (double)kp.dt * (double)kp.chemotactic_f[sp] * gl;
+        d_int = (double)kp.dt * fl;
+        if (amp > 0.f) d_D[sp] = (double)kp.dt / (double)amp * xl;  // d sqrt(2 D dt)/dD = dt / sqrt(2 D dt)
+    }
+    warp_add_double(d_chi, &dpar[0]);
+    warp_add_double(d_int, &dpar[1]);
+    for (int s = 0; s < kp.ns; ++s) warp_add_double(d_D[s], &dpar[2 + s]);
+}
+
+// Pair term of the adjoint over the cell list of X^n (sorted S):
+// lambda_X^n_i += dt sum_j H_ij (lambda_Y_i - lambda_Y_j).
+template <int DIM, bool PERIODIC>
+__global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restrict__ lamY, float *__restrict__ lamXn)
+{
+    const int64_t j = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    if (j >= kp.n) return;
+    const float4 me = kp.S[j];
+    const uint32_t w = __float_as_uint(me.w);
+    const int64_t id = w & ID_MASK;
+    if (id >= kp.n) return;
+    const int sp = (int)(w >> SP_SHIFT);
+    float li[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < DIM; ++a) li[a] = lamY[id * DIM + a];
+    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    const float pc[3] = {me.x, me.y, me.z};
+    for (int a = 0; a < DIM; ++a) {
+        c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+        const float f = __fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a];
+        if (kp.search == 2) {
+            lo[a] = f < 0.5f ? c[a] - 1 : c[a];
+            hi[a] = lo[a] + 1;
+        } else {
+            lo[a] = c[a] - 1;
+            hi[a] = c[a] + 1;
+        }
+        if (!PERIODIC) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], kp.nb[a] - 1);
+        }
+    }
+    float acc[3] = {0.f, 0.f, 0.f};
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        int zz = z;
+        if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            int yy = y;
+            if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                int xx = x;
+                if (PERIODIC) xx = x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x);
+                const uint32_t k = rowk + (uint32_t)xx;
+                const uint32_t q0 = bin_start(kp.cnt_cur, kp.gstart, k);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), (uint32_t)kp.n);
+                for (uint32_t q = q0; q < q1; ++q) {
+                    if (q == (uint32_t)j) continue;
+                    const float4 o = kp.S[q];
+                    float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
+                    if (PERIODIC)
+                        for (int a = 0; a < DIM; ++a) {
+                            if (d[a] > kp.halfL[a]) d[a] -= kp.L[a];
+                            else if (d[a] < -kp.halfL[a]) d[a] += kp.L[a];
+                        }
+                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                    const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+                    if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) continue;
+                    const int64_t jd = __float_as_uint(o.w) & ID_MASK;
+                    if (jd >= kp.n) continue;
+                    const float r = sqrtf(r2), rinv = 1.f / r;
+                    const float e = __expf(-r * kp.inv_eps[st]);
+                    const float f = kp.amp_f[st] * (e - kp.shift[st]);
+                    const float fp = -kp.amp_f[st] * kp.inv_eps[st] * e;
+                    float dl[3], dot = 0.f;
+                    for (int a = 0; a < DIM; ++a) {
+                        dl[a] = li[a] - lamY[jd * DIM + a];
+                        dot = fmaf(d[a] * rinv, dl[a], dot);
+                    }
+                    const float s1 = f * rinv, s2 = (fp - f * rinv) * dot;
+                    for (int a = 0; a < DIM; ++a) acc[a] += s1 * dl[a] + s2 * d[a] * rinv;
+                }
+            }
+        }
+    }
+    for (int a = 0; a < DIM; ++a) lamXn[id * DIM + a] += kp.dt * acc[a];
+}
+
+__global__ void k_params_out(const double *dpar, float *out, int np)
+{
+    const int i = threadIdx.x;
+    if (i < np) out[i] = (float)dpar[i];
+}
+
+unsigned blocks(int64_t n) { return (unsigned)((n + ATPB - 1) / ATPB); }
+
+#define ATRY(expr)                                                                                      \
+    do {                                                                                                \
+        cudaError_t e_ = (expr);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return eng_fail(CHEMO_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+int check_adjoint_model(const chemo_sim *s)
+{
+    const chemo_params &p = s->prm;
+    if (p.reactions) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover type switching (reactions = 1)");
+    for (int i = 0; i < p.n_species; ++i)
+        if (p.consume[i] != 0.f) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover consumption (consume != 0)");
+    if (p.chem_mode == 0 && p.pde_bc == 1) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover Dirichlet walls");
+    return CHEMO_OK;
+}
+
+// Current sorted state into (pos by id, species by id).
+int gather(chemo_sim *s, float *pos, uint8_t *sp, cudaStream_t st)
+{
+    if (s->kp.n == 0) return CHEMO_OK;
+    k_gather_state<<<blocks(s->kp.n), ATPB, 0, st>>>(eng_view(s), pos, sp);
+    ATRY(cudaGetLastError());
+    return CHEMO_OK;
+}
+
+float *cur_field(chemo_sim *s) { return s->kp.has_grid ? s->kp.c[s->cur] : nullptr; }
+
+}  // namespace
+
+extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *stream)
+{
+    if (!s || nsteps < 0 || every < 1) return eng_fail(CHEMO_EINVAL, "chemo_record: bad arguments");
+    if (int r = check_adjoint_model(s)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    chemo_tape_free(s->tape);
+    s->tape = new (std::nothrow) chemo_tape();
+    if (!s->tape) return eng_fail(CHEMO_ENOMEM, "host allocation failed");
+    chemo_tape *t = s->tape;
+    const KP &kp = s->kp;
+    t->n = kp.n;
+    t->G = kp.has_grid ? kp.G : 0;
+    t->nsteps = nsteps;
+    t->every = every;
+    t->step0 = s->step;
+    t->dim = kp.dim;
+    t->ns = kp.ns;
+    t->nseg = (int)((nsteps + every - 1) / every);
+    const size_t pb = (size_t)std::max<int64_t>(t->n, 1) * kp.dim * sizeof(float);
+    const size_t gb = (size_t)std::max<int64_t>(t->G, 1) * sizeof(float);
+    void *p;
+    int r;
+    for (int k = 0; k <= t->nseg; ++k) {
+        if ((r = talloc(t, &p, pb))) return r;
+        t->ck_pos.push_back((float *)p);
+        if ((r = talloc(t, &p, gb))) return r;
+        t->ck_c.push_back((float *)p);
+    }
+    if ((r = talloc(t, &p, (size_t)std::max<int64_t>(t->n, 1)))) return r;
+    t->species = (uint8_t *)p;
+    // forward with checkpoints at the start of every segment and at the end
+    for (int k = 0; k <= t->nseg; ++k) {
+        if ((r = gather(s, t->ck_pos[k], k == 0 ? t->species : nullptr, st))) return r;
+        if (t->G) ATRY(cudaMemcpyAsync(t->ck_c[k], cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
+        if (k == t->nseg) break;
+        const int64_t len = std::min<int64_t>(every, nsteps - (int64_t)k * every);
+        if ((r = chemo_step_n(s, len, stream))) return r;
+    }
+    return CHEMO_OK;
+}
+
+extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
+                              float *dL_dpos0, int mem_kind, void *stream)
+{
+    if (!s) return eng_fail(CHEMO_EINVAL, "sim is NULL");
+    chemo_tape *t = s->tape;
+    if (!t) return eng_fail(CHEMO_EINVAL, "chemo_gradient: no recorded run (call chemo_record first)");
+    if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE) return eng_fail(CHEMO_EINVAL, "bad mem_kind");
+    if (!dL_dpos_final || !dL_dparams) return eng_fail(CHEMO_EINVAL, "dL_dpos_final and dL_dparams are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int dim = t->dim;
+    const int64_t n = t->n, G = t->G;
+    const size_t pb = (size_t)std::max<int64_t>(n, 1) * dim * sizeof(float);
+    const size_t gb = (size_t)std::max<int64_t>(G, 1) * sizeof(float);
+    void *p;
+    int r;
+    if (!t->seg_pos) {
+        if ((r = talloc(t, &p, pb * (size_t)(t->every + 1)))) return r;
+        t->seg_pos = (float *)p;
+        if ((r = talloc(t, &p, gb * (size_t)t->every))) return r;
+        t->seg_c = (float *)p;
+        for (int k = 0; k < 2; ++k) {
+            if ((r = talloc(t, &p, pb))) return r;
+            t->lamX[k] = (float *)p;
+            if ((r = talloc(t, &p, gb))) return r;
+            t->lamC[k] = (float *)p;
+        }
+        if ((r = talloc(t, &p, pb))) return r;
+        t->lamY = (float *)p;
+        if ((r = talloc(t, &p, gb))) return r;
+        t->lamS = (float *)p;
+        if ((r = talloc(t, &p, pb))) return r;
+        t->F1 = (float *)p;
+        if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS)))) return r;
+        t->dpar = (double *)p;
+    }
+    const cudaMemcpyKind in_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    int lx = 0, lc = 0;
+    if (n) ATRY(cudaMemcpyAsync(t->lamX[lx], dL_dpos_final, (size_t)n * dim * sizeof(float), in_kind, st));
+    if (G) {
+        if (dL_dc_final) ATRY(cudaMemcpyAsync(t->lamC[lc], dL_dc_final, (size_t)G * sizeof(float), in_kind, st));
+        else ATRY(cudaMemsetAsync(t->lamC[lc], 0, gb, st));
+    }
+    ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS), st));
+    // unit-strength force tables (the pair force is linear in inter)
+    chemo_params unit = s->prm;
+    unit.inter = 1.f;
+    const int64_t end_step = s->step;
+    for (int seg = t->nseg - 1; seg >= 0; --seg) {
+        const int64_t n0 = (int64_t)seg * t->every;
+        const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
+        // restore the checkpoint and re-run the segment, storing its states
+        if ((r = eng_ingest(s, t->ck_pos[seg], t->species, nullptr, CHEMO_MEM_DEVICE, st))) return r;
+        if (G) ATRY(cudaMemcpyAsync(cur_field(s), t->ck_c[seg], gb, cudaMemcpyDeviceToDevice, st));
+        if ((r = chemo_set_step_index(s, t->step0 + n0, stream))) return r;
+        for (int64_t k = 0; k < len; ++k) {
+            if ((r = gather(s, t->seg_pos + (size_t)k * n * dim, nullptr, st))) return r;
+            if (G) ATRY(cudaMemcpyAsync(t->seg_c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
+            if ((r = eng_enqueue_step(s, st, nullptr))) return r;
+        }
+        if ((r = gather(s, t->seg_pos + (size_t)len * n * dim, nullptr, st))) return r;
+        // reverse sweep over the segment
+        for (int64_t k = len - 1; k >= 0; --k) {
+            const unsigned long long step = (unsigned long long)(t->step0 + n0 + k);
+            const float *Xn = t->seg_pos + (size_t)k * n * dim;
+            const float *Xn1 = t->seg_pos + (size_t)(k + 1) * n * dim;
+            const float *cn = G ? t->seg_c + (size_t)k * G : nullptr;
+            KP kp = eng_view(s);
+            // 1. PDE transpose (substeps), lambda_S
+            if (G) {
+                const int ss = kp.substeps;
+                for (int m = 0; m < ss; ++m) {
+                    k_adj_pde<<<blocks(G), ATPB, 0, st>>>(kp, t->lamC[lc], t->lamC[lc ^ 1], t->lamS, 1.f / ss, m == 0);
+                    ATRY(cudaGetLastError());
+                    lc ^= 1;
+                }
+            }
+            // cell list of X^n and its unit-strength pair force
+            if ((r = eng_ingest(s, Xn, t->species, nullptr, CHEMO_MEM_DEVICE, st))) return r;
+            kp = eng_view(s);
+            KP ku = kp;
+            eng_fill_model(unit, ku);
+            if (n) ATRY(launch_stage_forces(ku, t->F1, nullptr, nullptr, st));
+            // 2-5. per-cell terms, then the pair term
+            kp.inter_f = s->prm.inter;
+            if (n) {
+                if (dim == 2)
+                    k_adj_cells<2><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, t->F1,
+                                                             t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
+                                                             G ? 1 : 0);
+                else
+                    k_adj_cells<3><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, t->F1,
+                                                             t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
+                                                             G ? 1 : 0);
+                ATRY(cudaGetLastError());
+                if (kp.pairs) {
+                    if (dim == 2) {
+                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<2, false><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                    } else {
+                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<3, false><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                    }
+                    ATRY(cudaGetLastError());
+                }
+            }
+            lx ^= 1;
+        }
+    }
+    // outputs
+    const int np = 2 + t->ns;
+    float *dpf;
+    if ((r = talloc(t, &p, sizeof(float) * 16))) return r;
+    dpf = (float *)p;
+    k_params_out<<<1, 32, 0, st>>>(t->dpar, dpf, np);
+    ATRY(cudaGetLastError());
+    const cudaMemcpyKind out_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    ATRY(cudaMemcpyAsync(dL_dparams, dpf, sizeof(float) * np, out_kind, st));
+    if (dL_dpos0 && n) ATRY(cudaMemcpyAsync(dL_dpos0, t->lamX[lx], (size_t)n * dim * sizeof(float), out_kind, st));
+    // leave the simulation at the final state of the recorded run
+    if ((r = eng_ingest(s, t->ck_pos[t->nseg], t->species, nullptr, CHEMO_MEM_DEVICE, st))) return r;
+    if (G) ATRY(cudaMemcpyAsync(cur_field(s), t->ck_c[t->nseg], gb, cudaMemcpyDeviceToDevice, st));
+    if ((r = chemo_set_step_index(s, end_step, stream))) return r;
+    if (mem_kind == CHEMO_MEM_HOST) ATRY(cudaStreamSynchronize(st));
+    return CHEMO_OK;
+}

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/chemo.h"
+#include "chemo_engine.h"
 #include "chemo_internal.cuh"
 
 using namespace chemo;
@@ -43,23 +44,6 @@ __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v;
 
 }  // namespace
 
-struct chemo_sim {
-    chemo_params prm{};
-    KP kp{};
-    uint32_t *cnt8[2] = {nullptr, nullptr};  // packed bin counts, double buffered
-    int cntp = 0;                // cnt8[cntp] describes the sorted state
-    int cur = 0;                 // c[cur] holds c^n
-    int64_t step = 0;            // host mirror of the next step index
-    int launches_per_step = 0;
-    cudaStream_t aux = nullptr;  // second stream for the PDE
-    cudaStream_t cap = nullptr;  // capture stream for graphs
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    cudaGraphExec_t graph[2][2][2] = {};  // [2-step, 16-step][grid parity][count parity]
-    std::vector<void *> allocs;
-    int64_t bytes = 0;
-    void *scratch = nullptr;     // staging for host transfers and stage outputs
-    size_t scratch_bytes = 0;
-};
 
 namespace {
 
@@ -203,6 +187,7 @@ void fill_model(const chemo_params &p, KP &kp)
         const bool in = s < p.n_species;
         kp.noise[s] = in ? (float)std::sqrt(2.0 * (double)p.D[s] * p.dt) : 0.f;
         kp.chem[s] = in ? p.chi * p.chemotactic[s] : 0.f;
+        kp.chemotactic_f[s] = in ? p.chemotactic[s] : 0.f;
         kp.src[s] = in ? (float)((double)p.secrete[s] * p.dt / hd) : 0.f;
         kp.cons[s] = in ? (float)((double)p.consume[s] / hd) : 0.f;
         kp.rk0[s] = in ? p.react_k0[s] : 0.f;
@@ -227,6 +212,7 @@ void fill_model(const chemo_params &p, KP &kp)
     if (!(fmax > 0.0)) fmax = 1.0;
     kp.fq = (float)std::ldexp(fmax, -25);
     kp.fq_inv = (float)(1.0 / (double)kp.fq);
+    kp.inter_f = p.inter;
     kp.reactions = p.reactions ? 1 : 0;
     kp.dt = (float)p.dt;
     kp.dt_d = p.dt;
@@ -480,6 +466,24 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
 
 }  // namespace
 
+int eng_fail(int status, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+    return status;
+}
+int eng_dalloc(chemo_sim *s, void **p, size_t bytes) { return dalloc(s, p, bytes); }
+KP eng_view(const chemo_sim *s) { return view(s); }
+int eng_enqueue_step(chemo_sim *s, cudaStream_t st, int *launches) { return enqueue_step(s, st, launches); }
+int eng_ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp, int mem_kind, cudaStream_t st)
+{
+    return ingest(s, pos, sp, disp, mem_kind, st);
+}
+void eng_drop_graphs(chemo_sim *s) { drop_graphs(s); }
+void eng_fill_model(const chemo_params &p, KP &kp) { fill_model(p, kp); }
+
 // Parameter block of a particle set that is binned and searched only
 // (no grid, no buffers): validation, cell-list layout and model constants.
 int chemo_internal_build_kp(const chemo_params *params, int64_t n, KP *out)
@@ -524,6 +528,7 @@ void chemo_destroy(chemo_sim *s)
     if (!s) return;
     cudaDeviceSynchronize();
     drop_graphs(s);
+    chemo_tape_free(s->tape);
     for (void *p : s->allocs) cudaFree(p);
     if (s->scratch) cudaFree(s->scratch);
     if (s->aux) cudaStreamDestroy(s->aux);
@@ -586,6 +591,7 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     kp.scan_seq = ctl + 1;
     kp.err = ctl + 2;
     kp.step = reinterpret_cast<unsigned long long *>(ctl + 4);
+    kp.pair_count = nullptr;  // set only while profiling (ctl + 8)
     kp.c[0] = kp.c[1] = nullptr;
     kp.srcg = kp.Rg = nullptr;
     if (kp.has_grid) {
@@ -742,14 +748,6 @@ int chemo_read_field(chemo_sim *s, float *c_out, int mem_kind, void *stream)
     return CHEMO_OK;
 }
 
-int chemo_gradient(chemo_sim *s, int64_t nsteps, int32_t ckpt_every, const float *dL_dpos_final,
-                   const float *dL_dc_final, float *dL_dparams, float *dL_dpos0, int mem_kind, void *stream)
-{
-    (void)s; (void)nsteps; (void)ckpt_every; (void)dL_dpos_final; (void)dL_dc_final;
-    (void)dL_dparams; (void)dL_dpos0; (void)mem_kind; (void)stream;
-    return fail(CHEMO_ENOTSUP, "chemo_gradient (adjoint) is not available in this build");
-}
-
 int chemo_set_params(chemo_sim *s, const chemo_params *p)
 {
     g_last_error[0] = 0;
@@ -770,6 +768,8 @@ int chemo_set_params(chemo_sim *s, const chemo_params *p)
     fill_model(*p, s->kp);
     s->prm = *p;
     drop_graphs(s);  // graphs hold the old constants
+    chemo_tape_free(s->tape);  // a recorded run belongs to the old parameters
+    s->tape = nullptr;
     return CHEMO_OK;
 }
 
@@ -825,6 +825,9 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     const bool grid = s->kp.has_grid && s->kp.chem_mode == 0;
     const bool overlap = grid && s->kp.overlap;
     const bool fused = grid && s->kp.fused_deposit;
+    // in-cutoff pairs are counted into ctl + 8 while profiling
+    unsigned long long *pc = reinterpret_cast<unsigned long long *>(s->kp.tile_ctr + 8);
+    CUDA_TRY(cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
     // event pairs per step: particle, pde, scan, scatter, whole step
     std::vector<cudaEvent_t> ev((size_t)nsteps * 10, nullptr);
     for (auto &e : ev)
@@ -835,7 +838,8 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         }
     int r = CHEMO_OK;
     for (int64_t k = 0; k < nsteps && r == CHEMO_OK; ++k) {
-        const KP kp = view(s);
+        KP kp = view(s);
+        kp.pair_count = pc;
         cudaEvent_t *e = &ev[(size_t)k * 10];
         cudaError_t err = cudaEventRecord(e[8], st);
         if (fused && !overlap) {
@@ -876,17 +880,20 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         if (err != cudaSuccess) r = fail(CHEMO_ECUDA, "profile sync: %s", cudaGetErrorString(err));
     }
     if (r == CHEMO_OK) {
-        double acc[CHEMO_PROF_SLOTS] = {0, 0, 0, 0, 0};
-        const int pairs[CHEMO_PROF_SLOTS][2] = {{0, 1}, {2, 3}, {4, 5}, {5, 6}, {8, 9}};
+        double acc[5] = {0, 0, 0, 0, 0};
+        const int pairs[5][2] = {{0, 1}, {2, 3}, {4, 5}, {5, 6}, {8, 9}};
         for (int64_t k = 0; k < nsteps; ++k) {
             cudaEvent_t *e = &ev[(size_t)k * 10];
-            for (int q = 0; q < CHEMO_PROF_SLOTS; ++q) {
+            for (int q = 0; q < 5; ++q) {
                 if (q == 1 && !grid) continue;
                 float ms = 0.f;
                 if (cudaEventElapsedTime(&ms, e[pairs[q][0]], e[pairs[q][1]]) == cudaSuccess) acc[q] += ms;
             }
         }
-        for (int q = 0; q < CHEMO_PROF_SLOTS; ++q) kernel_ms[q] = (float)(acc[q] / (double)nsteps);
+        for (int q = 0; q < 5; ++q) kernel_ms[q] = (float)(acc[q] / (double)nsteps);
+        unsigned long long npairs = 0;
+        if (cudaMemcpy(&npairs, pc, sizeof(npairs), cudaMemcpyDeviceToHost) == cudaSuccess)
+            kernel_ms[5] = (float)((double)npairs / (double)nsteps);
     }
     for (auto &x : ev) cudaEventDestroy(x);
     return r;

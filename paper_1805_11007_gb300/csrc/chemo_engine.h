@@ -1,0 +1,46 @@
+// chemo_engine.h -- the simulation object shared by the engine translation
+// units (chemo_capi.cu: forward; adjoint.cu: recording and adjoint). Not part
+// of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "../../include/chemo.h"
+#include "chemo_internal.cuh"
+
+using chemo::KP;
+
+struct chemo_tape;  // recorded run (adjoint.cu)
+
+struct chemo_sim {
+    chemo_params prm{};
+    KP kp{};
+    uint32_t *cnt8[2] = {nullptr, nullptr};  // packed bin counts, double buffered
+    int cntp = 0;                // cnt8[cntp] describes the sorted state
+    int cur = 0;                 // c[cur] holds c^n
+    int64_t step = 0;            // host mirror of the next step index
+    int launches_per_step = 0;
+    cudaStream_t aux = nullptr;  // second stream for the PDE
+    cudaStream_t cap = nullptr;  // capture stream for graphs
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaGraphExec_t graph[2][2][2] = {};  // [2-step, 16-step][grid parity][count parity]
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    void *scratch = nullptr;     // staging for host transfers and stage outputs
+    size_t scratch_bytes = 0;
+    chemo_tape *tape = nullptr;  // recorded run for the adjoint (adjoint.cu)
+};
+
+// Engine services used by adjoint.cu (implemented in chemo_capi.cu).
+int eng_fail(int status, const char *fmt, ...);
+int eng_dalloc(chemo_sim *s, void **p, size_t bytes);
+KP eng_view(const chemo_sim *s);
+int eng_enqueue_step(chemo_sim *s, cudaStream_t st, int *launches);
+int eng_ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp, int mem_kind, cudaStream_t st);
+void eng_drop_graphs(chemo_sim *s);
+// Model constants of params into kp (species tables, noise, ...).
+void eng_fill_model(const chemo_params &p, KP &kp);
+// Releases a recorded run (adjoint.cu).
+void chemo_tape_free(chemo_tape *t);

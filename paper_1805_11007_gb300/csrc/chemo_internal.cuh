@@ -48,6 +48,8 @@ struct KP {
     float rsp2[MAXS];            // squared search radius of each species (max cutoff, small margin)
     float noise[MAXS];           // sqrt(2 D_s dt)
     float chem[MAXS];            // chi * chemotactic_s
+    float chemotactic_f[MAXS];   // chemotactic_s (the multiplier of chi)
+    float inter_f;               // interaction strength
     float src[MAXS];             // k_s dt / h^d
     float cons[MAXS];            // kappa_s / h^d
     float rk0[MAXS], rkc[MAXS];  // switching rates
@@ -85,6 +87,7 @@ struct KP {
     float *srcg, *Rg;            // source and consumption grids (substeps > 1)
     uint32_t *err;               // latched error bits
     unsigned long long *step;    // absolute index of the step being computed
+    unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
 };
 
 // ---------------------------------------------------------------------------

@@ -232,10 +232,8 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                 const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
                 if (r2 < rc2 && r2 > 0.f && qq != self) {
                     lst[nl++ * TPB] = qq;
-                    if (STATS) {
-                        count += 1;
-                        idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
-                    }
+                    count += 1;
+                    if (STATS) idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
                 }
                 o = on;
             }
@@ -382,12 +380,16 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     const uint32_t id = w & ID_MASK;
     int sp = (int)(w >> SP_SHIFT);
 
-    int cnt_unused = 0;
+    int npairs = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
     if (kp.pairs)  // warp-synchronous: every lane takes part
-        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, cnt_unused, ids_unused,
+        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused,
                                              smem + sizeof(SmemTables));
+    if (kp.pair_count) {  // profiling only: in-cutoff pairs of this step
+        const int wsum = __reduce_add_sync(0xffffffffu, npairs);
+        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
+    }
     if (!valid) return;
     const unsigned long long step = *kp.step;
 

@@ -97,6 +97,8 @@ def test_struct_size_mismatch_rejected(chemo):
     assert "struct_size" in chemo.chemo_last_error()
 
 
-def test_gradient_reports_not_supported_without_device(chemo):
-    st = chemo.lib().chemo_gradient(None, 1, 1, None, None, None, None, 0, None)
-    assert st == chemo.ENOTSUP
+def test_gradient_needs_a_simulation(chemo):
+    st = chemo.lib().chemo_gradient(None, None, None, None, None, 0, None)
+    assert st == chemo.EINVAL
+    st = chemo.lib().chemo_record(None, 1, 1, None)
+    assert st == chemo.EINVAL

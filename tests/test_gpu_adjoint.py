@@ -1,0 +1,107 @@
+"""The adjoint (chemo_record + chemo_gradient, through torch.autograd)
+against FP64 central finite differences of the oracle, with the noise frozen
+(same Philox counters): gradients of the differentiable workload's loss
+(mean x-displacement + mean squared soft occupancy) with respect to chi, the
+interaction strength and the diffusivities, and with respect to initial
+positions."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import chemo_oracle as orc
+from paper_1805_11007_gb300 import adjoint as adj
+from paper_1805_11007_gb300 import chemo
+from paper_1805_11007_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+NB = 12  # analysis grid of the occupancy loss
+
+
+def _setup(n=1500, grid=33, **over):
+    p = wl.params("adjoint_2d", grid=[grid, grid, 1], **over)
+    pos = wl.uniform_positions(n, 2, p["lo"], p["hi"], seed=21)
+    sp = wl.half_species(n, 2)
+    c0 = wl.random_field(p, seed=22, scale=0.3) if p["chem_mode"] == 0 else None
+    return p, pos, sp, c0
+
+
+def _gpu_grads(p, pos, sp, c0, nsteps, every):
+    dpos = torch.from_numpy(pos).cuda()
+    dsp = torch.from_numpy(sp).cuda()
+    dc0 = torch.from_numpy(c0).cuda() if c0 is not None else None
+    sim = chemo.chemo_create(p, dpos, dsp)
+    try:
+        theta = torch.tensor(adj.theta_of(p), dtype=torch.float64, requires_grad=True)
+        x0 = dpos.clone().requires_grad_(True)
+        xN = adj.ChemoRun.apply(theta, x0, sim, nsteps, every, dsp, dc0)
+        L = adj.mean_x_displacement(xN, x0) + adj.occupancy_loss(xN, NB, p["lo"], p["hi"])
+        L.backward()
+        return float(L.item()), theta.grad.numpy().copy(), x0.grad.cpu().numpy().astype(np.float64)
+    finally:
+        sim.close()
+
+
+def _oracle_loss(p, pos, sp, c0, nsteps, theta=None, pos0=None):
+    q = adj.with_theta(p, theta) if theta is not None else p
+    x0 = pos if pos0 is None else pos0
+    xN, _, _, _ = orc.run(q, x0, sp, None if c0 is None else c0.astype(np.float64), nsteps=nsteps)
+    return adj.loss_numpy(xN, x0, NB, p["lo"], p["hi"])
+
+
+@pytest.mark.parametrize("over", [dict(), dict(chem_mode=1, fixed_grad=[3.0, -2.0, 0.0], boundary=1, pde_bc=2,
+                                               diameter=[0.01, 0.02])])
+def test_parameter_gradients_match_oracle_finite_differences(over):
+    p, pos, sp, c0 = _setup(**over)
+    nsteps, every = 20, 5
+    L_gpu, g, _ = _gpu_grads(p, pos, sp, c0, nsteps, every)
+    L_orc = _oracle_loss(p, pos, sp, c0, nsteps)
+    assert abs(L_gpu - L_orc) <= 1e-4 * abs(L_orc)
+    theta = np.array(adj.theta_of(p))
+    h = 1e-4
+    fd = np.zeros_like(theta)
+    for k in range(theta.size):
+        tp = theta.copy(); tp[k] += h
+        tm = theta.copy(); tm[k] -= h
+        fd[k] = (_oracle_loss(p, pos, sp, c0, nsteps, tp) - _oracle_loss(p, pos, sp, c0, nsteps, tm)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    err = np.abs(g - fd)
+    assert np.all(err <= 0.03 * np.abs(fd) + 0.01 * scale), (g, fd)
+
+
+def test_initial_position_gradient_matches_oracle_finite_differences():
+    p, pos, sp, c0 = _setup(n=800)
+    nsteps, every = 12, 4
+    _, _, gx = _gpu_grads(p, pos, sp, c0, nsteps, every)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(pos.shape[0], size=6, replace=False)
+    h = 1e-5
+    for i in pick:
+        for a in range(2):
+            xp = pos.astype(np.float64).copy(); xp[i, a] += h
+            xm = pos.astype(np.float64).copy(); xm[i, a] -= h
+            fd = (_oracle_loss(p, pos, sp, c0, nsteps, pos0=xp) - _oracle_loss(p, pos, sp, c0, nsteps, pos0=xm)) / (2 * h)
+            assert abs(gx[i, a] - fd) <= 0.03 * abs(fd) + 2e-3 * np.abs(gx).max(), (i, a, gx[i, a], fd)
+
+
+def test_record_leaves_final_state_and_gradient_restores_it():
+    p, pos, sp, c0 = _setup(n=1000)
+    dpos = torch.from_numpy(pos).cuda()
+    dsp = torch.from_numpy(sp).cuda()
+    with chemo.chemo_create(p, dpos, dsp) as a, chemo.chemo_create(p, dpos, dsp) as b:
+        chemo.chemo_write_field(a, torch.from_numpy(c0).cuda())
+        chemo.chemo_write_field(b, torch.from_numpy(c0).cuda())
+        chemo.chemo_record(a, 10, 3)
+        chemo.chemo_step_n(b, 10)
+        pa, _, _ = chemo.read_state_host(a)
+        pb, _, _ = chemo.read_state_host(b)
+        assert np.abs(pa - pb).max() <= 1e-5
+        g = torch.zeros((1000, 2), dtype=torch.float32, device="cuda")
+        g[:, 0] = 1.0 / 1000
+        dth = torch.zeros(4, dtype=torch.float32, device="cuda")
+        chemo.chemo_gradient(a, g, dth)
+        pa2, _, _ = chemo.read_state_host(a)
+        np.testing.assert_array_equal(pa2, pa)
+        assert chemo.chemo_step_index(a) == 10
+        assert torch.isfinite(dth).all()
