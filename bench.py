@@ -92,7 +92,7 @@ FP32_LANES = 152 * 128
 
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
 # traffic field; None where the kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": None, "k_pde": None, "k_scan": None, "k_scatter": None}
+NCU_TRAFFIC_BYTES = {"k_step": 61.93e6, "k_pde": 93.65e6, "k_scan": 38.20e6, "k_scatter": 45.05e6}
 
 
 # ---------------------------------------------------------------------------
@@ -259,14 +259,17 @@ def adjoint_ratio(chemo, wl, devc, stream):
         g = torch.zeros((n, 2), dtype=torch.float32, device=devc)
         g[:, 0] = 1.0 / n
         dth = torch.zeros(2 + p["n_species"], dtype=torch.float32, device=devc)
+        c0 = torch.zeros(tuple(chemo.grid_shape(p)), dtype=torch.float32, device=devc)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         for rep in range(2):  # the first pass warms up graphs and allocations
             chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+            chemo.chemo_write_field(sim, c0, stream=stream)
             chemo.chemo_set_step_index(sim, 0, stream=stream)
             ev[0].record(stream)
             chemo.chemo_step_n(sim, steps, stream=stream)
             ev[1].record(stream)
             chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+            chemo.chemo_write_field(sim, c0, stream=stream)
             chemo.chemo_set_step_index(sim, 0, stream=stream)
             ev[2].record(stream)
             chemo.chemo_record(sim, steps, every, stream=stream)
