@@ -54,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-steps", type=int, default=RUN_STEPS)
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     return ap.parse_args()
 
 
@@ -287,6 +288,81 @@ def adjoint_ratio(chemo, wl, devc, stream):
         sim.close()
 
 
+def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500, serial_reps=16, serial_steps=100):
+    """The 256-replicate ensemble (2D walls physics, sizes log-uniform in
+    [1e3, 6.4e4], 128^2 grid each) advanced as one batched simulation per
+    rank (replicates sharded across ranks by particle count), against the
+    same replicates run one simulation at a time."""
+    import numpy as np
+    import torch
+    from paper_1805_11007_gb300 import ensemble as en
+    p, sizes, pos, sp = wl.ensemble_state()
+    mine = en.shard_replicates(sizes, world)[rank]
+    s_m, pos_m, sp_m = en.take(pos, sp, sizes, mine)
+    dpos = torch.from_numpy(pos_m).to(devc)
+    dsp = torch.from_numpy(sp_m).to(devc)
+    sim = chemo.chemo_create_batch(p, s_m, dpos, dsp, stream=stream)
+    c0 = torch.zeros((len(s_m),) + tuple(chemo.grid_shape(p)), dtype=torch.float32, device=devc)
+
+    def reset():
+        chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+        chemo.chemo_write_field(sim, c0, stream=stream)
+        chemo.chemo_set_step_index(sim, 0, stream=stream)
+
+    try:
+        reset()
+        chemo.chemo_step_n(sim, 20, stream=stream)
+        reset()
+        barrier()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        chemo.chemo_step_n(sim, steps, stream=stream)
+        ev[1].record(stream)
+        barrier()
+        chemo.chemo_check(sim, stream=stream)
+        t = torch.tensor([ev[0].elapsed_time(ev[1])], dtype=torch.float64, device=devc)
+        if dist is not None:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        reset()
+        prof = chemo.chemo_profile_steps(sim, 50, stream=stream)
+        info = chemo.chemo_get_info(sim)
+    finally:
+        sim.close()
+    out = {"workload": "ensemble_2d: %d replicates of the 2D walls physics, N_r log-uniform in [1e3, 6.4e4] "
+                       "(sum %d), %dx%d grid each (%d PDE substep), %d steps, one batched simulation per GPU"
+                       % (len(sizes), int(sizes.sum()), p["grid"][0], p["grid"][1], info["pde_substeps"], steps),
+           "value": float(sizes.sum()) * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "launches_per_step": info["launches_per_step"],
+           "kernel_ms": {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")}}
+    if rank == 0:
+        # the same replicates one simulation at a time (each with its own
+        # CUDA graphs), for the batching gain
+        reps = mine[:serial_reps]
+        sims = []
+        try:
+            for r in reps:
+                s1, p1, q1 = en.take(pos, sp, sizes, [r])
+                sims.append((chemo.chemo_create(wl.replicate_params(p, r), torch.from_numpy(p1).to(devc),
+                                                torch.from_numpy(q1).to(devc), stream=stream), int(s1[0])))
+            for sm, _ in sims:
+                chemo.chemo_step_n(sm, 4, stream=stream)
+            torch.cuda.synchronize()
+            ev[2].record(stream)
+            for sm, _ in sims:
+                chemo.chemo_step_n(sm, serial_steps, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            ms1 = ev[2].elapsed_time(ev[3])
+            psteps = sum(m for _, m in sims) * serial_steps
+            out["one_at_a_time"] = {"value": psteps / (ms1 * 1e-3), "unit": UNIT, "replicates": len(sims),
+                                    "steps": serial_steps, "ms_per_replicate_step": ms1 / (len(sims) * serial_steps)}
+        finally:
+            for sm, _ in sims:
+                sm.close()
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -432,6 +508,10 @@ def main():
                       "chemo_read_state to pinned host; the chemical grid stays on the device"}
     sim.close()
 
+    ensemble = None
+    if not args.no_ensemble:
+        ensemble = ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier)
+
     # adjoint / forward time of the differentiable workload (2D, 50k cells,
     # 512^2 grid with 12 PDE substeps, 200 steps, checkpoints every 20)
     adjoint = None
@@ -457,6 +537,7 @@ def main():
             "clocks": clock_rec,
             "pair_interactions_per_s": pairs_per_step * world / (ms_per_step * 1e-3),
             "adjoint": adjoint,
+            "ensemble": ensemble,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -122,6 +122,8 @@ typedef struct chemo_info {
     int64_t grid_nodes;
     int64_t device_bytes;        /* device memory held by the simulation */
     int32_t launches_per_step;   /* kernels one chemo_step launches */
+    int32_t layers;              /* replicates stacked in the simulation (1 unless
+                                    created by chemo_create_batch) */
 } chemo_info;
 
 typedef struct chemo_sim chemo_sim;
@@ -136,6 +138,40 @@ typedef struct chemo_sim chemo_sim;
  * 2^29 particles...), ENOMEM, ECUDA. */
 int chemo_create(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species,
                  int mem_kind, void *stream, chemo_sim **out);
+
+/* Creates an ensemble of `replicates` independent 2D simulations of the same
+ * model in one object (the realisations over which the paper averages its
+ * statistics, Sect. 4, Fig. 1): replicate r holds n_per_replicate[r] cells
+ * (any sizes, 0 allowed), its own copy of the grid, and the Philox key
+ * params->seed + r; its cells are ids 0..n_r-1 of that replicate, so replicate
+ * r evolves exactly like a chemo_create simulation of its own cells with seed
+ * params->seed + r (bitwise for the particles; the field's float atomics may
+ * round differently). Caller arrays are the replicates' arrays concatenated in
+ * replicate order: pos (sum n_r) x 2, species (sum n_r); grids are
+ * replicates x grid[1] x grid[0] (C-order). One chemo_step advances every
+ * replicate with the same number of launches as a single simulation.
+ * n_per_replicate is host memory. Every other call (write/read state and
+ * field, step, step_n, check, stage calls) works on the concatenated arrays;
+ * chemo_record / chemo_gradient return ENOTSUP for replicates > 1.
+ * Errors: EINVAL (dim != 2 with replicates > 1, replicates < 1 or > 65535, a
+ * negative size, more than 2^29 cells in total, the checks of chemo_create),
+ * ENOMEM, ECUDA. */
+int chemo_create_batch(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
+                       const float *pos, const uint8_t *species, int mem_kind, void *stream, chemo_sim **out);
+
+/* Autotuner of the cell list and launch sequence (no counterpart in the
+ * paper, which leaves the bin size to the user, Sect. 3.1). Times
+ * `trial_steps` steps (after 4 warm-up steps) of the given (batched) particle
+ * set for each candidate: search_mode 1 (3^d bins, side r_c x {1, 1.25, 1.5,
+ * 2}) and 2 (2^d bins, side 2 r_c x {1, 1.25}), then the PDE overlap on and
+ * off for the best; the results do not depend on the choice. *best_out
+ * receives params with bin_side, search_mode and pde_overlap set to the
+ * fastest candidate, *best_ms_out (if non-NULL) its device time per step.
+ * Temporary simulations are created and destroyed on `stream`.
+ * Errors: as chemo_create_batch; EINVAL if trial_steps < 1. */
+int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
+                   const float *pos, const uint8_t *species, int mem_kind, int32_t trial_steps, void *stream,
+                   chemo_params *best_out, float *best_ms_out);
 
 /* Replaces the particle state: pos (n x dim), species (n) and, if the
  * simulation tracks it, disp (n x dim, NULL = zero). Ids are the array

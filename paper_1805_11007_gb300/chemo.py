@@ -81,6 +81,7 @@ class chemo_info(ctypes.Structure):
         ("grid_nodes", ctypes.c_int64),
         ("device_bytes", ctypes.c_int64),
         ("launches_per_step", ctypes.c_int32),
+        ("layers", ctypes.c_int32),
     ]
 
 
@@ -151,6 +152,9 @@ def _declare(L):
     PP = ctypes.POINTER(chemo_params)
     sigs = {
         "chemo_create": ([PP, i64, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "chemo_create_batch": ([PP, i32, vp, vp, vp, ctypes.c_int, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "chemo_autotune": ([PP, i32, vp, vp, vp, ctypes.c_int, i32, vp, PP, ctypes.POINTER(ctypes.c_float)],
+                           ctypes.c_int),
         "chemo_write_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_write_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_step": ([vp, vp], ctypes.c_int),
@@ -241,11 +245,14 @@ def _kind(*kinds):
 class Sim:
     """Owned handle of a simulation (chemo_destroy on close / garbage)."""
 
-    def __init__(self, handle, params: dict, n: int):
+    def __init__(self, handle, params: dict, n: int, sizes=None):
         self.handle = handle
         self.params = dict(params)
         self.n = int(n)
         self.dim = int(params["dim"])
+        # replicate sizes (one entry unless created by chemo_create_batch)
+        self.sizes = [int(n)] if sizes is None else [int(v) for v in sizes]
+        self.replicates = len(self.sizes)
 
     def close(self):
         if self.handle:
@@ -282,6 +289,39 @@ def chemo_create(params: dict, pos, species, stream=None) -> Sim:
     _check(lib().chemo_create(ctypes.byref(prm), n, pp, sp, _kind(kp_, ks), _stream(stream), ctypes.byref(out)),
            "chemo_create")
     return Sim(out, params, n)
+
+
+def chemo_create_batch(params: dict, n_per_replicate, pos, species, stream=None) -> Sim:
+    """Creates an ensemble of 2D replicates (replicate r: n_per_replicate[r]
+    cells, Philox key seed + r); pos (sum n, 2) and species (sum n,) are the
+    replicates' arrays concatenated in replicate order."""
+    sizes = np.ascontiguousarray(np.asarray(n_per_replicate, dtype=np.int64).reshape(-1))
+    pp, kp_, _a = _buf(pos, np.float32)
+    sp, ks, _b = _buf(species, np.uint8)
+    out = ctypes.c_void_p()
+    prm = make_params(params)
+    _check(lib().chemo_create_batch(ctypes.byref(prm), int(sizes.size), sizes.ctypes.data, pp, sp, _kind(kp_, ks),
+                                    _stream(stream), ctypes.byref(out)), "chemo_create_batch")
+    return Sim(out, params, int(sizes.sum()), sizes.tolist())
+
+
+def chemo_autotune(params: dict, n_per_replicate, pos, species, trial_steps: int = 20, stream=None):
+    """Fastest (bin_side, search_mode, pde_overlap) for this particle set:
+    returns (params dict with those fields set, device ms per step)."""
+    sizes = np.ascontiguousarray(np.asarray(n_per_replicate, dtype=np.int64).reshape(-1))
+    pp, kp_, _a = _buf(pos, np.float32)
+    sp, ks, _b = _buf(species, np.uint8)
+    prm = make_params(params)
+    best = chemo_params()
+    ms = ctypes.c_float(0.0)
+    _check(lib().chemo_autotune(ctypes.byref(prm), int(sizes.size), sizes.ctypes.data, pp, sp, _kind(kp_, ks),
+                                int(trial_steps), _stream(stream), ctypes.byref(best), ctypes.byref(ms)),
+           "chemo_autotune")
+    q = dict(params)
+    q["bin_side"] = float(best.bin_side)
+    q["search_mode"] = int(best.search_mode)
+    q["pde_overlap"] = int(best.pde_overlap)
+    return q, float(ms.value)
 
 
 def chemo_write_state(sim: Sim, pos, species, disp=None, stream=None):
@@ -443,6 +483,9 @@ def read_state_host(sim: Sim):
 
 
 def read_field_host(sim: Sim):
-    c = np.zeros(grid_shape(sim.params), np.float32)
+    shape = grid_shape(sim.params)
+    if sim.replicates > 1:
+        shape = (sim.replicates,) + shape
+    c = np.zeros(shape, np.float32)
     chemo_read_field(sim, c)
     return c

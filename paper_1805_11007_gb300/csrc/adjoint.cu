@@ -383,6 +383,7 @@ unsigned blocks(int64_t n) { return (unsigned)((n + ATPB - 1) / ATPB); }
 int check_adjoint_model(const chemo_sim *s)
 {
     const chemo_params &p = s->prm;
+    if (s->kp.layers > 1) return eng_fail(CHEMO_ENOTSUP, "the adjoint covers single simulations (replicates = 1)");
     if (p.reactions) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover type switching (reactions = 1)");
     for (int i = 0; i < p.n_species; ++i)
         if (p.consume[i] != 0.f) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover consumption (consume != 0)");

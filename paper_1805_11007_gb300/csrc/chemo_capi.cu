@@ -256,8 +256,9 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         // no interaction: bins only order the particles (about 2^d per bin)
         double vol = 1.0;
         for (int a = 0; a < p.dim; ++a) vol *= p.hi[a] - p.lo[a];
+        const double per_layer = (double)std::max<int64_t>(n, 1) / (double)std::max(kp.layers, 1);
         bmin = p.bin_side > 0.f ? (double)p.bin_side
-                                : std::pow(vol * (double)(1 << p.dim) / (double)std::max<int64_t>(n, 1), 1.0 / p.dim);
+                                : std::pow(vol * (double)(1 << p.dim) / std::max(per_layer, 1.0), 1.0 / p.dim);
     }
     int64_t total = 1;
     for (int a = 0; a < p.dim; ++a) {
@@ -271,6 +272,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         kp.bside[a] = (float)(L / kp.nb[a]);
         total *= kp.nb[a];
     }
+    if (p.dim == 2) kp.nb[2] = std::max(kp.layers, 1);  // replicates as the third bin index
     if (pairs && kp.periodic) {
         for (int a = 0; a < p.dim; ++a) {
             if (search == 1 && kp.nb[a] < 3)
@@ -284,7 +286,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
     // row-major bins, rows padded to a multiple of 8 so that a group of 8
     // bins never straddles two rows
     kp.px = (kp.nb[0] + 7) & ~7;
-    const int64_t slots = (int64_t)kp.px * (p.dim >= 2 ? kp.nb[1] : 1) * (p.dim == 3 ? kp.nb[2] : 1);
+    const int64_t slots = (int64_t)kp.px * kp.nb[1] * kp.nb[2];
     if (slots > ((int64_t)1 << 31)) return fail(CHEMO_EINVAL, "cell list would need %lld bins", (long long)slots);
     kp.bin_slots = slots;
     kp.ngroups = slots / 8;
@@ -313,6 +315,10 @@ int fill_grid(const chemo_params &p, KP &kp)
         kp.inv_h[a] = (float)(1.0 / h);
         kp.inv_2h[a] = (float)(0.5 / h);
         kp.inv_h2[a] = (float)(1.0 / (h * h));
+    }
+    if (p.dim == 2) {  // one grid per replicate, stacked as the third index
+        kp.g[2] = std::max(kp.layers, 1);
+        G *= kp.g[2];
     }
     if (G > ((int64_t)1 << 34)) return fail(CHEMO_EINVAL, "grid too large");
     kp.G = G;
@@ -494,6 +500,8 @@ int chemo_internal_build_kp(const chemo_params *params, int64_t n, KP *out)
     if (n < 0 || n > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "n = %lld out of range", (long long)n);
     KP kp{};
     kp.n = n;
+    kp.layers = 1;
+    kp.layer_off = nullptr;
     if (int r = fill_layout(*params, n, kp)) return r;
     if (int r = fill_grid(*params, kp)) return r;
     fill_model(*params, kp);
@@ -541,12 +549,27 @@ void chemo_destroy(chemo_sim *s)
 int chemo_create(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species, int mem_kind,
                  void *stream, chemo_sim **out)
 {
+    return chemo_create_batch(params, 1, &n, pos, species, mem_kind, stream, out);
+}
+
+int chemo_create_batch(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
+                       const float *pos, const uint8_t *species, int mem_kind, void *stream, chemo_sim **out)
+{
     g_last_error[0] = 0;
-    if (!params || !out) return fail(CHEMO_EINVAL, "params and out are required");
+    if (!params || !out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and out are required");
     *out = nullptr;
     if (int r = check_mem_kind(mem_kind)) return r;
     if (int r = check_params(*params)) return r;
-    if (n < 0 || n > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "n = %lld out of range [0, 2^29]", (long long)n);
+    if (replicates < 1 || replicates > 65535) return fail(CHEMO_EINVAL, "replicates = %d out of range [1, 65535]", replicates);
+    if (replicates > 1 && params->dim != 2) return fail(CHEMO_EINVAL, "replicates > 1 needs dim = 2");
+    std::vector<int64_t> off((size_t)replicates + 1, 0);
+    for (int r = 0; r < replicates; ++r) {
+        const int64_t m = n_per_replicate[r];
+        if (m < 0 || m > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "replicate %d: n = %lld out of range", r, (long long)m);
+        off[(size_t)r + 1] = off[(size_t)r] + m;
+        if (off[(size_t)r + 1] > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "more than 2^29 cells in total");
+    }
+    const int64_t n = off[(size_t)replicates];
     if (n > 0 && mem_kind == CHEMO_MEM_DEVICE && !(is_device_ptr(pos) && is_device_ptr(species)))
         return fail(CHEMO_EINVAL, "mem_kind is DEVICE but pos/species are not device pointers");
     chemo_sim *s = new (std::nothrow) chemo_sim();
@@ -554,6 +577,9 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     s->prm = *params;
     KP &kp = s->kp;
     kp.n = n;
+    kp.layers = replicates;
+    kp.layer_off = nullptr;
+    s->layer_off_host = off;
     int r;
     if ((r = fill_layout(*params, n, kp)) || (r = fill_grid(*params, kp))) {
         delete s;
@@ -592,6 +618,11 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     kp.err = ctl + 2;
     kp.step = reinterpret_cast<unsigned long long *>(ctl + 4);
     kp.pair_count = nullptr;  // set only while profiling (ctl + 8)
+    if (replicates > 1) {
+        int64_t *lo;
+        ALLOC(lo, off.size() * sizeof(int64_t));
+        kp.layer_off = lo;
+    }
     kp.c[0] = kp.c[1] = nullptr;
     kp.srcg = kp.Rg = nullptr;
     if (kp.has_grid) {
@@ -608,6 +639,9 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     if (e == cudaSuccess) e = cudaMemsetAsync(s->cnt8[1], 0, cwords * sizeof(uint32_t), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(kp.tiles, 0, tiles * sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, 64, st);
+    if (e == cudaSuccess && kp.layer_off)  // from the simulation's own host copy (outlives the copy)
+        e = cudaMemcpyAsync(const_cast<int64_t *>(kp.layer_off), s->layer_off_host.data(),
+                            s->layer_off_host.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && kp.has_grid) {
         e = cudaMemsetAsync(kp.c[0], 0, (size_t)kp.G * sizeof(float), st);
         if (e == cudaSuccess) e = cudaMemsetAsync(kp.c[1], 0, (size_t)kp.G * sizeof(float), st);
@@ -629,6 +663,99 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     // launches per step: particles, scan, scatter, and the PDE substeps
     s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.substeps : 0);
     *out = s;
+    return CHEMO_OK;
+}
+
+// Device time per step of one candidate parameter set (ms), or a status.
+static int trial_time(const chemo_params &q, int32_t replicates, const int64_t *n_per, const float *pos,
+                      const uint8_t *species, int mem_kind, int32_t trial_steps, cudaStream_t st, float *ms)
+{
+    chemo_sim *sim = nullptr;
+    int r = chemo_create_batch(&q, replicates, n_per, pos, species, mem_kind, st, &sim);
+    if (r) return r;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) {
+        r = chemo_step_n(sim, 4, st);  // warm-up (captures the graphs)
+        if (!r) e = cudaEventRecord(e0, st);
+        if (!r && e == cudaSuccess) r = chemo_step_n(sim, trial_steps, st);
+        if (!r && e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (!r && e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (!r && e == cudaSuccess) e = cudaEventElapsedTime(ms, e0, e1);
+        if (!r && e == cudaSuccess) {
+            *ms /= (float)trial_steps;
+            r = chemo_check(sim, st);
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    chemo_destroy(sim);
+    if (!r && e != cudaSuccess) r = fail(CHEMO_ECUDA, "autotune timing: %s", cudaGetErrorString(e));
+    return r;
+}
+
+int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
+                   const float *pos, const uint8_t *species, int mem_kind, int32_t trial_steps, void *stream,
+                   chemo_params *best_out, float *best_ms_out)
+{
+    g_last_error[0] = 0;
+    if (!params || !best_out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and best_out are required");
+    if (trial_steps < 1) return fail(CHEMO_EINVAL, "trial_steps must be >= 1");
+    if (int r = check_params(*params)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double rc = max_cutoff(*params);
+    std::vector<chemo_params> cands;
+    if (rc > 0.0 && params->inter != 0.f) {
+        const double f1[4] = {1.0, 1.25, 1.5, 2.0}, f2[2] = {1.0, 1.25};
+        for (int mode = 1; mode <= 2; ++mode) {
+            const int nf = mode == 1 ? 4 : 2;
+            const double bmin = (mode == 2 ? 2.0 : 1.0) * rc * (1.0 + 1.0 / 4096.0);
+            for (int k = 0; k < nf; ++k) {
+                chemo_params q = *params;
+                q.search_mode = mode;
+                // the minimum side is the automatic one; larger sides are well above it
+                q.bin_side = k == 0 ? 0.f : (float)(bmin * (mode == 1 ? f1[k] : f2[k]));
+                cands.push_back(q);
+            }
+        }
+    } else {
+        cands.push_back(*params);
+    }
+    int best = -1;
+    float best_ms = 0.f;
+    int last_err = CHEMO_OK;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        float ms = 0.f;
+        const int r = trial_time(cands[i], replicates, n_per_replicate, pos, species, mem_kind, trial_steps, st, &ms);
+        if (r == CHEMO_EINVAL) {  // layout not admissible for this box (too few periodic bins...)
+            last_err = r;
+            continue;
+        }
+        if (r) return r;
+        if (best < 0 || ms < best_ms) {
+            best = (int)i;
+            best_ms = ms;
+        }
+    }
+    if (best < 0) return last_err ? last_err : fail(CHEMO_EINVAL, "no admissible candidate");
+    chemo_params q = cands[(size_t)best];
+    if (params->chem_mode == 0) {  // PDE overlap (one-substep fields): try the other settings
+        for (int ov = 1; ov <= 2; ++ov) {
+            chemo_params v = q;
+            v.pde_overlap = ov;
+            float ms = 0.f;
+            const int r = trial_time(v, replicates, n_per_replicate, pos, species, mem_kind, trial_steps, st, &ms);
+            if (r) return r;
+            if (ms < best_ms) {
+                best_ms = ms;
+                q = v;
+            }
+        }
+    }
+    g_last_error[0] = 0;
+    *best_out = q;
+    if (best_ms_out) *best_ms_out = best_ms;
     return CHEMO_OK;
 }
 
@@ -814,6 +941,7 @@ int chemo_get_info(const chemo_sim *s, chemo_info *info)
     info->grid_nodes = kp.G;
     info->device_bytes = s->bytes;
     info->launches_per_step = s->launches_per_step;
+    info->layers = kp.layers;
     return CHEMO_OK;
 }
 

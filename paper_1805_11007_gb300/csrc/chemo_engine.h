@@ -31,6 +31,7 @@ struct chemo_sim {
     void *scratch = nullptr;     // staging for host transfers and stage outputs
     size_t scratch_bytes = 0;
     chemo_tape *tape = nullptr;  // recorded run for the adjoint (adjoint.cu)
+    std::vector<int64_t> layer_off_host;  // replicate offsets (layers + 1), host copy
 };
 
 // Engine services used by adjoint.cu (implemented in chemo_capi.cu).

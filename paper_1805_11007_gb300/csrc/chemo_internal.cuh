@@ -38,6 +38,14 @@ struct KP {
     int px;                     // row pitch of the bin table (nb[0] rounded up to 8)
     int64_t bin_slots;          // px * nb[1] * nb[2]; bins are row-major, x fastest
     int64_t ngroups;            // bin_slots / 8: groups of 8 bins of one row
+    // Replicates (2D only): independent simulations of the same model stacked
+    // as layers. A particle's layer is its .z (an exact small integer); bins
+    // and grid nodes carry the layer as their third index (nb[2] = g[2] =
+    // layers), so pairs, gradients and deposits never cross layers. Layer l
+    // holds the ids layer_off[l] .. layer_off[l+1]-1 of the caller's arrays,
+    // stored in .w as the id local to the layer; its Philox key is seed + l.
+    int layers;
+    const int64_t *layer_off;    // device, layers + 1 entries (NULL when layers == 1)
     // species tables (index s * MAXS + t)
     int ns;
     float rc2[MAXS * MAXS];      // r_c,st^2
@@ -109,13 +117,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Words of cell `id` at step `step` on stream `tag`: counter
-// (id, step lo, tag, step hi), key (seed lo, seed hi).
+// Words of cell `id` (local to its layer) at step `step` on stream `tag`:
+// counter (id, step lo, tag, step hi), key (seed + layer) as (lo, hi) words.
 __device__ __forceinline__ uint4 cell_words(const KP &kp, uint32_t id, unsigned long long step,
-                                            uint32_t tag)
+                                            uint32_t tag, uint32_t layer = 0u)
 {
-    return philox4x32_10(make_uint4(id, (uint32_t)step, tag, (uint32_t)(step >> 32)), kp.seed_lo,
-                         kp.seed_hi);
+    const uint32_t k0 = kp.seed_lo + layer;
+    const uint32_t k1 = kp.seed_hi + (k0 < kp.seed_lo ? 1u : 0u);
+    return philox4x32_10(make_uint4(id, (uint32_t)step, tag, (uint32_t)(step >> 32)), k0, k1);
 }
 
 // u = (w + 1/2) 2^-32 in single precision (never 0).
@@ -179,11 +188,26 @@ __device__ __forceinline__ uint32_t count_bin(uint32_t *cnt, uint32_t k, uint32_
     return slot;
 }
 
+// Layer of a particle (0 unless replicates are stacked), clamped to the table.
+__device__ __forceinline__ int layer_of(const KP &kp, float4 p)
+{
+    if (kp.dim == 3 || kp.layers <= 1) return 0;
+    const int l = (int)p.z;
+    return l < 0 ? 0 : (l >= kp.layers ? kp.layers - 1 : l);
+}
+
+// Index of a particle in the caller's arrays (layer offset + local id).
+__device__ __forceinline__ int64_t gid_of(const KP &kp, float4 p)
+{
+    const int64_t id = __float_as_uint(p.w) & ID_MASK;
+    return kp.layers > 1 ? kp.layer_off[layer_of(kp, p)] + id : id;
+}
+
 __device__ __forceinline__ void cell_of(const KP &kp, float4 p, int &cx, int &cy, int &cz)
 {
     cx = bin_axis(p.x, kp.lo[0], kp.inv_b[0], kp.nb[0]);
     cy = bin_axis(p.y, kp.lo[1], kp.inv_b[1], kp.nb[1]);
-    cz = kp.dim == 3 ? bin_axis(p.z, kp.lo[2], kp.inv_b[2], kp.nb[2]) : 0;
+    cz = kp.dim == 3 ? bin_axis(p.z, kp.lo[2], kp.inv_b[2], kp.nb[2]) : layer_of(kp, p);
 }
 
 __device__ __forceinline__ uint32_t key_of(const KP &kp, float4 p)

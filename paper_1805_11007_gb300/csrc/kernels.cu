@@ -168,6 +168,7 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
             hi[a] = min(hi[a], kp.nb[a] - 1);
         }
     }
+    if (DIM == 2) c[2] = lo[2] = hi[2] = layer_of(kp, me);  // rows of the particle's own layer
     const float rs2 = kp.rsp2[sp];
     const uint32_t *__restrict__ cnt = kp.cnt_cur;
     const uint32_t *__restrict__ gst = kp.gstart;
@@ -279,6 +280,7 @@ __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restr
     gcell(kp, 0, p.x, i0, i1, fx);
     gcell(kp, 1, p.y, j0, j1, fy);
     if (DIM == 3) gcell(kp, 2, p.z, k0, k1, fz);
+    else k0 = layer_of(kp, p);  // the particle's own layer of the grid
     const int64_t gx = kp.g[0], plane = (int64_t)kp.g[0] * kp.g[1];
     // base node (i0, j0, k0) and offsets to the other nodes used
     const int64_t b = (int64_t)i0 + gx * ((int64_t)j0 + (int64_t)kp.g[1] * k0);
@@ -378,6 +380,7 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
     const uint32_t id = w & ID_MASK;
+    const uint32_t layer = (uint32_t)layer_of(kp, me);
     int sp = (int)(w >> SP_SHIFT);
 
     int npairs = 0;
@@ -407,7 +410,7 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     }
 
     // Euler-Maruyama move, Eq. (2) with the drift of Eq. (1b)
-    const uint4 rw = cell_words(kp, id, step, TAG_MOVE);
+    const uint4 rw = cell_words(kp, id, step, TAG_MOVE, layer);
     const float2 n01 = box_muller(rw.x, rw.y);
     float n2 = 0.f;
     if (DIM == 3) n2 = box_muller(rw.z, rw.w).x;
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     // comparison that decides the species is taken in double precision, the
     // precision of the paper's code; u = (w + 1/2) 2^-32 is exact there.
     if (kp.reactions) {
-        const uint4 rr = cell_words(kp, id, step, TAG_REACT);
+        const uint4 rr = cell_words(kp, id, step, TAG_REACT, layer);
         const double u = ((double)rr.x + 0.5) * 2.3283064365386963e-10;
         const double prop = ((double)kp.rk0[sp] + (double)kp.rkc[sp] * (double)conc) * kp.dt_d;
         if (u < prop) sp = kp.rto[sp];
@@ -430,11 +433,11 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     if (PERIODIC) {
         xb = wrap_axis(x1, kp.lo[0], kp.hi[0], kp.L[0]);
         yb = wrap_axis(y1, kp.lo[1], kp.hi[1], kp.L[1]);
-        zb = DIM == 3 ? wrap_axis(z1, kp.lo[2], kp.hi[2], kp.L[2]) : 0.f;
+        zb = DIM == 3 ? wrap_axis(z1, kp.lo[2], kp.hi[2], kp.L[2]) : me.z;
     } else {
         xb = reflect_axis(x1, kp.lo[0], kp.hi[0]);
         yb = reflect_axis(y1, kp.lo[1], kp.hi[1]);
-        zb = DIM == 3 ? reflect_axis(z1, kp.lo[2], kp.hi[2]) : 0.f;
+        zb = DIM == 3 ? reflect_axis(z1, kp.lo[2], kp.hi[2]) : me.z;
     }
     const bool finite = isfinite(x1) && isfinite(y1) && (DIM == 2 || isfinite(z1));
     if (!finite) {
@@ -490,7 +493,19 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
         set_err(kp, ERR_SPECIES);
         s = 0;
     }
-    const float4 u = make_float4(x[0], x[1], x[2], __uint_as_float((uint32_t)i | (s << SP_SHIFT)));
+    // layer of entry i: the last l with layer_off[l] <= i (binary search)
+    int64_t local = i;
+    if (kp.layers > 1) {
+        int l0 = 0, l1 = kp.layers;
+        while (l1 - l0 > 1) {
+            const int mid = (l0 + l1) >> 1;
+            if (kp.layer_off[mid] <= i) l0 = mid;
+            else l1 = mid;
+        }
+        local = i - kp.layer_off[l0];
+        x[2] = (float)l0;
+    }
+    const float4 u = make_float4(x[0], x[1], x[2], __uint_as_float((uint32_t)local | (s << SP_SHIFT)));
     kp.U[i] = u;
     if (kp.dU) {
         float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -672,6 +687,7 @@ __device__ __forceinline__ void deposit_cic(const KP &kp, float4 u, int sp, floa
     gcell(kp, 0, u.x, i0, i1, fx);
     gcell(kp, 1, u.y, j0, j1, fy);
     if (DIM == 3) gcell(kp, 2, u.z, k0, k1, fz);
+    else k0 = layer_of(kp, u);
     const bool walls = kp.pde_bc != 2;
 #pragma unroll
     for (int m = 0; m < (1 << DIM); ++m) {
@@ -820,7 +836,8 @@ __global__ void __launch_bounds__(256) k_pde_stream(KP kp, const float *__restri
     const int s1 = min(s0 + chunk, ns);
     if (s0 >= ns) return;  // whole warp (s0 depends on warp / block only)
     const int64_t sstride = DIM == 3 ? (int64_t)gx * gy : (int64_t)gx;
-    const int64_t rowbase = (DIM == 3 ? (int64_t)yy * gx : 0) + 4 * (int64_t)qq;
+    // 2D: blockIdx.y is the layer (replicate) of the grid
+    const int64_t rowbase = (DIM == 3 ? (int64_t)yy * gx : (int64_t)blockIdx.y * gx * gy) + 4 * (int64_t)qq;
     int64_t oym = 0, oyp = 0;
     if (DIM == 3) {
         oym = (int64_t)(ghost<BC>(yy - 1, gy) - yy) * gx;
@@ -902,7 +919,7 @@ __global__ void k_unsort(KP kp, float *__restrict__ pos, uint8_t *__restrict__ s
     if (j >= kp.n) return;
     const float4 u = kp.S[j];
     const uint32_t w = __float_as_uint(u.w);
-    const int64_t id = w & ID_MASK;
+    const int64_t id = gid_of(kp, u);
     if (id >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
         return;
@@ -933,7 +950,7 @@ __global__ void k_stage_bins(KP kp, int32_t *__restrict__ cells)
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (j >= kp.n) return;
     const float4 u = kp.S[j];
-    const int64_t id = __float_as_uint(u.w) & ID_MASK;
+    const int64_t id = gid_of(kp, u);
     if (id >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
         return;
@@ -948,7 +965,7 @@ __global__ void k_stage_bins(KP kp, int32_t *__restrict__ cells)
 __global__ void k_stage_sort(KP kp, uint32_t *__restrict__ ids)
 {
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (j < kp.n) ids[j] = __float_as_uint(kp.S[j].w) & ID_MASK;
+    if (j < kp.n) ids[j] = (uint32_t)gid_of(kp, kp.S[j]);
 }
 
 // Offset of every bin (bin_slots + 1 entries) of the sorted state.
@@ -970,7 +987,7 @@ __global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restric
     const bool valid = j < kp.n;
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
-    const int64_t id = w & ID_MASK;
+    const int64_t id = valid ? gid_of(kp, me) : 0;
     int cnt = 0;
     unsigned long long ids = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
@@ -996,7 +1013,7 @@ __global__ void k_stage_drift(KP kp, int cur, float *__restrict__ out)
     if (j >= kp.n) return;
     const float4 me = kp.S[j];
     const uint32_t w = __float_as_uint(me.w);
-    const int64_t id = w & ID_MASK;
+    const int64_t id = gid_of(kp, me);
     if (id >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
         return;
@@ -1125,7 +1142,7 @@ static void pde_stream_launch(const KP &kp, const float *cin, float *cout, int u
         int chunk = 4;
         while (chunk < kp.g[1] && (int64_t)bx * 8 * ((kp.g[1] + 2 * chunk - 1) / (2 * chunk)) >= 2432) chunk *= 2;
         const int warps = (kp.g[1] + chunk - 1) / chunk;
-        const dim3 grid(bx, 1, (warps + 7) / 8);
+        const dim3 grid(bx, kp.g[2], (warps + 7) / 8);
         if (kp.pde_bc == 0) k_pde_stream<2, 0><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
         else if (kp.pde_bc == 1) k_pde_stream<2, 1><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
         else k_pde_stream<2, 2><<<grid, block, 0, st>>>(kp, cin, cout, use_src, last, chunk);
@@ -1136,7 +1153,7 @@ cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (!kp.has_grid || kp.chem_mode != 0) return cudaSuccess;
     const bool stream = kp.g[0] % 4 == 0 && kp.g[0] >= 8;
-    const dim3 grid((kp.g[0] + 127) / 128, kp.g[1], kp.dim == 3 ? kp.g[2] : 1);
+    const dim3 grid((kp.g[0] + 127) / 128, kp.g[1], kp.g[2]);  // g[2]: planes (3D) or layers (2D)
     const int s = kp.substeps;
     const int use_src = kp.fused_deposit ? 0 : 1;
     int c = cur;

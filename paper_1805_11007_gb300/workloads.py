@@ -156,3 +156,31 @@ def ensemble_sizes(replicates: int, n_min: int, n_max: int, seed: int) -> np.nda
     """Replicate sizes drawn log-uniform in [n_min, n_max]."""
     rng = np.random.default_rng(seed)
     return np.floor(np.exp(rng.uniform(np.log(n_min), np.log(n_max), size=replicates))).astype(np.int64)
+
+
+def ensemble_state(name: str = "ensemble_2d", replicates: int | None = None, seed: int | None = None,
+                   sizes=None, **overrides):
+    """(params, sizes int64 (R,), pos float32 (sum n, 2), species uint8
+    (sum n,)) of an ensemble workload: replicate r has sizes[r] cells drawn
+    uniform in the box with seed + 1000 + r, species split in halves. The
+    replicates' arrays are concatenated in replicate order (the layout of
+    chemo_create_batch); replicate r runs with Philox key params['seed'] + r."""
+    w = WORKLOADS[name]
+    p = params(name, **overrides)
+    seed = p["seed"] if seed is None else seed
+    if sizes is None:
+        R = w["replicates"] if replicates is None else replicates
+        sizes = ensemble_sizes(R, w["n_min"], w["n_max"], seed)
+    sizes = np.asarray(sizes, dtype=np.int64).reshape(-1)
+    pos = [uniform_positions(int(m), p["dim"], p["lo"], p["hi"], seed + 1000 + r) for r, m in enumerate(sizes)]
+    sp = [half_species(int(m), p["n_species"]) for m in sizes]
+    pos = np.concatenate(pos, axis=0) if len(pos) else np.zeros((0, p["dim"]), np.float32)
+    sp = np.concatenate(sp) if len(sp) else np.zeros(0, np.uint8)
+    return p, sizes, np.ascontiguousarray(pos, dtype=np.float32), np.ascontiguousarray(sp)
+
+
+def replicate_params(params_: dict, r: int) -> dict:
+    """Parameters of replicate r of an ensemble run on its own (seed + r)."""
+    q = copy.deepcopy(params_)
+    q["seed"] = int(params_.get("seed", 0)) + int(r)
+    return q

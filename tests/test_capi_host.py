@@ -102,3 +102,31 @@ def test_gradient_needs_a_simulation(chemo):
     assert st == chemo.EINVAL
     st = chemo.lib().chemo_record(None, 1, 1, None)
     assert st == chemo.EINVAL
+
+
+@pytest.mark.parametrize("case", ["dim3", "zero", "negative", "too_many"])
+def test_batch_arguments_rejected_on_host(chemo, case):
+    """chemo_create_batch validates its replicate arguments before touching
+    the device: 3D ensembles, no replicates, negative sizes, > 65535."""
+    from paper_1805_11007_gb300 import workloads as wl
+    p = wl.params("ensemble_2d")
+    sizes = [0, 0]
+    if case == "dim3":
+        p = wl.params("clumps_grid_3d", grid=[8, 8, 8])
+    elif case == "zero":
+        sizes = []
+    elif case == "negative":
+        sizes = [3, -1]
+    else:
+        sizes = [0] * 65536
+    with pytest.raises(chemo.ChemoError) as ei:
+        chemo.chemo_create_batch(p, sizes, np.zeros((0, p["dim"]), np.float32), np.zeros(0, np.uint8))
+    assert ei.value.status == chemo.EINVAL
+
+
+def test_autotune_needs_trial_steps(chemo):
+    from paper_1805_11007_gb300 import workloads as wl
+    p = wl.params("ensemble_2d")
+    with pytest.raises(chemo.ChemoError) as ei:
+        chemo.chemo_autotune(p, [0], np.zeros((0, 2), np.float32), np.zeros(0, np.uint8), trial_steps=0)
+    assert ei.value.status == chemo.EINVAL
