@@ -257,8 +257,17 @@ def adjoint_ratio(chemo, wl, devc, stream):
     dsp = torch.from_numpy(sp).to(devc)
     sim = chemo.chemo_create(p, dpos, dsp, stream=stream)
     try:
-        g = torch.zeros((n, 2), dtype=torch.float32, device=devc)
-        g[:, 0] = 1.0 / n
+        # dL/dX(T) of the differentiable workload's loss, L = mean x
+        # displacement + mean squared soft occupancy of a 64^2 analysis grid,
+        # at the final state of a forward run (torch autograd on the device)
+        from paper_1805_11007_gb300 import adjoint as adj
+        chemo.chemo_step_n(sim, steps, stream=stream)
+        xT = torch.zeros((n, 2), dtype=torch.float32, device=devc)
+        chemo.chemo_read_state(sim, xT, None, None, stream=stream)
+        xT.requires_grad_(True)
+        loss = adj.mean_x_displacement(xT, dpos) + adj.occupancy_loss(xT, 64, p["lo"], p["hi"])
+        g, = torch.autograd.grad(loss, xT)
+        g = g.detach().contiguous()
         dth = torch.zeros(2 + p["n_species"], dtype=torch.float32, device=devc)
         c0 = torch.zeros(tuple(chemo.grid_shape(p)), dtype=torch.float32, device=devc)
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -280,7 +289,7 @@ def adjoint_ratio(chemo, wl, devc, stream):
         fwd = ev[0].elapsed_time(ev[1])
         both = ev[2].elapsed_time(ev[3])
         return {"workload": "adjoint_2d: 2D walls, N=%d two species, %dx%d grid (%d PDE substeps), %d steps, "
-                            "checkpoints every %d, gradients wrt chi, inter, D_0, D_1"
+                            "checkpoints every %d, loss mean x displacement + soft occupancy (64^2), gradients wrt chi, inter, D_0, D_1"
                             % (n, p["grid"][0], p["grid"][1], chemo.chemo_get_info(sim)["pde_substeps"], steps, every),
                 "forward_ms": fwd, "forward_backward_ms": both, "ratio": both / fwd,
                 "gradients_finite": bool(torch.isfinite(dth).all().item())}
