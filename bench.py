@@ -93,7 +93,7 @@ FP32_LANES = 152 * 128
 
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
 # traffic field; None where the kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": 61.93e6, "k_pde": 93.65e6, "k_scan": 38.20e6, "k_scatter": 45.05e6}
+NCU_TRAFFIC_BYTES = {"k_step": 62.80e6, "k_pde": 93.65e6, "k_scan": 38.20e6, "k_scatter": 45.05e6}
 
 
 # ---------------------------------------------------------------------------
@@ -308,6 +308,10 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
     p, sizes, pos, sp = wl.ensemble_state()
     mine = en.shard_replicates(sizes, world)[rank]
     s_m, pos_m, sp_m = en.take(pos, sp, sizes, mine)
+    # the cell list and launch choices of this ensemble, tuned on it
+    t0 = time.perf_counter()
+    p, tuned_ms = chemo.chemo_autotune(p, s_m, pos_m, sp_m, trial_steps=10, stream=stream)
+    tune_s = time.perf_counter() - t0
     dpos = torch.from_numpy(pos_m).to(devc)
     dsp = torch.from_numpy(sp_m).to(devc)
     sim = chemo.chemo_create_batch(p, s_m, dpos, dsp, stream=stream)
@@ -343,6 +347,8 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
                        % (len(sizes), int(sizes.sum()), p["grid"][0], p["grid"][1], info["pde_substeps"], steps),
            "value": float(sizes.sum()) * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "launches_per_step": info["launches_per_step"],
+           "autotuned": {"search_mode": p["search_mode"], "bin_side": p["bin_side"], "warp_runs": p["warp_runs"],
+                         "pde_overlap": p["pde_overlap"], "trial_ms_per_step": tuned_ms, "tuning_s": tune_s},
            "kernel_ms": {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")}}
     if rank == 0:
         # the same replicates one simulation at a time (each with its own

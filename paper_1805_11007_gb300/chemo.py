@@ -65,6 +65,7 @@ class chemo_params(ctypes.Structure):
         ("search_mode", ctypes.c_int32),
         ("bin_order", ctypes.c_int32),
         ("pde_overlap", ctypes.c_int32),
+        ("warp_runs", ctypes.c_int32),
     ]
 
 
@@ -128,6 +129,7 @@ def make_params(d: dict) -> chemo_params:
     p.search_mode = int(d.get("search_mode", 0))
     p.bin_order = int(d.get("bin_order", 0))
     p.pde_overlap = int(d.get("pde_overlap", 0))
+    p.warp_runs = int(d.get("warp_runs", 0))
     return p
 
 
@@ -321,6 +323,7 @@ def chemo_autotune(params: dict, n_per_replicate, pos, species, trial_steps: int
     q["bin_side"] = float(best.bin_side)
     q["search_mode"] = int(best.search_mode)
     q["pde_overlap"] = int(best.pde_overlap)
+    q["warp_runs"] = int(best.warp_runs)
     return q, float(ms.value)
 
 

@@ -133,7 +133,8 @@ int check_params(const chemo_params &p)
     if (p.cutoff_mode != 0 && p.cutoff_mode != 1) return fail(CHEMO_EINVAL, "cutoff_mode must be 0 or 1");
     if (!(p.cutoff_factor >= 0.f)) return fail(CHEMO_EINVAL, "cutoff_factor must be >= 0");
     if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
-    if (p.search_mode < 0 || p.search_mode > 2) return fail(CHEMO_EINVAL, "search_mode must be 0, 1 or 2");
+    if (p.search_mode < 0 || p.search_mode > 3) return fail(CHEMO_EINVAL, "search_mode must be 0, 1, 2 or 3");
+    if (p.warp_runs < 0 || p.warp_runs > 32) return fail(CHEMO_EINVAL, "warp_runs must be 0..32");
     if (p.bin_order < 0 || p.bin_order > 2) return fail(CHEMO_EINVAL, "bin_order must be 0, 1 or 2");
     if (p.pde_overlap < 0 || p.pde_overlap > 2) return fail(CHEMO_EINVAL, "pde_overlap must be 0, 1 or 2");
     if (p.chem_mode == 0) {
@@ -275,7 +276,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
     if (p.dim == 2) kp.nb[2] = std::max(kp.layers, 1);  // replicates as the third bin index
     if (pairs && kp.periodic) {
         for (int a = 0; a < p.dim; ++a) {
-            if (search == 1 && kp.nb[a] < 3)
+            if (search != 2 && kp.nb[a] < 3)
                 return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= r_c; need >= 3 (box too small "
                                           "for the cutoff; try search_mode 2)", a, kp.nb[a]);
             if (search == 2 && kp.nb[a] < 3)
@@ -291,6 +292,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
     kp.bin_slots = slots;
     kp.ngroups = slots / 8;
     kp.search = search;
+    kp.warp_runs = p.warp_runs > 0 ? p.warp_runs : 8;
     return CHEMO_OK;
 }
 
@@ -707,15 +709,16 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
     const double rc = max_cutoff(*params);
     std::vector<chemo_params> cands;
     if (rc > 0.0 && params->inter != 0.f) {
-        const double f1[4] = {1.0, 1.25, 1.5, 2.0}, f2[2] = {1.0, 1.25};
-        for (int mode = 1; mode <= 2; ++mode) {
-            const int nf = mode == 1 ? 4 : 2;
+        // bin side factors of each search mode (1: 3^d warp, 2: 2^d, 3: 3^d per lane)
+        const double fac[3][4] = {{1.0, 1.25, 1.5, 2.0}, {1.0, 1.25, 0.0, 0.0}, {1.0, 1.5, 0.0, 0.0}};
+        const int nf[3] = {4, 2, 2};
+        for (int mode = 1; mode <= 3; ++mode) {
             const double bmin = (mode == 2 ? 2.0 : 1.0) * rc * (1.0 + 1.0 / 4096.0);
-            for (int k = 0; k < nf; ++k) {
+            for (int k = 0; k < nf[mode - 1]; ++k) {
                 chemo_params q = *params;
                 q.search_mode = mode;
                 // the minimum side is the automatic one; larger sides are well above it
-                q.bin_side = k == 0 ? 0.f : (float)(bmin * (mode == 1 ? f1[k] : f2[k]));
+                q.bin_side = k == 0 ? 0.f : (float)(bmin * fac[mode - 1][k]);
                 cands.push_back(q);
             }
         }
@@ -740,6 +743,20 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
     }
     if (best < 0) return last_err ? last_err : fail(CHEMO_EINVAL, "no admissible candidate");
     chemo_params q = cands[(size_t)best];
+    if (q.search_mode == 1) {  // how sparse a warp may be and still search together
+        const int runs[3] = {4, 16, 32};
+        for (int v : runs) {
+            chemo_params c = q;
+            c.warp_runs = v;
+            float ms = 0.f;
+            const int r = trial_time(c, replicates, n_per_replicate, pos, species, mem_kind, trial_steps, st, &ms);
+            if (r) return r;
+            if (ms < best_ms) {
+                best_ms = ms;
+                q = c;
+            }
+        }
+    }
     if (params->chem_mode == 0) {  // PDE overlap (one-substep fields): try the other settings
         for (int ov = 1; ov <= 2; ++ov) {
             chemo_params v = q;

@@ -30,7 +30,8 @@ constexpr uint32_t TAG_REACT = 2u;
 struct KP {
     // particles and cell list
     int64_t n;
-    int dim, periodic, search;  // search 1: 3^d bins >= r_c, 2: 2^d bins >= 2 r_c
+    int dim, periodic, search;  // search 1: 3^d bins >= r_c (warp), 2: 2^d bins >= 2 r_c, 3: 3^d (per lane)
+    int warp_runs;              // search 1: warps with at most this many bins search together
     int pairs;                  // 0: no pair interaction (inter = 0 or zero range)
     float lo[3], hi[3], L[3], halfL[3];
     int nb[3];                  // bins per axis

@@ -122,7 +122,7 @@ __device__ __forceinline__ void flush_list(const KP &kp, const SmemTables &t, co
     int ax = 0, ay = 0, az = 0;
     for (int i = 0; i < m; ++i) {
         if (i < nl) {
-            const float4 o = __ldg(&kp.S[lst[i * TPB]]);
+            const float4 o = __ldg(&kp.S[lst[i * 32]]);
             float dx, dy, dz, r2;
             pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
             const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
@@ -144,11 +144,12 @@ __device__ __forceinline__ void flush_list(const KP &kp, const SmemTables &t, co
 // Must be called by all 32 lanes of the warp (`valid` false for padding lanes).
 template <int DIM, bool PERIODIC, bool STATS>
 __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, uint32_t self, float4 me, int sp,
-                                             bool valid, int &count, unsigned long long &idsum, unsigned char *smem_extra)
+                                             bool valid, int &count, unsigned long long &idsum, unsigned char *wbuf)
 {
-    uint2 *rng = reinterpret_cast<uint2 *>(smem_extra) + threadIdx.x;
-    uint32_t *lst = reinterpret_cast<uint32_t *>(smem_extra + (size_t)TPB * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) +
-                    threadIdx.x;
+    // the warp's region: staged ranges [RowCap][32], then lists [LIST_CAP][32]
+    const int lane = threadIdx.x & 31;
+    uint2 *rng = reinterpret_cast<uint2 *>(wbuf) + lane;
+    uint32_t *lst = reinterpret_cast<uint32_t *>(wbuf + (size_t)32 * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) + lane;
     int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
     const float pc[3] = {me.x, me.y, me.z};
@@ -190,15 +191,15 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                 if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
                 if (PERIODIC && x0 < 0) {
                     const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
-                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
+                    rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
                     x0 = 0;
                 }
                 if (PERIODIC && x1 >= kp.nb[0]) {
-                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
+                    rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
                     x1 = kp.nb[0] - 1;
                 }
                 if (x0 <= x1)
-                    rng[nr++ * TPB] = make_uint2(bin_start(cnt, gst, rowk + x0), bin_start(cnt, gst, rowk + x1 + 1));
+                    rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, rowk + x0), bin_start(cnt, gst, rowk + x1 + 1));
             }
         }
     }
@@ -213,7 +214,7 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
     int r = 0;
     uint32_t q = 0, qe = 0;
     while (q >= qe && r < nr) {
-        const uint2 g = rng[r++ * TPB];
+        const uint2 g = rng[r++ * 32];
         q = g.x;
         qe = min(g.y, n);  // offsets are trusted only up to n
     }
@@ -232,7 +233,7 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                 const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
                 const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
                 if (r2 < rc2 && r2 > 0.f && qq != self) {
-                    lst[nl++ * TPB] = qq;
+                    lst[nl++ * 32] = qq;
                     count += 1;
                     if (STATS) idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
                 }
@@ -241,7 +242,7 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
             q += m;
             if (q >= qe) {
                 while (q >= qe && r < nr) {
-                    const uint2 g = rng[r++ * TPB];
+                    const uint2 g = rng[r++ * 32];
                     q = g.x;
                     qe = min(g.y, n);
                 }
@@ -258,13 +259,289 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                        DIM == 3 ? __ll2float_rn(F.z) * kp.fq : 0.f);
 }
 
-// Dynamic shared memory of the kernels that evaluate pair forces: species
-// tables, staged row ranges and the neighbour lists.
+// ---------------------------------------------------------------------------
+// Warp-cooperative search (3^d window). The 32 lanes of a warp hold 32
+// consecutive cells of the sorted array, so they fall into a few runs of
+// cells that share a bin. For each run the warp walks the run's window once:
+// the window's candidates are split across the lanes (one coalesced load per
+// candidate), and each lane tests its candidate against every cell of the
+// run, whose positions are broadcast from shared memory. Pairs inside the
+// cutoff go to a queue of the warp (ballot + popc); the queue is evaluated
+// in a converged loop, each term added to its cell with a 32-bit shared
+// atomic (at most QCAP terms of magnitude < 2^25 per flush, no overflow) and
+// drained into 64-bit registers after every flush. The sum is exact, so the
+// force is the same as the per-lane search's and independent of the order.
+// ---------------------------------------------------------------------------
+constexpr int QCAP = 64;  // queue entries; flushed once more than QCAP - 32 are held
+
 template <int DIM, bool PERIODIC>
+struct WinRows {
+    static constexpr int value = (DIM == 3 ? 9 : 3) * (PERIODIC ? 2 : 1);
+};
+
+struct WarpSmem {
+    float4 ipos[32];               // the warp's cells: position and species (as a float)
+    uint2 queue[QCAP];             // (sorted index of the candidate, lane of the cell)
+    int facc[3][32];               // fixed-point force of each cell since the last drain
+    int cnt[32];                   // in-cutoff neighbours (stage statistics)
+    unsigned long long ids[32];    // sum of neighbour ids (stage statistics)
+    uint2 rows[18];                // window ranges of the current run: (first index, first candidate)
+};
+
+template <int DIM, bool PERIODIC, bool STATS>
+__device__ __forceinline__ void flush_queue(const KP &kp, const SmemTables &t, WarpSmem &ws, int qn, int lane,
+                                            long long &Fx, long long &Fy, long long &Fz)
+{
+    __syncwarp();
+    for (int e = lane; e < qn; e += 32) {
+        const uint2 ent = ws.queue[e];
+        const float4 o = __ldg(&kp.S[ent.x]);
+        const float4 pi = ws.ipos[ent.y];
+        float dx, dy, dz, r2;
+        pair_delta<DIM, PERIODIC>(kp, pi, o, dx, dy, dz, r2);
+        if (!(r2 > 0.f)) continue;  // coincident distinct cells exert no force
+        const int st = (int)pi.w * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+        const float rinv = rsqrtf(r2);
+        const float r = r2 * rinv;
+        const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
+        const float sq = (f * rinv) * kp.fq_inv;
+        atomicAdd(&ws.facc[0][ent.y], __float2int_rn(sq * dx));
+        atomicAdd(&ws.facc[1][ent.y], __float2int_rn(sq * dy));
+        if (DIM == 3) atomicAdd(&ws.facc[2][ent.y], __float2int_rn(sq * dz));
+        if (STATS) {
+            atomicAdd(&ws.cnt[ent.y], 1);
+            atomicAdd(&ws.ids[ent.y], (unsigned long long)(__float_as_uint(o.w) & ID_MASK));
+        }
+    }
+    __syncwarp();
+    Fx += ws.facc[0][lane];
+    Fy += ws.facc[1][lane];
+    Fz += ws.facc[2][lane];
+    ws.facc[0][lane] = 0;
+    ws.facc[1][lane] = 0;
+    ws.facc[2][lane] = 0;
+    __syncwarp();
+}
+
+// Tests candidate o (squared cutoffs c0 + w c1 against a cell of species
+// flag w) against the cells [h, e) of the run: bit k-h set when in reach.
+template <int DIM, bool PERIODIC>
+__device__ __forceinline__ void test_run2(const KP &kp, const WarpSmem &ws, int h, int e, float4 o0, float a0,
+                                          float b0, float4 o1, float a1, float b1, uint32_t &m0, uint32_t &m1)
+{
+    uint32_t bit = 1u;
+#pragma unroll 4
+    for (int k = h; k < e; ++k) {
+        const float4 pi = ws.ipos[k];
+        float dx, dy, dz, r2;
+        pair_delta<DIM, PERIODIC>(kp, pi, o0, dx, dy, dz, r2);
+        if (r2 < fmaf(pi.w, b0, a0)) m0 |= bit;
+        pair_delta<DIM, PERIODIC>(kp, pi, o1, dx, dy, dz, r2);
+        if (r2 < fmaf(pi.w, b1, a1)) m1 |= bit;
+        bit <<= 1;
+    }
+}
+
+// Pair force of the cell of every lane; `self` is the lane's sorted index
+// (lanes hold consecutive indices). All 32 lanes must call it. A warp whose
+// cells fall in more than kp.warp_runs bins (sparse regions, where a run
+// holds one or two cells) takes the per-lane search instead.
+template <int DIM, bool PERIODIC, bool STATS>
+__device__ __forceinline__ float3 pair_force_warp(const KP &kp, const SmemTables &t, unsigned char *wbuf,
+                                                  uint32_t self, float4 me, int sp, bool valid, int &count,
+                                                  unsigned long long &idsum)
+{
+    constexpr int NR = WinRows<DIM, PERIODIC>::value;
+    const int lane = threadIdx.x & 31;
+    const uint32_t base = self - (uint32_t)lane;
+    const uint32_t n = (uint32_t)kp.n;
+    const int cx = bin_axis(me.x, kp.lo[0], kp.inv_b[0], kp.nb[0]);
+    const int cy = bin_axis(me.y, kp.lo[1], kp.inv_b[1], kp.nb[1]);
+    const int cz = DIM == 3 ? bin_axis(me.z, kp.lo[2], kp.inv_b[2], kp.nb[2]) : layer_of(kp, me);
+    const uint32_t key = valid ? bin_key(kp, cx, cy, cz) : 0xFFFFFFFFu;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    const unsigned vmask = __ballot_sync(0xffffffffu, valid);
+    unsigned heads = __ballot_sync(0xffffffffu, valid && (lane == 0 || key != prev));
+    if (__popc(heads) > kp.warp_runs) return pair_force<DIM, PERIODIC, STATS>(kp, t, self, me, sp, valid, count, idsum, wbuf);
+
+    WarpSmem &ws = *reinterpret_cast<WarpSmem *>(wbuf);
+    ws.ipos[lane] = make_float4(me.x, me.y, me.z, (float)sp);
+    ws.facc[0][lane] = 0;
+    ws.facc[1][lane] = 0;
+    ws.facc[2][lane] = 0;
+    if (STATS) {
+        ws.cnt[lane] = 0;
+        ws.ids[lane] = 0ull;
+    }
+    const int nvalid = __popc(vmask);  // valid lanes are a prefix of the warp
+    const bool two = kp.ns <= 2;
+    const uint32_t *__restrict__ cnt = kp.cnt_cur;
+    const uint32_t *__restrict__ gst = kp.gstart;
+    const unsigned lt = (1u << lane) - 1u;
+    long long Fx = 0, Fy = 0, Fz = 0;
+    int qn = 0, npairs = 0;
+    __syncwarp();
+    while (heads) {
+        const int h = __ffs(heads) - 1;
+        heads &= heads - 1u;
+        const int e = heads ? __ffs(heads) - 1 : nvalid;  // the run is lanes [h, e)
+        const int bx = __shfl_sync(0xffffffffu, cx, h);
+        const int by = __shfl_sync(0xffffffffu, cy, h);
+        const int bz = __shfl_sync(0xffffffffu, cz, h);
+        // window ranges: lane r < NR owns range r (row, and for a periodic
+        // row the wrapped end bin as a second piece)
+        uint32_t q0 = 0, q1 = 0;
+        if (lane < NR) {
+            const int piece = PERIODIC ? lane / (NR / 2) : 0;
+            const int rr = PERIODIC ? lane % (NR / 2) : lane;
+            const int dy = (DIM == 3 ? rr % 3 : rr) - 1;
+            const int dz = DIM == 3 ? rr / 3 - 1 : 0;
+            int y = by + dy, z = bz + dz;
+            bool ok = true;
+            if (PERIODIC) {
+                y = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+                if (DIM == 3) z = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
+            } else {
+                ok = y >= 0 && y < kp.nb[1] && (DIM == 2 || (z >= 0 && z < kp.nb[2]));
+            }
+            int x0 = bx - 1, x1 = bx + 1;
+            if (PERIODIC) {
+                if (piece == 0) {
+                    x0 = max(x0, 0);
+                    x1 = min(x1, kp.nb[0] - 1);
+                } else if (bx - 1 < 0) {
+                    x0 = x1 = kp.nb[0] - 1;
+                } else if (bx + 1 >= kp.nb[0]) {
+                    x0 = x1 = 0;
+                } else {
+                    ok = false;
+                }
+            } else {
+                x0 = max(x0, 0);
+                x1 = min(x1, kp.nb[0] - 1);
+            }
+            if (ok) {
+                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)y + (uint32_t)kp.nb[1] * (uint32_t)z);
+                q0 = min(bin_start(cnt, gst, rowk + (uint32_t)x0), n);
+                q1 = min(bin_start(cnt, gst, rowk + (uint32_t)x1 + 1u), n);
+                q1 = max(q1, q0);
+            }
+        }
+        const uint32_t len = q1 - q0;
+        uint32_t incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane < NR) ws.rows[lane] = make_uint2(q0, incl - len);
+        __syncwarp();
+        // candidate passes of 64: lane takes candidates t0 + lane and
+        // t0 + 32 + lane and tests both against every cell of the run (bit
+        // masks of hits); the hits then go to the queue in ballot rounds
+        int r = 0;
+        const uint32_t first = base + (uint32_t)h;
+        const uint32_t runlen = (uint32_t)(e - h);
+        for (uint32_t t0 = 0; t0 < total; t0 += 64) {
+            uint32_t qa = 0xFFFFFFFFu, qb = 0xFFFFFFFFu;
+            float4 oa = make_float4(0.f, 0.f, 0.f, 0.f), ob = oa;
+            const uint32_t ta = t0 + (uint32_t)lane, tb = ta + 32u;
+            if (ta < total) {
+                while (r + 1 < NR && ws.rows[r + 1].y <= ta) ++r;
+                qa = ws.rows[r].x + (ta - ws.rows[r].y);
+                oa = __ldg(&kp.S[qa]);
+            }
+            if (tb < total) {
+                while (r + 1 < NR && ws.rows[r + 1].y <= tb) ++r;
+                qb = ws.rows[r].x + (tb - ws.rows[r].y);
+                ob = __ldg(&kp.S[qb]);
+            }
+            // squared cutoffs against species 0 (a) and the step to species 1 (b);
+            // no candidate: negative, never in reach
+            float aa = -1.f, ba = 0.f, ab = -1.f, bb = 0.f;
+            uint32_t ma = 0u, mb = 0u;
+            const uint32_t sa = __float_as_uint(oa.w) >> SP_SHIFT, sb = __float_as_uint(ob.w) >> SP_SHIFT;
+            if (two) {
+                if (qa != 0xFFFFFFFFu) {
+                    aa = t.rc2[sa];
+                    ba = t.rc2[MAXS + sa] - aa;
+                }
+                if (qb != 0xFFFFFFFFu) {
+                    ab = t.rc2[sb];
+                    bb = t.rc2[MAXS + sb] - ab;
+                }
+                test_run2<DIM, PERIODIC>(kp, ws, h, e, oa, aa, ba, ob, ab, bb, ma, mb);
+            } else {
+                uint32_t bit = 1u;
+                for (int k = h; k < e; ++k) {
+                    const float4 pi = ws.ipos[k];
+                    const int row = (int)pi.w * MAXS;
+                    float dx, dy, dz, r2;
+                    pair_delta<DIM, PERIODIC>(kp, pi, oa, dx, dy, dz, r2);
+                    if (qa != 0xFFFFFFFFu && r2 < t.rc2[row + (int)sa]) ma |= bit;
+                    pair_delta<DIM, PERIODIC>(kp, pi, ob, dx, dy, dz, r2);
+                    if (qb != 0xFFFFFFFFu && r2 < t.rc2[row + (int)sb]) mb |= bit;
+                    bit <<= 1;
+                }
+            }
+            if (qa - first < runlen) ma &= ~(1u << (qa - first));  // j != i
+            if (qb - first < runlen) mb &= ~(1u << (qb - first));
+            while (__any_sync(0xffffffffu, (ma | mb) != 0u)) {
+                const bool hb = (ma | mb) != 0u;
+                const unsigned hm = __ballot_sync(0xffffffffu, hb);
+                if (hb) {
+                    uint32_t q;
+                    int k;
+                    if (ma) {
+                        k = h + __ffs(ma) - 1;
+                        ma &= ma - 1u;
+                        q = qa;
+                    } else {
+                        k = h + __ffs(mb) - 1;
+                        mb &= mb - 1u;
+                        q = qb;
+                    }
+                    ws.queue[qn + __popc(hm & lt)] = make_uint2(q, (uint32_t)k);
+                }
+                qn += __popc(hm);
+                npairs += __popc(hm);
+                if (qn > QCAP - 32) {
+                    flush_queue<DIM, PERIODIC, STATS>(kp, t, ws, qn, lane, Fx, Fy, Fz);
+                    qn = 0;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    flush_queue<DIM, PERIODIC, STATS>(kp, t, ws, qn, lane, Fx, Fy, Fz);
+    if (STATS) {
+        count += ws.cnt[lane];
+        idsum += ws.ids[lane];
+    } else if (lane == 0) {
+        count += npairs;  // the warp's pairs (profiling; coincident cells included)
+    }
+    return make_float3(__ll2float_rn(Fx) * kp.fq, __ll2float_rn(Fy) * kp.fq, DIM == 3 ? __ll2float_rn(Fz) * kp.fq : 0.f);
+}
+
+// Shared memory of one warp of a pair kernel: the per-lane search stages
+// [RowCap][32] ranges and [LIST_CAP][32] list entries; the warp search uses a
+// WarpSmem (the hybrid kernel reserves the larger of the two).
+template <int DIM, bool PERIODIC, bool WARP>
+constexpr size_t warp_region()
+{
+    constexpr size_t lane_bytes = (size_t)32 * RowCap<DIM, PERIODIC>::value * sizeof(uint2) +
+                                  (size_t)32 * LIST_CAP * sizeof(uint32_t);
+    constexpr size_t r = WARP && sizeof(WarpSmem) > lane_bytes ? sizeof(WarpSmem) : lane_bytes;
+    return (r + 15) & ~(size_t)15;
+}
+
+// Dynamic shared memory of the kernels that evaluate pair forces: species
+// tables and one region per warp.
+template <int DIM, bool PERIODIC, bool WARP>
 constexpr size_t pair_smem()
 {
-    return sizeof(SmemTables) + (size_t)TPB * RowCap<DIM, PERIODIC>::value * sizeof(uint2) +
-           (size_t)TPB * LIST_CAP * sizeof(uint32_t);
+    return sizeof(SmemTables) + (size_t)(TPB / 32) * warp_region<DIM, PERIODIC, WARP>();
 }
 
 // ---------------------------------------------------------------------------
@@ -368,7 +645,7 @@ __device__ __forceinline__ float wrap_axis(float x, float lo, float hi, float L)
 // ---------------------------------------------------------------------------
 // k_step: the particle part of one step.
 // ---------------------------------------------------------------------------
-template <int DIM, bool PERIODIC>
+template <int DIM, bool PERIODIC, bool WARP>
 __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -386,9 +663,13 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     int npairs = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs)  // warp-synchronous: every lane takes part
-        F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused,
-                                             smem + sizeof(SmemTables));
+    if (kp.pairs) {  // warp-synchronous: every lane takes part
+        unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, WARP>();
+        if (WARP)
+            F = pair_force_warp<DIM, PERIODIC, false>(kp, t, wbuf, (uint32_t)j, me, sp, valid, npairs, ids_unused);
+        else
+            F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused, wbuf);
+    }
     if (kp.pair_count) {  // profiling only: in-cutoff pairs of this step
         const int wsum = __reduce_add_sync(0xffffffffu, npairs);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
@@ -975,7 +1256,7 @@ __global__ void k_stage_starts(KP kp, uint32_t *__restrict__ out)
     if (k <= kp.bin_slots) out[k] = bin_start(kp.cnt_cur, kp.gstart, (uint32_t)k);
 }
 
-template <int DIM, bool PERIODIC>
+template <int DIM, bool PERIODIC, bool WARP>
 __global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restrict__ F_out, int32_t *__restrict__ count,
                                                       unsigned long long *__restrict__ idsum)
 {
@@ -991,9 +1272,14 @@ __global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restric
     int cnt = 0;
     unsigned long long ids = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs)  // warp-synchronous: every lane takes part
-        F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), valid, cnt, ids,
-                                            smem + sizeof(SmemTables));
+    if (kp.pairs) {  // warp-synchronous: every lane takes part
+        unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, WARP>();
+        if (WARP)
+            F = pair_force_warp<DIM, PERIODIC, true>(kp, t, wbuf, (uint32_t)j, me, (int)(w >> SP_SHIFT), valid, cnt,
+                                                     ids);
+        else
+            F = pair_force<DIM, PERIODIC, true>(kp, t, (uint32_t)j, me, (int)(w >> SP_SHIFT), valid, cnt, ids, wbuf);
+    }
     if (!valid) return;
     if (id >= kp.n) {
         set_err(kp, ERR_OVERFLOW);
@@ -1066,32 +1352,46 @@ static void allow_smem(K kernel, size_t bytes)
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
 }
 
+template <bool W>
+static void pair_kernel_attributes_of()
+{
+    allow_smem(k_step<2, false, W>, pair_smem<2, false, W>());
+    allow_smem(k_step<2, true, W>, pair_smem<2, true, W>());
+    allow_smem(k_step<3, false, W>, pair_smem<3, false, W>());
+    allow_smem(k_step<3, true, W>, pair_smem<3, true, W>());
+    allow_smem(k_stage_forces<2, false, W>, pair_smem<2, false, W>());
+    allow_smem(k_stage_forces<2, true, W>, pair_smem<2, true, W>());
+    allow_smem(k_stage_forces<3, false, W>, pair_smem<3, false, W>());
+    allow_smem(k_stage_forces<3, true, W>, pair_smem<3, true, W>());
+}
+
 static void pair_kernel_attributes()
 {
     static bool done = false;
     if (done) return;
-    allow_smem(k_step<2, false>, pair_smem<2, false>());
-    allow_smem(k_step<2, true>, pair_smem<2, true>());
-    allow_smem(k_step<3, false>, pair_smem<3, false>());
-    allow_smem(k_step<3, true>, pair_smem<3, true>());
-    allow_smem(k_stage_forces<2, false>, pair_smem<2, false>());
-    allow_smem(k_stage_forces<2, true>, pair_smem<2, true>());
-    allow_smem(k_stage_forces<3, false>, pair_smem<3, false>());
-    allow_smem(k_stage_forces<3, true>, pair_smem<3, true>());
+    pair_kernel_attributes_of<false>();
+    pair_kernel_attributes_of<true>();
     done = true;
+}
+
+// The 3^d window uses the warp search, the 2^d window the per-lane search.
+template <int DIM, bool PERIODIC, bool W>
+static void step_launch(const KP &kp, int cur, cudaStream_t st)
+{
+    k_step<DIM, PERIODIC, W><<<(unsigned)((kp.n + TPB - 1) / TPB), TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
 }
 
 cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (kp.n == 0) return cudaSuccess;
     pair_kernel_attributes();
-    const unsigned nb = blocks_for(kp.n);
+    const bool w = kp.search == 1;
     if (kp.dim == 2) {
-        if (kp.periodic) k_step<2, true><<<nb, TPB, pair_smem<2, true>(), st>>>(kp, cur);
-        else k_step<2, false><<<nb, TPB, pair_smem<2, false>(), st>>>(kp, cur);
+        if (kp.periodic) w ? step_launch<2, true, true>(kp, cur, st) : step_launch<2, true, false>(kp, cur, st);
+        else w ? step_launch<2, false, true>(kp, cur, st) : step_launch<2, false, false>(kp, cur, st);
     } else {
-        if (kp.periodic) k_step<3, true><<<nb, TPB, pair_smem<3, true>(), st>>>(kp, cur);
-        else k_step<3, false><<<nb, TPB, pair_smem<3, false>(), st>>>(kp, cur);
+        if (kp.periodic) w ? step_launch<3, true, true>(kp, cur, st) : step_launch<3, true, false>(kp, cur, st);
+        else w ? step_launch<3, false, true>(kp, cur, st) : step_launch<3, false, false>(kp, cur, st);
     }
     if (launches) ++*launches;
     return cudaGetLastError();
@@ -1207,13 +1507,16 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
     if (kp.n == 0) return cudaSuccess;
     pair_kernel_attributes();
     const unsigned nb = blocks_for(kp.n);
+#define STAGE_F(D, P, W) k_stage_forces<D, P, W><<<nb, TPB, pair_smem<D, P, W>(), st>>>(kp, F, count, idsum)
+    const bool w = kp.search == 1;
     if (kp.dim == 2) {
-        if (kp.periodic) k_stage_forces<2, true><<<nb, TPB, pair_smem<2, true>(), st>>>(kp, F, count, idsum);
-        else k_stage_forces<2, false><<<nb, TPB, pair_smem<2, false>(), st>>>(kp, F, count, idsum);
+        if (kp.periodic) w ? STAGE_F(2, true, true) : STAGE_F(2, true, false);
+        else w ? STAGE_F(2, false, true) : STAGE_F(2, false, false);
     } else {
-        if (kp.periodic) k_stage_forces<3, true><<<nb, TPB, pair_smem<3, true>(), st>>>(kp, F, count, idsum);
-        else k_stage_forces<3, false><<<nb, TPB, pair_smem<3, false>(), st>>>(kp, F, count, idsum);
+        if (kp.periodic) w ? STAGE_F(3, true, true) : STAGE_F(3, true, false);
+        else w ? STAGE_F(3, false, true) : STAGE_F(3, false, false);
     }
+#undef STAGE_F
     return cudaGetLastError();
 }
 

@@ -30,10 +30,13 @@ def main(argv=None):
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--adjoint", type=int, default=0)
     ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--search-mode", type=int, default=None)
     a = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("profile_run needs a CUDA device")
     p, pos, sp = wl.initial_state(a.workload, n=a.n)
+    if a.search_mode is not None:
+        p = dict(p, search_mode=a.search_mode)
     dev = torch.device("cuda:0")
     dpos = torch.from_numpy(pos).to(dev)
     dsp = torch.from_numpy(sp).to(dev)

@@ -366,3 +366,43 @@ def test_set_params_changes_model_constants():
         with pytest.raises(chemo.ChemoError):
             chemo.chemo_set_params(sim, dict(p, grid=[65, 64, 1]))
     assert_step_matches(q, pos, sp, np.zeros(orc.grid_shape(p), np.float32), pos_g, sp_g, c_g)
+
+
+@pytest.mark.parametrize("name,over", [
+    ("walls_grid_2d", dict(grid=[64, 64, 1])),
+    ("walls_grid_2d", dict(boundary=1, pde_bc=2, grid=[64, 64, 1])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32], boundary=1, pde_bc=2)),
+])
+def test_warp_and_lane_search_agree_bitwise(name, over):
+    """The warp-cooperative 3^d search and the per-lane 2^d search round
+    every pair term the same way and sum exactly: identical forces, counts
+    and neighbour id sums."""
+    p, pos, sp = wl.initial_state(name, n=30011, **over)
+    outs = []
+    # 2^d per lane; 3^d warp search always; 3^d hybrid (default); 3^d per lane
+    for mode, runs in ((2, 0), (1, 32), (1, 0), (3, 0)):
+        with make_sim(dict(p, search_mode=mode, warp_runs=runs), pos, sp) as sim:
+            assert chemo.chemo_get_info(sim)["search_mode"] == mode
+            outs.append(gpu_forces(sim))
+    for o in outs[1:]:
+        for a, b in zip(outs[0], o):
+            np.testing.assert_array_equal(a, b)
+    assert_forces_match(p, outs[0][0], outs[0][1], outs[0][2], pos, sp)
+
+
+def test_warp_search_dense_cluster_bitwise():
+    """Thousands of cells in a few bins (runs of 32, windows of thousands of
+    candidates, queue flushes mid-run): the warp search equals the per-lane
+    search bit for bit."""
+    p = wl.params("walls_grid_2d", grid=[16, 16, 1])
+    rng = np.random.default_rng(7)
+    pos = (0.5 + 0.004 * rng.standard_normal((4000, 2))).astype(np.float32)
+    sp = wl.half_species(4000, 2)
+    outs = []
+    for mode, runs in ((3, 0), (1, 32)):
+        with make_sim(dict(p, search_mode=mode, warp_runs=runs), pos, sp) as sim:
+            outs.append(gpu_forces(sim))
+    for a, b in zip(outs[0], outs[1]):
+        np.testing.assert_array_equal(a, b)
+    assert_forces_match(p, outs[1][0], outs[1][1], outs[1][2], pos, sp)
