@@ -33,6 +33,8 @@
 #define ORC_MAX_SPECIES 8
 
 /* Model parameters, as the oracle reads them (its own definition). */
+#define ORC_PI 3.14159265358979323846
+
 typedef struct orc_params {
     int32_t dim;          /* 2 or 3 (the paper works in 2D, Sect. 2) */
     int32_t boundary;     /* 0 reflecting walls (Sect. 3.2), 1 periodic (Sect. 4) */
@@ -59,6 +61,10 @@ typedef struct orc_params {
     int32_t pde_substeps;                /* 0 = automatic (see orc_substeps) */
     double dt;
     uint64_t seed;
+    int32_t move_scheme;   /* 0 Euler-Maruyama (Eq. (2)), 1 tamed Euler (Sect. 3.2, Eq. sde_ETamed) */
+    int32_t hard_sphere;   /* 1: overlap correction after the move (Sect. 3.2, hard spheres) */
+    int32_t deposit_kernel;/* 0 cloud-in-cell (Sect. 2.3), 1 Gaussian kernel density estimate (Sect. 2.3) */
+    double kde_range;      /* KDE truncation radius in bandwidths (bandwidth = cell diameter) */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -260,8 +266,10 @@ static double orc_max_cutoff(const orc_params *p)
     double m = 0.0;
     for (int s = 0; s < p->n_species; ++s)
         for (int t = 0; t < p->n_species; ++t) {
-            double rc = p->cutoff_factor * 0.5 * (p->diameter[s] + p->diameter[t]);
+            double eps = 0.5 * (p->diameter[s] + p->diameter[t]);
+            double rc = p->cutoff_factor * eps;
             if (rc > m) m = rc;
+            if (p->hard_sphere && eps > m) m = eps;  /* contact distance of the correction */
         }
     return m;
 }
@@ -717,9 +725,21 @@ void orc_move(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const ui
         orc_normals(p->seed, ids[i], (uint64_t)step, ORC_TAG_MOVE, xi);
         int s = sp[i];
         double amp = sqrt(2.0 * p->D[s] * p->dt);
+        /* drift increment: dt a (Euler-Maruyama) or dt a / (1 + dt |a|)
+         * (tamed Euler; the paper tames the interaction drift of the alpha
+         * equation, here the whole drift, which is that for chi_s = 0) */
+        double scale = p->dt;
+        if (p->move_scheme == 1) {
+            double an = 0.0;
+            for (int a = 0; a < d; ++a) {
+                double v = F[i * d + a] + drift[i * d + a];
+                an += v * v;
+            }
+            scale = p->dt / (1.0 + p->dt * sqrt(an));
+        }
         for (int a = 0; a < d; ++a) {
             double x0 = pos[i * d + a];
-            double x1 = x0 + p->dt * (F[i * d + a] + drift[i * d + a]) + amp * xi[a];
+            double x1 = x0 + scale * (F[i * d + a] + drift[i * d + a]) + amp * xi[a];
             double xb;
             if (p->boundary == 1) {
                 xb = orc_boundary(p, a, x1);
@@ -746,18 +766,106 @@ void orc_move(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const ui
     free(conc);
 }
 
-/* Full step: orc_move, then the density estimate at X^{n+1} and the PDE
- * substeps c^n -> c^{n+1} (c in place; needs no grid when chem_mode = 1). */
+/* Hard-sphere overlap correction (Sect. 3.2): after the move, every pair
+ * closer than the contact distance eps_ij = (sigma_i + sigma_j)/2 is pushed
+ * apart along the line of centres by twice the penetration depth
+ * d_p = eps_ij - d_ij; cell i takes the fraction D_i / (D_i + D_j) of it (one
+ * half each when both are immobile). All corrections are computed from the
+ * moved positions and applied together, then the boundary rule again. disp
+ * (nullable) follows the corrected positions. Coincident cells (d_ij = 0)
+ * have no line of centres and are left alone. */
+void orc_hard_sphere(const orc_params *p, int64_t n, double *pos, const uint8_t *sp, double *disp)
+{
+    int d = p->dim;
+    double *dx = (double *)calloc((size_t)(n * d + 1), sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double diff[3] = {0, 0, 0}, r2 = 0.0;
+            for (int a = 0; a < d; ++a) {
+                diff[a] = orc_wrap_delta(p, a, pos[i * d + a] - pos[j * d + a]);
+                r2 += diff[a] * diff[a];
+            }
+            double contact = 0.5 * (p->diameter[sp[i]] + p->diameter[sp[j]]);
+            double r = sqrt(r2);
+            if (!(r > 0.0) || !(r < contact)) continue;
+            double Di = p->D[sp[i]], Dj = p->D[sp[j]];
+            double wi = Di + Dj > 0.0 ? Di / (Di + Dj) : 0.5;
+            double move = 2.0 * (contact - r) * wi;
+            for (int a = 0; a < d; ++a) dx[i * d + a] += move * diff[a] / r;
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int a = 0; a < d; ++a) {
+            double x0 = pos[i * d + a];
+            double x1 = x0 + dx[i * d + a];
+            double xb = orc_boundary(p, a, x1);
+            if (disp) disp[i * d + a] += p->boundary == 1 ? x1 - x0 : xb - x0;
+            pos[i * d + a] = xb;
+        }
+    free(dx);
+}
+
+/* Gaussian kernel density estimate of the cell densities at the grid nodes
+ * (Sect. 2.3 and the density listing of Sect. 3): node l gets
+ * rho_s(p_l) = sum_{i of species s} K_s(p_l - X_i) with
+ * K_s(x) = (2 pi sigma_s^2)^(-d/2) exp(-|x|^2 / (2 sigma_s^2)), the bandwidth
+ * sigma_s the species' diameter, summed over the cells within kde_range
+ * bandwidths (minimum image when periodic). Outputs S_l = dt sum_s k_s
+ * rho_s(p_l) and R_l = sum_s kappa_s rho_s(p_l), the forms of orc_deposit. */
+void orc_kde_deposit(const orc_params *p, int64_t n, const double *pos, const uint8_t *sp, double *S,
+                     double *R)
+{
+    int d = p->dim;
+    int N0 = orc_gdim(p, 0), N1 = orc_gdim(p, 1), N2 = orc_gdim(p, 2);
+#pragma omp parallel for schedule(static)
+    for (int64_t z = 0; z < N2; ++z)
+        for (int64_t y = 0; y < N1; ++y)
+            for (int64_t x = 0; x < N0; ++x) {
+                int k[3] = {(int)x, (int)y, (int)z};
+                double node[3] = {0, 0, 0};
+                for (int a = 0; a < d; ++a) node[a] = p->lo[a] + k[a] * orc_grid_h(p, a);
+                double s_acc = 0.0, r_acc = 0.0;
+                for (int64_t i = 0; i < n; ++i) {
+                    int s = sp[i];
+                    double ks = p->secrete[s], kap = p->consume[s];
+                    if (ks == 0.0 && kap == 0.0) continue;
+                    double sig = p->diameter[s];
+                    double r2 = 0.0;
+                    for (int a = 0; a < d; ++a) {
+                        double dd = orc_wrap_delta(p, a, node[a] - pos[i * d + a]);
+                        r2 += dd * dd;
+                    }
+                    double R = p->kde_range * sig;
+                    if (!(r2 < R * R)) continue;
+                    double K = pow(2.0 * ORC_PI * sig * sig, -0.5 * d) * exp(-r2 / (2.0 * sig * sig));
+                    s_acc += p->dt * ks * K;
+                    r_acc += kap * K;
+                }
+                int64_t g = orc_gidx(p, k);
+                S[g] = s_acc;
+                R[g] = r_acc;
+            }
+}
+
+/* Full step: orc_move (and the hard-sphere correction when enabled), then
+ * the density estimate at X^{n+1} and the PDE substeps c^n -> c^{n+1} (c in
+ * place; needs no grid when chem_mode = 1). */
 void orc_step(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const uint32_t *ids,
               double *c, int64_t step, double *disp, double *F_out, double *drift_out)
 {
     orc_move(p, n, pos, sp, ids, c, step, disp, F_out, drift_out);
+    if (p->hard_sphere) orc_hard_sphere(p, n, pos, sp, disp);
     if (p->chem_mode != 0) return;
     int64_t G = orc_grid_size(p);
     double *S = (double *)malloc(sizeof(double) * (size_t)G);
     double *R = (double *)malloc(sizeof(double) * (size_t)G);
     double *tmp = (double *)malloc(sizeof(double) * (size_t)G);
-    orc_deposit(p, n, pos, sp, S, R);
+    if (p->deposit_kernel == 1)
+        orc_kde_deposit(p, n, pos, sp, S, R);
+    else
+        orc_deposit(p, n, pos, sp, S, R);
     int s = orc_substeps(p);
     for (int m = 0; m < s; ++m) {
         orc_pde_substep(p, c, S, R, s, tmp);

@@ -73,6 +73,10 @@ class OrcParams(ctypes.Structure):
         ("pde_substeps", ctypes.c_int32),
         ("dt", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("move_scheme", ctypes.c_int32),
+        ("hard_sphere", ctypes.c_int32),
+        ("deposit_kernel", ctypes.c_int32),
+        ("kde_range", ctypes.c_double),
     ]
 
 
@@ -117,6 +121,10 @@ def make_params(d: dict) -> OrcParams:
     p.pde_substeps = int(d.get("pde_substeps", 0))
     p.dt = float(d["dt"])
     p.seed = int(d.get("seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    p.move_scheme = int(d.get("move_scheme", 0))
+    p.hard_sphere = int(d.get("hard_sphere", 0))
+    p.deposit_kernel = int(d.get("deposit_kernel", 0))
+    p.kde_range = _f32(d.get("kde_range", 0.0) or 3.0)
     return p
 
 
@@ -150,6 +158,8 @@ def _declare(L):
     L.orc_drift.argtypes = [P, i64, vp, vp, vp, vp]
     L.orc_conc.argtypes = [P, i64, vp, vp, vp]
     L.orc_deposit.argtypes = [P, i64, vp, vp, vp, vp]
+    L.orc_kde_deposit.argtypes = [P, i64, vp, vp, vp, vp]
+    L.orc_hard_sphere.argtypes = [P, i64, vp, vp, vp]
     L.orc_pde_substep.argtypes = [P, vp, vp, vp, ctypes.c_int, vp]
     L.orc_move.argtypes = [P, i64, vp, vp, vp, vp, i64, vp, vp, vp]
     L.orc_step.argtypes = [P, i64, vp, vp, vp, vp, i64, vp, vp, vp]
@@ -270,6 +280,28 @@ def deposit(params: dict, pos, species) -> tuple[np.ndarray, np.ndarray]:
     R = np.zeros(grid_shape(params))
     lib().orc_deposit(ctypes.byref(p), pos.shape[0], _ptr(pos), _ptr(sp), _ptr(S), _ptr(R))
     return S, R
+
+
+def kde_deposit(params: dict, pos, species) -> tuple[np.ndarray, np.ndarray]:
+    """Gaussian kernel density estimate at the nodes (source S, consumption R)."""
+    p = make_params(params)
+    pos = _pos(pos, p.dim)
+    sp = _u8(species)
+    S = np.zeros(grid_shape(params))
+    R = np.zeros(grid_shape(params))
+    lib().orc_kde_deposit(ctypes.byref(p), pos.shape[0], _ptr(pos), _ptr(sp), _ptr(S), _ptr(R))
+    return S, R
+
+
+def hard_sphere(params: dict, pos, species, disp=None):
+    """Hard-sphere overlap correction of positions (returns new positions
+    and, when given, the updated displacement)."""
+    p = make_params(params)
+    x = _pos(pos, p.dim).copy()
+    sp = _u8(species)
+    dd = None if disp is None else np.ascontiguousarray(np.asarray(disp, dtype=np.float64)).copy()
+    lib().orc_hard_sphere(ctypes.byref(p), x.shape[0], _ptr(x), _ptr(sp), None if dd is None else _ptr(dd))
+    return (x, dd) if disp is not None else x
 
 
 def pde_substep(params: dict, c, S=None, R=None, s: int = 1) -> np.ndarray:
