@@ -111,6 +111,16 @@ typedef struct chemo_params {
     int32_t warp_runs;           /* search_mode 1: a warp whose 32 cells fall in at most
                                     this many bins searches them together, a sparser warp
                                     searches per lane (0 = 8; 1..32) */
+    int32_t move_scheme;         /* 0 Euler-Maruyama (Eq. (2)); 1 tamed Euler (Sect. 3.2):
+                                    drift increment dt a / (1 + dt |a|), a the whole drift */
+    int32_t hard_sphere;         /* 1: after the move, overlapping pairs (closer than
+                                    (sigma_i + sigma_j)/2) are pushed apart along the line of
+                                    centres by twice the penetration, split D_i/(D_i+D_j)
+                                    (Sect. 3.2), then the boundary rule again */
+    int32_t deposit_kernel;      /* 0 cloud-in-cell (Sect. 2.3); 1 Gaussian kernel density
+                                    estimate with bandwidth sigma_s gathered at every node
+                                    (Sect. 2.3), truncated at kde_range bandwidths */
+    float kde_range;             /* KDE truncation radius in bandwidths (0 = 3) */
 } chemo_params;
 
 /* Layout facts of a simulation (read-only). */

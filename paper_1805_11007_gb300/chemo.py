@@ -66,6 +66,10 @@ class chemo_params(ctypes.Structure):
         ("bin_order", ctypes.c_int32),
         ("pde_overlap", ctypes.c_int32),
         ("warp_runs", ctypes.c_int32),
+        ("move_scheme", ctypes.c_int32),
+        ("hard_sphere", ctypes.c_int32),
+        ("deposit_kernel", ctypes.c_int32),
+        ("kde_range", ctypes.c_float),
     ]
 
 
@@ -130,6 +134,10 @@ def make_params(d: dict) -> chemo_params:
     p.bin_order = int(d.get("bin_order", 0))
     p.pde_overlap = int(d.get("pde_overlap", 0))
     p.warp_runs = int(d.get("warp_runs", 0))
+    p.move_scheme = int(d.get("move_scheme", 0))
+    p.hard_sphere = int(d.get("hard_sphere", 0))
+    p.deposit_kernel = int(d.get("deposit_kernel", 0))
+    p.kde_range = float(d.get("kde_range", 0.0))
     return p
 
 

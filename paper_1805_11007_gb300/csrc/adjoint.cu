@@ -385,6 +385,8 @@ int check_adjoint_model(const chemo_sim *s)
     const chemo_params &p = s->prm;
     if (s->kp.layers > 1) return eng_fail(CHEMO_ENOTSUP, "the adjoint covers single simulations (replicates = 1)");
     if (p.reactions) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover type switching (reactions = 1)");
+    if (p.move_scheme || p.hard_sphere || p.deposit_kernel)
+        return eng_fail(CHEMO_ENOTSUP, "the adjoint covers the Euler-Maruyama move with the CIC deposit only");
     for (int i = 0; i < p.n_species; ++i)
         if (p.consume[i] != 0.f) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover consumption (consume != 0)");
     if (p.chem_mode == 0 && p.pde_bc == 1) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover Dirichlet walls");

@@ -135,6 +135,16 @@ int check_params(const chemo_params &p)
     if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
     if (p.search_mode < 0 || p.search_mode > 3) return fail(CHEMO_EINVAL, "search_mode must be 0, 1, 2 or 3");
     if (p.warp_runs < 0 || p.warp_runs > 32) return fail(CHEMO_EINVAL, "warp_runs must be 0..32");
+    if (p.move_scheme != 0 && p.move_scheme != 1) return fail(CHEMO_EINVAL, "move_scheme must be 0 or 1");
+    if (p.hard_sphere != 0 && p.hard_sphere != 1) return fail(CHEMO_EINVAL, "hard_sphere must be 0 or 1");
+    if (p.deposit_kernel != 0 && p.deposit_kernel != 1) return fail(CHEMO_EINVAL, "deposit_kernel must be 0 or 1");
+    if (!(p.kde_range >= 0.f) || !std::isfinite(p.kde_range)) return fail(CHEMO_EINVAL, "kde_range must be >= 0");
+    if (p.deposit_kernel == 1) {
+        if (p.chem_mode != 0) return fail(CHEMO_EINVAL, "deposit_kernel 1 needs the grid (chem_mode 0)");
+        for (int s = 0; s < p.n_species; ++s)
+            if ((p.secrete[s] != 0.f || p.consume[s] != 0.f) && !(p.diameter[s] > 0.f))
+                return fail(CHEMO_EINVAL, "deposit_kernel 1: species %d deposits but has no diameter (bandwidth)", s);
+    }
     if (p.bin_order < 0 || p.bin_order > 2) return fail(CHEMO_EINVAL, "bin_order must be 0, 1 or 2");
     if (p.pde_overlap < 0 || p.pde_overlap > 2) return fail(CHEMO_EINVAL, "pde_overlap must be 0, 1 or 2");
     if (p.chem_mode == 0) {
@@ -215,6 +225,37 @@ void fill_model(const chemo_params &p, KP &kp)
     kp.fq_inv = (float)(1.0 / (double)kp.fq);
     kp.inter_f = p.inter;
     kp.reactions = p.reactions ? 1 : 0;
+    // variants: tamed move, hard-sphere tables, kernel density constants
+    kp.move_scheme = p.move_scheme;
+    kp.hard_sphere = p.hard_sphere;
+    for (int s = 0; s < MAXS; ++s)
+        for (int t = 0; t < MAXS; ++t) {
+            const int i = s * MAXS + t;
+            const bool in = s < p.n_species && t < p.n_species;
+            kp.hs_contact[i] = in ? (float)(0.5 * ((double)p.diameter[s] + (double)p.diameter[t])) : 0.f;
+            const double Ds = in ? (double)p.D[s] : 0.0, Dt = in ? (double)p.D[t] : 0.0;
+            kp.hs_share[i] = (float)(Ds + Dt > 0.0 ? Ds / (Ds + Dt) : 0.5);
+        }
+    kp.kde = p.deposit_kernel == 1 ? 1 : 0;
+    const double krange = p.kde_range > 0.f ? (double)p.kde_range : 3.0;
+    for (int s = 0; s < MAXS; ++s) {
+        const double sig = s < p.n_species ? (double)p.diameter[s] : 0.0;
+        const bool dep = s < p.n_species && (p.secrete[s] != 0.f || p.consume[s] != 0.f) && sig > 0.0;
+        const double norm = dep ? std::pow(2.0 * 3.14159265358979323846 * sig * sig, -0.5 * p.dim) : 0.0;
+        kp.kde_r2[s] = dep ? (float)(krange * sig * krange * sig) : -1.f;
+        kp.kde_c[s] = dep ? (float)(0.5 / (sig * sig)) : 0.f;
+        kp.kde_src[s] = dep ? (float)(p.dt * (double)p.secrete[s] * norm) : 0.f;
+        kp.kde_cons[s] = dep ? (float)((double)p.consume[s] * norm) : 0.f;
+    }
+    double smax = 0.0, rmax = 0.0;
+    for (int s = 0; s < MAXS; ++s) {
+        smax = std::max(smax, (double)std::fabs(kp.kde_src[s]));
+        rmax = std::max(rmax, (double)std::fabs(kp.kde_cons[s]));
+    }
+    kp.kde_qs = (float)std::ldexp(smax > 0.0 ? smax : 1.0, -32);
+    kp.kde_qr = (float)std::ldexp(rmax > 0.0 ? rmax : 1.0, -32);
+    kp.kde_qs_inv = (float)(1.0 / (double)kp.kde_qs);
+    kp.kde_qr_inv = (float)(1.0 / (double)kp.kde_qr);
     kp.dt = (float)p.dt;
     kp.dt_d = p.dt;
     kp.seed_lo = (uint32_t)p.seed;
@@ -240,12 +281,19 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         kp.inv_b[a] = 0.f;
         kp.bside[a] = 0.f;
     }
-    const double rc = max_cutoff(p);
-    const bool pairs = rc > 0.0 && p.inter != 0.f;
+    const double rc_force = max_cutoff(p);
+    const bool pairs = rc_force > 0.0 && p.inter != 0.f;
+    double contact = 0.0;  // hard-sphere contact distance: searched like a cutoff
+    if (p.hard_sphere)
+        for (int s = 0; s < p.n_species; ++s)
+            for (int t = 0; t < p.n_species; ++t)
+                contact = std::max(contact, 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]));
+    const double rc = std::max(pairs ? rc_force : 0.0, contact);
+    const bool search_on = rc > 0.0;
     int search = (p.search_mode == 0 || !pairs) ? 1 : p.search_mode;
     kp.pairs = pairs ? 1 : 0;
     double bmin;
-    if (pairs) {
+    if (search_on) {
         bmin = (search == 2 ? 2.0 : 1.0) * rc * (1.0 + 1.0 / 4096.0);
         if (p.bin_side > 0.f) {
             if ((double)p.bin_side < bmin)
@@ -261,12 +309,18 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         bmin = p.bin_side > 0.f ? (double)p.bin_side
                                 : std::pow(vol * (double)(1 << p.dim) / std::max(per_layer, 1.0), 1.0 / p.dim);
     }
+    double kde_radius = 0.0;  // largest truncation radius of the density kernel
+    if (p.deposit_kernel == 1) {  // the density window spans at most 3 bins per side
+        const double krange = p.kde_range > 0.f ? (double)p.kde_range : 3.0;
+        for (int s = 0; s < p.n_species; ++s) kde_radius = std::max(kde_radius, krange * (double)p.diameter[s]);
+        bmin = std::max(bmin, kde_radius / 3.0);
+    }
     int64_t total = 1;
     for (int a = 0; a < p.dim; ++a) {
         const double L = p.hi[a] - p.lo[a];
         double m = std::floor(L / bmin);
         if (m < 1.0) m = 1.0;
-        if (!pairs) m = std::min(m, 1024.0);
+        if (!search_on) m = std::min(m, 1024.0);
         if (m > 65535.0) return fail(CHEMO_EINVAL, "axis %d needs %g bins: cutoff too small for the box", a, m);
         kp.nb[a] = (int)m;
         kp.inv_b[a] = (float)((double)kp.nb[a] / L);
@@ -274,7 +328,17 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
         total *= kp.nb[a];
     }
     if (p.dim == 2) kp.nb[2] = std::max(kp.layers, 1);  // replicates as the third bin index
-    if (pairs && kp.periodic) {
+    kp.kde_win = 0;
+    if (p.deposit_kernel == 1) {
+        for (int a = 0; a < p.dim; ++a)
+            kp.kde_win = std::max(kp.kde_win, (int)std::ceil(kde_radius / (double)kp.bside[a] * (1.0 - 1e-9)));
+        if (kp.periodic)
+            for (int a = 0; a < p.dim; ++a)
+                if (kp.nb[a] < 2 * kp.kde_win + 1)
+                    return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins: too few for the density kernel's range",
+                                a, kp.nb[a]);
+    }
+    if (search_on && kp.periodic) {
         for (int a = 0; a < p.dim; ++a) {
             if (search != 2 && kp.nb[a] < 3)
                 return fail(CHEMO_EINVAL, "periodic axis %d holds %d bins of side >= r_c; need >= 3 (box too small "
@@ -303,6 +367,9 @@ int fill_grid(const chemo_params &p, KP &kp)
     for (int a = 0; a < 3; ++a) {
         kp.g[a] = 1;
         kp.inv_h[a] = kp.inv_2h[a] = kp.inv_h2[a] = 0.f;
+        kp.hgrid[a] = 0.f;
+        kp.hgrid_d[a] = 0.0;
+        kp.lo_d[a] = a < p.dim ? p.lo[a] : 0.0;
     }
     kp.pde_bc = p.pde_bc;
     kp.substeps = 1;
@@ -315,6 +382,8 @@ int fill_grid(const chemo_params &p, KP &kp)
         G *= p.grid[a];
         const double h = grid_h(p, a);
         kp.inv_h[a] = (float)(1.0 / h);
+        kp.hgrid[a] = (float)h;
+        kp.hgrid_d[a] = h;
         kp.inv_2h[a] = (float)(0.5 / h);
         kp.inv_h2[a] = (float)(1.0 / (h * h));
     }
@@ -326,7 +395,9 @@ int fill_grid(const chemo_params &p, KP &kp)
     kp.G = G;
     kp.substeps = resolve_substeps(p);
     kp.dts = (float)(p.dt / kp.substeps);
-    kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1) ? 1 : 0;
+    // one substep: the CIC deposit goes straight into c^{n+1} (the density
+    // kernel writes a source grid instead)
+    kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1 && p.deposit_kernel == 0) ? 1 : 0;
     kp.overlap = kp.fused_deposit && p.pde_overlap != 1;
     return CHEMO_OK;
 }
@@ -360,6 +431,27 @@ int sort_from_u(chemo_sim *s, const KP &k, cudaStream_t st)
     return CHEMO_OK;
 }
 
+// The part of a step after the particle kernel: offsets and placement of the
+// moved cells (with the CIC deposit, and the step counter advanced), the
+// hard-sphere correction with its own re-sort when enabled, and the
+// kernel density gather into the source grid when enabled. Flips the count
+// buffers once per sort.
+int enqueue_sort_and_density(chemo_sim *s, const KP &kp, cudaStream_t st, int *launches)
+{
+    CUDA_TRY(launch_scan(kp, st, launches));
+    CUDA_TRY(launch_scatter(kp, s->cur, kp.hard_sphere ? 0 : 1, st, launches));
+    s->cntp ^= 1;
+    if (kp.hard_sphere) {
+        const KP k2 = view(s);  // S = moved cells, cnt_cur their bins
+        CUDA_TRY(launch_hard_sphere(k2, st, launches));
+        CUDA_TRY(launch_scan(k2, st, launches));
+        CUDA_TRY(launch_scatter(k2, s->cur, 1, st, launches));
+        s->cntp ^= 1;
+    }
+    if (kp.kde && kp.has_grid) CUDA_TRY(launch_kde(view(s), kp.srcg, kp.Rg, st, launches));
+    return CHEMO_OK;
+}
+
 // Enqueues one step on st. Counts launched kernels into *launches.
 int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
 {
@@ -375,11 +467,9 @@ int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
     }
     CUDA_TRY(launch_step_particles(kp, s->cur, st, launches));
     if (overlap) CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
-    CUDA_TRY(launch_scan(kp, st, launches));
-    CUDA_TRY(launch_scatter(kp, s->cur, 1, st, launches));
+    if (int r = enqueue_sort_and_density(s, kp, st, launches)) return r;
     if (grid && !kp.fused_deposit) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
     if (grid) s->cur = kp.fused_deposit ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
-    s->cntp ^= 1;
     s->step += 1;
     return CHEMO_OK;
 }
@@ -663,7 +753,8 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
         return r;
     }
     // launches per step: particles, scan, scatter, and the PDE substeps
-    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.substeps : 0);
+    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.substeps : 0) +
+                           (kp.hard_sphere ? (n > 0 ? 3 : 2) : 0) + (kp.kde && kp.has_grid ? 1 : 0);
     *out = s;
     return CHEMO_OK;
 }
@@ -970,6 +1061,7 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     const bool grid = s->kp.has_grid && s->kp.chem_mode == 0;
     const bool overlap = grid && s->kp.overlap;
     const bool fused = grid && s->kp.fused_deposit;
+    const bool variants = s->kp.hard_sphere || s->kp.kde;
     // in-cutoff pairs are counted into ctl + 8 while profiling
     unsigned long long *pc = reinterpret_cast<unsigned long long *>(s->kp.tile_ctr + 8);
     CUDA_TRY(cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
@@ -1005,9 +1097,15 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         if (err == cudaSuccess) err = cudaEventRecord(e[1], st);
         if (overlap && err == cudaSuccess) err = cudaStreamWaitEvent(st, s->ev_join, 0);
         if (err == cudaSuccess) err = cudaEventRecord(e[4], st);
-        if (err == cudaSuccess) err = launch_scan(kp, st, nullptr);
+        if (err == cudaSuccess && !variants) err = launch_scan(kp, st, nullptr);
         if (err == cudaSuccess) err = cudaEventRecord(e[5], st);
-        if (err == cudaSuccess) err = launch_scatter(kp, s->cur, 1, st, nullptr);
+        if (err == cudaSuccess && !variants) err = launch_scatter(kp, s->cur, 1, st, nullptr);
+        if (err == cudaSuccess && variants) {
+            // the scan, scatter, correction and density kernels are timed
+            // together in the scatter slot
+            if (enqueue_sort_and_density(s, kp, st, nullptr) != CHEMO_OK) err = cudaErrorUnknown;
+            s->cntp ^= 1;  // the sequence flipped the count buffers itself; undone by the flip below
+        }
         if (err == cudaSuccess) err = cudaEventRecord(e[6], st);
         if (grid && !fused) {
             if (err == cudaSuccess) err = cudaEventRecord(e[2], st);
@@ -1170,7 +1268,10 @@ int chemo_stage_deposit(chemo_sim *s, float *S_out, float *R_out, int mem_kind, 
     if (int r = scratch(s, 2 * gb, &tmp)) return r;
     float *dS = (float *)tmp, *dR = (float *)((char *)tmp + gb);
     CUDA_TRY(cudaMemsetAsync(tmp, 0, 2 * gb, st));
-    CUDA_TRY(launch_stage_deposit(view(s), dS, dR, st));
+    if (s->kp.kde)
+        CUDA_TRY(launch_kde(view(s), dS, dR, st, nullptr));
+    else
+        CUDA_TRY(launch_stage_deposit(view(s), dS, dR, st));
     if (int r = stage_out(s, S_out, dS, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
     if (int r = stage_out(s, R_out, dR, (size_t)s->kp.G * sizeof(float), mem_kind, st)) return r;
     return finish(s, mem_kind, stream);

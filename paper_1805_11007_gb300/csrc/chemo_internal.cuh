@@ -64,6 +64,21 @@ struct KP {
     float rk0[MAXS], rkc[MAXS];  // switching rates
     int rto[MAXS];
     int reactions;
+    // variants
+    int move_scheme;             // 0 Euler-Maruyama, 1 tamed Euler
+    int hard_sphere;             // overlap correction after the move
+    float hs_contact[MAXS * MAXS];  // contact distance (sigma_s + sigma_t)/2
+    float hs_share[MAXS * MAXS];    // share of the separation taken by the first: D_s/(D_s+D_t)
+    int kde;                     // 1: Gaussian kernel density deposit (gathered per node)
+    int kde_win;                 // bins searched on each side of a node's bin
+    float kde_r2[MAXS];          // squared truncation radius (kde_range sigma_s)^2
+    float kde_c[MAXS];           // 1 / (2 sigma_s^2)
+    float kde_src[MAXS];         // dt k_s (2 pi sigma_s^2)^(-d/2)
+    float kde_cons[MAXS];        // kappa_s (2 pi sigma_s^2)^(-d/2)
+    float kde_qs, kde_qs_inv;    // fixed-point quantum of the source sum (2^-32 of its largest term)
+    float kde_qr, kde_qr_inv;    // the same for the consumption sum
+    float hgrid[3];              // grid spacing per axis
+    double lo_d[3], hgrid_d[3];  // box corner and grid spacing in double (node positions)
     float dt;
     double dt_d;                 // dt in double (switching decision)
     uint32_t seed_lo, seed_hi;
@@ -298,6 +313,8 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
 cudaError_t launch_stage_drift(const KP &kp, int cur, float *drift, cudaStream_t st);
 cudaError_t launch_stage_deposit(const KP &kp, float *S, float *R, cudaStream_t st);
 cudaError_t launch_fill(float *p, float v, int64_t n, cudaStream_t st);
+cudaError_t launch_hard_sphere(const KP &kp, cudaStream_t st, int *launches);
+cudaError_t launch_kde(const KP &kp, float *S, float *R, cudaStream_t st, int *launches);
 
 }  // namespace chemo
 

@@ -696,9 +696,15 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     float n2 = 0.f;
     if (DIM == 3) n2 = box_muller(rw.z, rw.w).x;
     const float amp = kp.noise[sp];
-    const float x1 = me.x + kp.dt * (F.x + dr.x) + amp * n01.x;
-    const float y1 = me.y + kp.dt * (F.y + dr.y) + amp * n01.y;
-    const float z1 = DIM == 3 ? me.z + kp.dt * (F.z + dr.z) + amp * n2 : 0.f;
+    // drift increment dt a, or dt a / (1 + dt |a|) for the tamed scheme
+    float sc = kp.dt;
+    if (kp.move_scheme == 1) {
+        const float ax = F.x + dr.x, ay = F.y + dr.y, az = DIM == 3 ? F.z + dr.z : 0.f;
+        sc = kp.dt / (1.f + kp.dt * sqrtf(fmaf(ax, ax, fmaf(ay, ay, az * az))));
+    }
+    const float x1 = me.x + sc * (F.x + dr.x) + amp * n01.x;
+    const float y1 = me.y + sc * (F.y + dr.y) + amp * n01.y;
+    const float z1 = DIM == 3 ? me.z + sc * (F.z + dr.z) + amp * n2 : 0.f;
 
     // fixed-step switching (Sect. 3.4): switch when u < rate dt. The
     // comparison that decides the species is taken in double precision, the
@@ -1014,7 +1020,7 @@ __global__ void __launch_bounds__(TPB) k_scatter(KP kp, int cur, int advance)
     }
     kp.S[dst] = u;
     if (kp.dS) kp.dS[dst] = kp.dU[j];
-    if (advance && kp.has_grid && kp.chem_mode == 0) {
+    if (advance && kp.has_grid && kp.chem_mode == 0 && !kp.kde) {
         const int sp = (int)(__float_as_uint(u.w) >> SP_SHIFT);
         if (kp.fused_deposit)
             deposit_cic<DIM>(kp, u, sp, kp.c[cur ^ 1], nullptr, kp.c[cur], true);
@@ -1189,6 +1195,164 @@ __global__ void __launch_bounds__(256) k_pde_stream(KP kp, const float *__restri
         v0 = vp;
         vp = vq;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Hard-sphere overlap correction (Sect. 3.2) of the moved, sorted cells:
+// every pair closer than its contact distance is pushed apart along the line
+// of centres by twice the penetration, cell i taking D_i / (D_i + D_j) of
+// it; all corrections come from the moved positions, then the boundary rule
+// again. The corrected cells go to U with their bins counted for the next
+// sort (as after the particle kernel).
+// ---------------------------------------------------------------------------
+template <int DIM, bool PERIODIC>
+__global__ void __launch_bounds__(TPB) k_hard_sphere(KP kp)
+{
+    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (j >= kp.n) return;
+    const float4 me = kp.S[j];
+    const uint32_t w = __float_as_uint(me.w);
+    const int sp = (int)(w >> SP_SHIFT);
+    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    const float pc[3] = {me.x, me.y, me.z};
+    for (int a = 0; a < DIM; ++a) {
+        c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+        lo[a] = c[a] - 1;
+        hi[a] = c[a] + 1;
+        if (!PERIODIC) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], kp.nb[a] - 1);
+        }
+    }
+    if (DIM == 2) lo[2] = hi[2] = layer_of(kp, me);
+    float acc[3] = {0.f, 0.f, 0.f};
+    const uint32_t n = (uint32_t)kp.n;
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        const int zz = (PERIODIC && DIM == 3) ? (z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z)) : z;
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            const int yy = PERIODIC ? (y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y)) : y;
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                const int xx = PERIODIC ? (x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x)) : x;
+                const uint32_t k = bin_key(kp, xx, yy, zz);
+                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, k), n);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), n);
+                for (uint32_t q = q0; q < q1; ++q) {
+                    if (q == (uint32_t)j) continue;
+                    const float4 o = __ldg(&kp.S[q]);
+                    float dx, dy, dz, r2;
+                    pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                    const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+                    const float contact = kp.hs_contact[st];
+                    if (!(r2 > 0.f) || !(r2 < contact * contact)) continue;
+                    const float r = sqrtf(r2);
+                    const float move = 2.f * (contact - r) * kp.hs_share[st] / r;
+                    acc[0] = fmaf(move, dx, acc[0]);
+                    acc[1] = fmaf(move, dy, acc[1]);
+                    if (DIM == 3) acc[2] = fmaf(move, dz, acc[2]);
+                }
+            }
+        }
+    }
+    const float x1 = me.x + acc[0], y1 = me.y + acc[1], z1 = DIM == 3 ? me.z + acc[2] : me.z;
+    float xb, yb, zb;
+    if (PERIODIC) {
+        xb = wrap_axis(x1, kp.lo[0], kp.hi[0], kp.L[0]);
+        yb = wrap_axis(y1, kp.lo[1], kp.hi[1], kp.L[1]);
+        zb = DIM == 3 ? wrap_axis(z1, kp.lo[2], kp.hi[2], kp.L[2]) : me.z;
+    } else {
+        xb = reflect_axis(x1, kp.lo[0], kp.hi[0]);
+        yb = reflect_axis(y1, kp.lo[1], kp.hi[1]);
+        zb = DIM == 3 ? reflect_axis(z1, kp.lo[2], kp.hi[2]) : me.z;
+    }
+    if (kp.dS) {
+        float4 d = kp.dS[j];
+        if (PERIODIC) {
+            d.x += acc[0];
+            d.y += acc[1];
+            d.z += DIM == 3 ? acc[2] : 0.f;
+        } else {
+            d.x += xb - me.x;
+            d.y += yb - me.y;
+            d.z += DIM == 3 ? zb - me.z : 0.f;
+        }
+        kp.dU[j] = d;
+    }
+    const float4 nu = make_float4(xb, yb, zb, me.w);
+    kp.U[j] = nu;
+    kp.slot[j] = count_bin(kp.cnt_nxt, key_of(kp, nu), kp.err);
+}
+
+// ---------------------------------------------------------------------------
+// Gaussian kernel density estimate at the grid nodes (Sect. 2.3; the density
+// listing of Sect. 3): node l gathers, through the cell list of the sorted
+// state, the cells within kde_range bandwidths, K_s(x) = (2 pi sigma_s^2)^
+// (-d/2) exp(-|x|^2 / (2 sigma_s^2)), and writes the source dt sum k_s K_s
+// and the consumption sum kappa_s K_s. The sums are exact (int64 fixed point,
+// 2^-32 of the largest term), so the result does not depend on the order of
+// the cells inside a bin.
+// ---------------------------------------------------------------------------
+template <int DIM, bool PERIODIC>
+__global__ void __launch_bounds__(TPB) k_kde(KP kp, float *__restrict__ S_out, float *__restrict__ R_out)
+{
+    const int64_t g = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (g >= kp.G) return;
+    const int gx = kp.g[0], gy = kp.g[1];
+    const int ix = (int)(g % gx);
+    const int iy = (int)((g / gx) % gy);
+    const int iz = (int)(g / ((int64_t)gx * gy));  // plane (3D) or layer (2D)
+    // node position as a float pair hi + lo (the steep kernel magnifies the
+    // rounding of a single float node coordinate): the difference to a cell
+    // is (hi - x) + lo
+    const int ik[3] = {ix, iy, iz};
+    float node[3] = {0.f, 0.f, (float)iz}, nlo[3] = {0.f, 0.f, 0.f};
+    for (int a = 0; a < DIM; ++a) {
+        const double v = kp.lo_d[a] + (double)ik[a] * kp.hgrid_d[a];
+        node[a] = (float)v;
+        nlo[a] = (float)(v - (double)node[a]);
+    }
+    const float4 me = make_float4(node[0], node[1], node[2], 0.f);
+    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    const int W = kp.kde_win;
+    for (int a = 0; a < DIM; ++a) {
+        c[a] = bin_axis(node[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+        lo[a] = c[a] - W;
+        hi[a] = c[a] + W;
+        if (!PERIODIC) {
+            lo[a] = max(lo[a], 0);
+            hi[a] = min(hi[a], kp.nb[a] - 1);
+        }
+    }
+    if (DIM == 2) lo[2] = hi[2] = min(max(iz, 0), kp.layers - 1);
+    long long accS = 0, accR = 0;
+    const uint32_t n = (uint32_t)kp.n;
+    for (int z = lo[2]; z <= hi[2]; ++z) {
+        const int zz = (PERIODIC && DIM == 3) ? (z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z)) : z;
+        for (int y = lo[1]; y <= hi[1]; ++y) {
+            const int yy = PERIODIC ? (y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y)) : y;
+            for (int x = lo[0]; x <= hi[0]; ++x) {
+                const int xx = PERIODIC ? (x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x)) : x;
+                const uint32_t k = bin_key(kp, xx, yy, zz);
+                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, k), n);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), n);
+                for (uint32_t q = q0; q < q1; ++q) {
+                    const float4 o = __ldg(&kp.S[q]);
+                    const int s = (int)(__float_as_uint(o.w) >> SP_SHIFT);
+                    float dx, dy, dz, r2;
+                    pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                    dx += nlo[0];
+                    dy += nlo[1];
+                    dz = DIM == 3 ? dz + nlo[2] : 0.f;
+                    r2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
+                    if (!(r2 < kp.kde_r2[s])) continue;
+                    const float e = __expf(-r2 * kp.kde_c[s]);
+                    accS += __float2ll_rn(kp.kde_src[s] * e * kp.kde_qs_inv);
+                    accR += __float2ll_rn(kp.kde_cons[s] * e * kp.kde_qr_inv);
+                }
+            }
+        }
+    }
+    S_out[g] = (float)((double)accS * (double)kp.kde_qs);
+    if (R_out) R_out[g] = (float)((double)accR * (double)kp.kde_qr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1517,6 +1681,36 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
         else w ? STAGE_F(3, false, true) : STAGE_F(3, false, false);
     }
 #undef STAGE_F
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hard_sphere(const KP &kp, cudaStream_t st, int *launches)
+{
+    if (kp.n == 0) return cudaSuccess;
+    const unsigned nb = blocks_for(kp.n);
+    if (kp.dim == 2) {
+        if (kp.periodic) k_hard_sphere<2, true><<<nb, TPB, 0, st>>>(kp);
+        else k_hard_sphere<2, false><<<nb, TPB, 0, st>>>(kp);
+    } else {
+        if (kp.periodic) k_hard_sphere<3, true><<<nb, TPB, 0, st>>>(kp);
+        else k_hard_sphere<3, false><<<nb, TPB, 0, st>>>(kp);
+    }
+    if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kde(const KP &kp, float *S, float *R, cudaStream_t st, int *launches)
+{
+    if (!kp.has_grid || kp.G == 0) return cudaSuccess;
+    const unsigned nb = blocks_for(kp.G);
+    if (kp.dim == 2) {
+        if (kp.periodic) k_kde<2, true><<<nb, TPB, 0, st>>>(kp, S, R);
+        else k_kde<2, false><<<nb, TPB, 0, st>>>(kp, S, R);
+    } else {
+        if (kp.periodic) k_kde<3, true><<<nb, TPB, 0, st>>>(kp, S, R);
+        else k_kde<3, false><<<nb, TPB, 0, st>>>(kp, S, R);
+    }
+    if (launches) ++*launches;
     return cudaGetLastError();
 }
 

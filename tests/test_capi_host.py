@@ -75,7 +75,9 @@ def test_status_strings(chemo):
 @pytest.mark.parametrize("bad", [
     dict(dim=4), dict(n_species=0), dict(n_species=9), dict(dt=0.0), dict(grid=[2, 64, 1]),
     dict(boundary=1, pde_bc=0), dict(boundary=0, pde_bc=2), dict(cutoff_mode=3), dict(search_mode=5),
-    dict(hi=[0.0, 1.0, 1.0]), dict(react_to=[5, 0]),
+    dict(hi=[0.0, 1.0, 1.0]), dict(react_to=[5, 0]), dict(warp_runs=33), dict(move_scheme=2),
+    dict(hard_sphere=2), dict(deposit_kernel=2), dict(kde_range=-1.0),
+    dict(deposit_kernel=1, chem_mode=1), dict(deposit_kernel=1, diameter=[0.0, 0.01]),
 ])
 def test_invalid_parameters_rejected_on_host(chemo, bad):
     from paper_1805_11007_gb300 import workloads as wl
