@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--profile-steps", type=int, default=RUN_STEPS)
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -378,6 +379,39 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
     return out
 
 
+def variants_leg(chemo, wl, devc, stream, steps=200):
+    """Device ms per step of the 2D walls workload (100,000 cells, 512^2 grid,
+    12 PDE substeps) with each model variant switched on alone: the
+    Euler-Maruyama / cloud-in-cell baseline, tamed Euler, the hard-sphere
+    correction (with its re-sort), the Gaussian kernel density deposit, and
+    type switching."""
+    import torch
+    base, pos, sp = wl.initial_state("walls_grid_2d")
+    dpos = torch.from_numpy(pos).to(devc)
+    dsp = torch.from_numpy(sp).to(devc)
+    cases = {"baseline": {}, "tamed_euler": {"move_scheme": 1}, "hard_sphere": {"hard_sphere": 1},
+             "kde_deposit": {"deposit_kernel": 1},
+             "reactions": {"reactions": 1, "react_k0": [10.0, 0.0], "react_kc": [0.0, 5.0], "react_to": [1, 0]}}
+    out = {"workload": "walls_grid_2d: 2D walls, N=%d two species, 512x512 grid (12 PDE substeps), %d steps from "
+                       "the initial state" % (pos.shape[0], steps)}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for name, over in cases.items():
+        p = dict(base, **over)
+        with chemo.chemo_create(p, dpos, dsp, stream=stream) as sim:
+            chemo.chemo_step_n(sim, 4, stream=stream)
+            chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
+            chemo.chemo_set_step_index(sim, 0, stream=stream)
+            ev[0].record(stream)
+            chemo.chemo_step_n(sim, steps, stream=stream)
+            ev[1].record(stream)
+            torch.cuda.synchronize()
+            chemo.chemo_check(sim, stream=stream)
+            ms = ev[0].elapsed_time(ev[1]) / steps
+            out[name] = {"ms_per_step": ms, "particle_steps_per_s": pos.shape[0] / (ms * 1e-3),
+                         "launches_per_step": chemo.chemo_get_info(sim)["launches_per_step"]}
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -523,6 +557,10 @@ def main():
                       "chemo_read_state to pinned host; the chemical grid stays on the device"}
     sim.close()
 
+    variants = None
+    if rank == 0 and not args.no_variants:
+        variants = variants_leg(chemo, wl, devc, stream)
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier)
@@ -553,6 +591,7 @@ def main():
             "pair_interactions_per_s": pairs_per_step * world / (ms_per_step * 1e-3),
             "adjoint": adjoint,
             "ensemble": ensemble,
+            "variants": variants,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

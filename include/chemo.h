@@ -233,8 +233,11 @@ int chemo_record(chemo_sim *sim, int64_t nsteps, int32_t every, void *stream);
  * re-run forward before its reverse sweep (Sect. 2 model: pair force Jacobian,
  * interpolation Jacobian, reflection signs, deposit and PDE transposes). The
  * cutoff jump and the reflection kinks are not differentiated (measure-zero
- * events). The simulation is left at the final state of the recorded run.
- * Synchronises `stream` when mem_kind is HOST. EINVAL if no run is recorded. */
+ * events). dL/dinter is 0 when inter = 0 (no pair force, no cell list for
+ * its cutoff). Memory: per segment the states, fields, sorted states, cell
+ * lists and pair forces of `every` steps. The simulation is left at the
+ * final state of the recorded run. Synchronises `stream` when mem_kind is
+ * HOST. EINVAL if no run is recorded. */
 int chemo_gradient(chemo_sim *sim, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
                    float *dL_dpos0, int mem_kind, void *stream);
 

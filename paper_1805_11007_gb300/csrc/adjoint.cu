@@ -52,7 +52,12 @@ struct Tape {
     float *lamY = nullptr;              // n x dim by id
     float *lamC[2] = {nullptr, nullptr};  // G
     float *lamS = nullptr;              // G
-    float *F1 = nullptr;                // unit-strength pair force by id, n x dim
+    float4 *seg_S = nullptr;            // sorted state at the start of each step of the segment
+    uint32_t *seg_cnt = nullptr;        // its bin counts (packed 16-bit)
+    uint32_t *seg_gst = nullptr;        // its group offsets
+    float *seg_F = nullptr;             // pair force of each step, by id (n x dim)
+    size_t cwords = 0, gwords = 0;      // words of one count table / offset table
+    float *dpf = nullptr;               // parameter gradient (float) for the caller
     double *dpar = nullptr;             // 2 + MAXS accumulators
 };
 
@@ -173,16 +178,17 @@ __device__ __forceinline__ void warp_add_double(double v, double *dst)
 }
 
 // Per-cell adjoint terms (by id). Reads X^n, X^{n+1}, c^n, lambda_X^{n+1},
-// lambda_S and the unit-strength pair force; writes lambda_Y and the local
+// lambda_S and the step's pair force Fb (f_unit Fb = dF/dinter); writes lambda_Y and the local
 // part of lambda_X^n, scatters the interpolation transpose into lambda_c and
 // accumulates the parameter gradients.
 template <int DIM>
 __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restrict__ Xn, const float *__restrict__ Xn1,
                                                     const uint8_t *__restrict__ spec, const float *__restrict__ cn,
                                                     const float *__restrict__ lamX1, const float *__restrict__ lamS,
-                                                    const float *__restrict__ F1, float *__restrict__ lamY,
+                                                    const float *__restrict__ Fb, float f_unit, float *__restrict__ lamY,
                                                     float *__restrict__ lamXn, float *__restrict__ lamC,
-                                                    unsigned long long step, double *dpar, int has_grid)
+                                                    unsigned long long step, double *dpar, int has_grid,
+                                                    int lams_over_tau)
 {
     const int64_t i = (int64_t)blockIdx.x * ATPB + threadIdx.x;
     const bool valid = i < kp.n;
@@ -203,7 +209,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
             corners<DIM>(kp, x1, node, w, dw);
             for (int m = 0; m < (1 << DIM); ++m) {
                 float inv_tau = 1.f;
-                if (kp.pde_bc != 2)
+                if (kp.pde_bc != 2 && !lams_over_tau)  // (already divided by tau when lams_over_tau)
                     for (int a = 0; a < DIM; ++a)
                         if (node[m][a] == 0 || node[m][a] == kp.g[a] - 1) inv_tau *= 2.f;
                 const float l = lamS[nidx(kp, node[m])] * inv_tau * kp.src[sp];
@@ -237,7 +243,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
         const float amp = kp.noise[sp];
         float sgn[3] = {1.f, 1.f, 1.f};
         for (int a = 0; a < DIM; ++a) {
-            const float Fa = kp.inter_f * F1[i * DIM + a];
+            const float Fa = Fb[i * DIM + a];
             float y = x0[a] + kp.dt * (Fa + chem * G[a]) + amp * xi[a];
             if (!kp.periodic) {
                 for (int it = 0; it < 16 && (y < kp.lo[a] || y > kp.hi[a]); ++it) {
@@ -276,7 +282,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
         double gl = 0.0, fl = 0.0, xl = 0.0;
         for (int a = 0; a < DIM; ++a) {
             gl += (double)G[a] * ly[a];
-            fl += (double)F1[i * DIM + a] * ly[a];
+            fl += (double)Fb[i * DIM + a] * (double)f_unit * ly[a];
             xl += (double)xi[a] * ly[a];
         }
         d_chi = (double)kp.dt * (double)kp.chemotactic_f[sp] * gl;
@@ -477,10 +483,22 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         t->lamY = (float *)p;
         if ((r = talloc(t, &p, gb))) return r;
         t->lamS = (float *)p;
-        if ((r = talloc(t, &p, pb))) return r;
-        t->F1 = (float *)p;
+        const KP &k0 = s->kp;
+        t->cwords = (size_t)k0.bin_slots / 2;
+        t->gwords = ((size_t)k0.ngroups + 1 + 3) & ~(size_t)3;
+        const size_t E = (size_t)t->every;
+        if ((r = talloc(t, &p, E * (size_t)std::max<int64_t>(n, 1) * sizeof(float4)))) return r;
+        t->seg_S = (float4 *)p;
+        if ((r = talloc(t, &p, E * t->cwords * sizeof(uint32_t)))) return r;
+        t->seg_cnt = (uint32_t *)p;
+        if ((r = talloc(t, &p, E * t->gwords * sizeof(uint32_t)))) return r;
+        t->seg_gst = (uint32_t *)p;
+        if ((r = talloc(t, &p, E * pb))) return r;
+        t->seg_F = (float *)p;
         if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS)))) return r;
         t->dpar = (double *)p;
+        if ((r = talloc(t, &p, sizeof(float) * (2 + MAXS)))) return r;
+        t->dpf = (float *)p;
     }
     const cudaMemcpyKind in_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
     int lx = 0, lc = 0;
@@ -490,9 +508,9 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         else ATRY(cudaMemsetAsync(t->lamC[lc], 0, gb, st));
     }
     ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS), st));
-    // unit-strength force tables (the pair force is linear in inter)
-    chemo_params unit = s->prm;
-    unit.inter = 1.f;
+    // the pair force is linear in inter: dF/dinter = F / inter (the cell list
+    // is not built for the cutoff when inter = 0, and dL/dinter is then 0)
+    const float f_unit = s->prm.inter != 0.f ? 1.f / s->prm.inter : 0.f;
     const int64_t end_step = s->step;
     for (int seg = t->nseg - 1; seg >= 0; --seg) {
         const int64_t n0 = (int64_t)seg * t->every;
@@ -504,7 +522,19 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         for (int64_t k = 0; k < len; ++k) {
             if ((r = gather(s, t->seg_pos + (size_t)k * n * dim, nullptr, st))) return r;
             if (G) ATRY(cudaMemcpyAsync(t->seg_c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
-            if ((r = eng_enqueue_step(s, st, nullptr))) return r;
+            // the sorted state and its cell list, for the pair term of the reverse sweep
+            const KP v = eng_view(s);
+            if (n) ATRY(cudaMemcpyAsync(t->seg_S + (size_t)k * n, v.S, (size_t)n * sizeof(float4),
+                                        cudaMemcpyDeviceToDevice, st));
+            ATRY(cudaMemcpyAsync(t->seg_cnt + (size_t)k * t->cwords, v.cnt_cur, t->cwords * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+            ATRY(cudaMemcpyAsync(t->seg_gst + (size_t)k * t->gwords, v.gstart, t->gwords * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, st));
+            if (n) ATRY(cudaMemsetAsync(t->seg_F + (size_t)k * n * dim, 0, (size_t)n * dim * sizeof(float), st));
+            s->kp.F_save = t->seg_F + (size_t)k * n * dim;  // the step's pair force, by id
+            r = eng_enqueue_step(s, st, nullptr);
+            s->kp.F_save = nullptr;
+            if (r) return r;
         }
         if ((r = gather(s, t->seg_pos + (size_t)len * n * dim, nullptr, st))) return r;
         // reverse sweep over the segment
@@ -515,7 +545,19 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
             const float *cn = G ? t->seg_c + (size_t)k * G : nullptr;
             KP kp = eng_view(s);
             // 1. PDE transpose (substeps), lambda_S
-            if (G) {
+            if (G && kp.pde_multi) {
+                // 2D: the transpose of the mirror-ghost operator is tau L tau^-1, so
+                // nu = lambda / tau runs the forward substeps (several per launch);
+                // lambda_S / tau is the mean of the substeps' nu
+                int left = kp.substeps;
+                for (int l = 0; l < kp.pde_launches; ++l) {
+                    const int nsub = (left + (kp.pde_launches - l) - 1) / (kp.pde_launches - l);
+                    ATRY(launch_pde_multi(kp, t->lamC[lc], t->lamC[lc ^ 1], nsub, 0, t->lamS, l == 0,
+                                          1.f / (float)kp.substeps, 1, st));
+                    left -= nsub;
+                    lc ^= 1;
+                }
+            } else if (G) {
                 const int ss = kp.substeps;
                 for (int m = 0; m < ss; ++m) {
                     k_adj_pde<<<blocks(G), ATPB, 0, st>>>(kp, t->lamC[lc], t->lamC[lc ^ 1], t->lamS, 1.f / ss, m == 0);
@@ -523,23 +565,21 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                     lc ^= 1;
                 }
             }
-            // cell list of X^n and its unit-strength pair force
-            if ((r = eng_ingest(s, Xn, t->species, nullptr, CHEMO_MEM_DEVICE, st))) return r;
-            kp = eng_view(s);
-            KP ku = kp;
-            eng_fill_model(unit, ku);
-            if (n) ATRY(launch_stage_forces(ku, t->F1, nullptr, nullptr, st));
+            // the cell list of X^n and its pair force, saved by the re-run
+            kp.S = t->seg_S + (size_t)k * n;
+            kp.cnt_cur = t->seg_cnt + (size_t)k * t->cwords;
+            kp.gstart = t->seg_gst + (size_t)k * t->gwords;
+            const float *Fk = t->seg_F + (size_t)k * n * dim;
             // 2-5. per-cell terms, then the pair term
-            kp.inter_f = s->prm.inter;
             if (n) {
                 if (dim == 2)
-                    k_adj_cells<2><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, t->F1,
+                    k_adj_cells<2><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             G ? 1 : 0);
+                                                             G ? 1 : 0, kp.pde_multi);
                 else
-                    k_adj_cells<3><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, t->F1,
+                    k_adj_cells<3><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             G ? 1 : 0);
+                                                             G ? 1 : 0, kp.pde_multi);
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
                     if (dim == 2) {
@@ -557,9 +597,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     }
     // outputs
     const int np = 2 + t->ns;
-    float *dpf;
-    if ((r = talloc(t, &p, sizeof(float) * 16))) return r;
-    dpf = (float *)p;
+    float *dpf = t->dpf;
     k_params_out<<<1, 32, 0, st>>>(t->dpar, dpf, np);
     ATRY(cudaGetLastError());
     const cudaMemcpyKind out_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;

@@ -374,6 +374,9 @@ int fill_grid(const chemo_params &p, KP &kp)
     kp.pde_bc = p.pde_bc;
     kp.substeps = 1;
     kp.dts = (float)p.dt;
+    kp.pde_multi = 0;
+    kp.pde_launches = 1;
+    kp.zero_src = 0;
     kp.fused_deposit = 0;
     if (!kp.has_grid) return CHEMO_OK;
     int64_t G = 1;
@@ -395,6 +398,11 @@ int fill_grid(const chemo_params &p, KP &kp)
     kp.G = G;
     kp.substeps = resolve_substeps(p);
     kp.dts = (float)(p.dt / kp.substeps);
+    // 2D grids with several substeps run them PDE_MULTI_MAX at a time in
+    // one launch (the halo of a tile grows by one node per substep)
+    kp.pde_multi = (p.dim == 2 && kp.substeps > 1) ? 1 : 0;
+    kp.pde_launches = kp.pde_multi ? (kp.substeps + PDE_MULTI_MAX - 1) / PDE_MULTI_MAX : kp.substeps;
+    kp.zero_src = (kp.pde_multi && p.deposit_kernel == 0) ? 1 : 0;
     // one substep: the CIC deposit goes straight into c^{n+1} (the density
     // kernel writes a source grid instead)
     kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1 && p.deposit_kernel == 0) ? 1 : 0;
@@ -469,7 +477,7 @@ int enqueue_step(chemo_sim *s, cudaStream_t st, int *launches)
     if (overlap) CUDA_TRY(cudaStreamWaitEvent(st, s->ev_join, 0));
     if (int r = enqueue_sort_and_density(s, kp, st, launches)) return r;
     if (grid && !kp.fused_deposit) CUDA_TRY(launch_pde(kp, s->cur, st, launches));
-    if (grid) s->cur = kp.fused_deposit ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+    if (grid) s->cur = kp.fused_deposit ? (s->cur ^ 1) : (s->cur ^ (kp.pde_launches & 1));
     s->step += 1;
     return CHEMO_OK;
 }
@@ -753,7 +761,7 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
         return r;
     }
     // launches per step: particles, scan, scatter, and the PDE substeps
-    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.substeps : 0) +
+    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.pde_launches : 0) +
                            (kp.hard_sphere ? (n > 0 ? 3 : 2) : 0) + (kp.kde && kp.has_grid ? 1 : 0);
     *out = s;
     return CHEMO_OK;
@@ -1114,7 +1122,7 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
         }
         if (err == cudaSuccess) err = cudaEventRecord(e[9], st);
         if (err != cudaSuccess) r = fail(CHEMO_ECUDA, "profile: %s", cudaGetErrorString(err));
-        if (grid) s->cur = fused ? (s->cur ^ 1) : (s->cur ^ (kp.substeps & 1));
+        if (grid) s->cur = fused ? (s->cur ^ 1) : (s->cur ^ (kp.pde_launches & 1));
         s->cntp ^= 1;
         s->step += 1;
     }

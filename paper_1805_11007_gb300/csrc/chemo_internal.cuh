@@ -93,6 +93,9 @@ struct KP {
     float Dc, gamma;
     int substeps;
     float dts;
+    int pde_multi;               // 1: 2D grid, several substeps per launch (temporal blocking)
+    int pde_launches;            // PDE launches per step (each swaps the c buffers once)
+    int zero_src;                // 1: the particle kernel clears the source grids of the last step
     int fused_deposit;           // 1: deposit straight into c^{n+1} (one substep)
     int overlap;                 // 1: PDE concurrent with the particle kernel (second stream)
     // buffers
@@ -112,6 +115,7 @@ struct KP {
     uint32_t *err;               // latched error bits
     unsigned long long *step;    // absolute index of the step being computed
     unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
+    float *F_save;               // non-NULL: the particle kernel stores each cell's pair force (by id)
 };
 
 // ---------------------------------------------------------------------------
@@ -304,6 +308,16 @@ cudaError_t launch_pack(const KP &kp, const float *pos, const uint8_t *sp, const
 cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches);
 cudaError_t launch_scatter(const KP &kp, int cur, int advance_step, cudaStream_t st, int *launches);
 cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches);
+// Substeps per launch of the temporal-blocked 2D PDE kernel (its halo width).
+constexpr int PDE_MULTI_MAX = 12;
+// Runs `nsub` substeps of the 2D PDE in one launch from cin to cout (c grids
+// of kp); use_src adds the source / consumption grids; avg (nullable)
+// receives (avg_first) or accumulates avg_scale times the sum of the
+// substeps' input values; tau_mode 1 works on c/tau (trapezoid weights) and
+// stores tau times the result (the transposed operator of the mirror-ghost
+// Laplacian, for the adjoint).
+cudaError_t launch_pde_multi(const KP &kp, const float *cin, float *cout, int nsub, int use_src, float *avg,
+                             int avg_first, float avg_scale, int tau_mode, cudaStream_t st);
 cudaError_t launch_unsort(const KP &kp, float *pos, uint8_t *sp, float *disp, cudaStream_t st);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, cudaStream_t st);
 cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st);

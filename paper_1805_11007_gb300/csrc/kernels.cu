@@ -651,8 +651,14 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
     load_tables(kp, t);
-    __syncthreads();
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (kp.zero_src) {  // source grids of the last step, read by its PDE: cleared for this step's deposit
+        for (int64_t g = j; g < kp.G; g += (int64_t)gridDim.x * TPB) {
+            kp.srcg[g] = 0.f;
+            kp.Rg[g] = 0.f;
+        }
+    }
+    __syncthreads();
     const bool valid = j < kp.n;
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
@@ -675,6 +681,12 @@ __global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
     }
     if (!valid) return;
+    if (kp.F_save) {  // recorded for the adjoint
+        const int64_t gi = gid_of(kp, me);
+        kp.F_save[gi * DIM + 0] = F.x;
+        kp.F_save[gi * DIM + 1] = F.y;
+        if (DIM == 3) kp.F_save[gi * DIM + 2] = F.z;
+    }
     const unsigned long long step = *kp.step;
 
     float3 dr = make_float3(0.f, 0.f, 0.f);
@@ -1198,6 +1210,117 @@ __global__ void __launch_bounds__(256) k_pde_stream(KP kp, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
+// k_pde_multi: up to PDE_MULTI_MAX substeps of Eq. (1d) on a 2D grid in one
+// launch (temporal blocking). A block owns a PM_T x PM_T tile of nodes and
+// loads it with a halo of nsub nodes into shared memory: the mirror-ghost
+// (Neumann) problem is exactly the problem on the mirror-extended grid with
+// mirror-extended data and sources, so the halo is filled by reflecting the
+// node index (periodic: wrapping; Dirichlet: wall nodes are held and the
+// halo beyond them is never used). Each substep updates every node but the
+// outer ring of the tile; the stale ring reaches one node further in per
+// substep, never the tile itself.
+// ---------------------------------------------------------------------------
+constexpr int PM_T = 32;
+constexpr int PM_TPB = 256;
+
+__device__ __forceinline__ int pm_map(int k, int N, int bc)
+{
+    if (bc == 2) {
+        k %= N;
+        return k < 0 ? k + N : k;
+    }
+    if (bc == 1) return k < 0 ? 0 : (k > N - 1 ? N - 1 : k);
+    const int P = 2 * (N - 1);  // mirror: the index reflects with period 2 (N - 1)
+    k %= P;
+    if (k < 0) k += P;
+    return k > N - 1 ? P - k : k;
+}
+
+template <int BC>
+__global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__restrict__ cin, float *__restrict__ cout,
+                                                      int nsub, int use_src, float *__restrict__ avg, int avg_first,
+                                                      float avg_scale, int tau_mode)
+{
+    extern __shared__ float pm[];
+    const int H = nsub, W = PM_T + 2 * nsub, WW = W * W;
+    float *A = pm, *B = pm + WW;
+    float *Sv = pm + 2 * WW, *Rv = pm + 3 * WW;
+    const int gx = kp.g[0], gy = kp.g[1];
+    const int x0 = blockIdx.x * PM_T - H, y0 = blockIdx.y * PM_T - H;
+    const int64_t lbase = (int64_t)blockIdx.z * gx * gy;  // layer of an ensemble
+    for (int i = threadIdx.x; i < WW; i += PM_TPB) {
+        const int mx = pm_map(x0 + i % W, gx, BC), my = pm_map(y0 + i / W, gy, BC);
+        const int64_t g = lbase + (int64_t)my * gx + mx;
+        float v = cin[g];
+        if (tau_mode && BC != 2) {  // c / tau: tau = 1/2 per wall axis
+            if (mx == 0 || mx == gx - 1) v *= 2.f;
+            if (my == 0 || my == gy - 1) v *= 2.f;
+        }
+        A[i] = v;
+        if (use_src) {
+            Sv[i] = kp.srcg[g];
+            Rv[i] = kp.Rg[g];
+        }
+    }
+    constexpr int OWN = PM_T * PM_T / PM_TPB;  // output nodes per thread
+    float acc[OWN];
+#pragma unroll
+    for (int q = 0; q < OWN; ++q) acc[q] = 0.f;
+    const float ihx = kp.inv_h2[0], ihy = kp.inv_h2[1], Dc = kp.Dc, gam = kp.gamma, dts = kp.dts;
+    const float inv_s = 1.f / (float)kp.substeps;
+    for (int m = 0; m < nsub; ++m) {
+        __syncthreads();
+        if (avg) {
+#pragma unroll
+            for (int q = 0; q < OWN; ++q) {
+                const int o = threadIdx.x + PM_TPB * q;
+                acc[q] += A[(o / PM_T + H) * W + o % PM_T + H];
+            }
+        }
+        for (int i = threadIdx.x; i < WW; i += PM_TPB) {
+            const int tx = i % W, ty = i / W;
+            if (tx == 0 || ty == 0 || tx == W - 1 || ty == W - 1) continue;
+            const float c = A[i];
+            const float lap = (A[i - 1] + A[i + 1] - 2.f * c) * ihx + (A[i - W] + A[i + W] - 2.f * c) * ihy;
+            float rhs = Dc * lap - gam * c;
+            float add = 0.f;
+            if (use_src) {
+                rhs -= Rv[i] * c;
+                add = Sv[i] * inv_s;
+            }
+            float out = fmaf(dts, rhs, c + add);
+            if (BC == 1) {  // Dirichlet: wall nodes keep their value
+                const int X = x0 + tx, Y = y0 + ty;
+                if (X <= 0 || Y <= 0 || X >= gx - 1 || Y >= gy - 1) out = c;
+            }
+            B[i] = out;
+        }
+        float *tmp = A;
+        A = B;
+        B = tmp;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < OWN; ++q) {
+        const int o = threadIdx.x + PM_TPB * q;
+        const int ox = o % PM_T, oy = o / PM_T;
+        const int X = blockIdx.x * PM_T + ox, Y = blockIdx.y * PM_T + oy;
+        if (X >= gx || Y >= gy) continue;
+        float v = A[(oy + H) * W + ox + H];
+        float av = acc[q];
+        if (tau_mode && BC != 2) {
+            float t = 1.f;
+            if (X == 0 || X == gx - 1) t *= 0.5f;
+            if (Y == 0 || Y == gy - 1) t *= 0.5f;
+            v *= t;
+        }
+        const int64_t g = lbase + (int64_t)Y * gx + X;
+        cout[g] = v;
+        if (avg) avg[g] = avg_first ? av * avg_scale : fmaf(av, avg_scale, avg[g]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Hard-sphere overlap correction (Sect. 3.2) of the moved, sorted cells:
 // every pair closer than its contact distance is pushed apart along the line
 // of centres by twice the penetration, cell i taking D_i / (D_i + D_j) of
@@ -1613,9 +1736,49 @@ static void pde_stream_launch(const KP &kp, const float *cin, float *cout, int u
     }
 }
 
+static size_t pde_multi_smem(int nsub)
+{
+    const size_t W = (size_t)(PM_T + 2 * nsub);
+    return 4 * W * W * sizeof(float);
+}
+
+cudaError_t launch_pde_multi(const KP &kp, const float *cin, float *cout, int nsub, int use_src, float *avg,
+                             int avg_first, float avg_scale, int tau_mode, cudaStream_t st)
+{
+    static bool attr = false;
+    if (!attr) {
+        const int mx = (int)pde_multi_smem(PDE_MULTI_MAX);
+        cudaFuncSetAttribute(k_pde_multi<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_pde_multi<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        cudaFuncSetAttribute(k_pde_multi<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+        attr = true;
+    }
+    if (nsub < 1 || nsub > PDE_MULTI_MAX) return cudaErrorInvalidValue;
+    const dim3 grid((kp.g[0] + PM_T - 1) / PM_T, (kp.g[1] + PM_T - 1) / PM_T, kp.g[2]);
+    const size_t sm = pde_multi_smem(nsub);
+    if (kp.pde_bc == 0) k_pde_multi<0><<<grid, PM_TPB, sm, st>>>(kp, cin, cout, nsub, use_src, avg, avg_first, avg_scale, tau_mode);
+    else if (kp.pde_bc == 1) k_pde_multi<1><<<grid, PM_TPB, sm, st>>>(kp, cin, cout, nsub, use_src, avg, avg_first, avg_scale, tau_mode);
+    else k_pde_multi<2><<<grid, PM_TPB, sm, st>>>(kp, cin, cout, nsub, use_src, avg, avg_first, avg_scale, tau_mode);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (!kp.has_grid || kp.chem_mode != 0) return cudaSuccess;
+    if (kp.pde_multi) {
+        // the substeps split as evenly as possible over the launches
+        int c = cur, left = kp.substeps;
+        for (int l = 0; l < kp.pde_launches; ++l) {
+            const int nsub = (left + (kp.pde_launches - l) - 1) / (kp.pde_launches - l);
+            const cudaError_t e = launch_pde_multi(kp, kp.c[c], kp.c[c ^ 1], nsub, kp.fused_deposit ? 0 : 1, nullptr,
+                                                   0, 0.f, 0, st);
+            if (e != cudaSuccess) return e;
+            left -= nsub;
+            c ^= 1;
+            if (launches) ++*launches;
+        }
+        return cudaSuccess;
+    }
     const bool stream = kp.g[0] % 4 == 0 && kp.g[0] >= 8;
     const dim3 grid((kp.g[0] + 127) / 128, kp.g[1], kp.g[2]);  // g[2]: planes (3D) or layers (2D)
     const int s = kp.substeps;

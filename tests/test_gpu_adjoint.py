@@ -50,7 +50,10 @@ def _oracle_loss(p, pos, sp, c0, nsteps, theta=None, pos0=None):
 
 
 @pytest.mark.parametrize("over", [dict(), dict(chem_mode=1, fixed_grad=[3.0, -2.0, 0.0], boundary=1, pde_bc=2,
-                                               diameter=[0.01, 0.02])])
+                                               diameter=[0.01, 0.02]),
+                                  # several PDE substeps (one and two launches of the multi-substep kernel)
+                                  dict(pde_substeps=3, Dc=20.0), dict(pde_substeps=14, Dc=50.0),
+                                  dict(pde_substeps=5, Dc=20.0, boundary=1, pde_bc=2)])
 def test_parameter_gradients_match_oracle_finite_differences(over):
     p, pos, sp, c0 = _setup(**over)
     nsteps, every = 20, 5
