@@ -38,7 +38,7 @@ using namespace chemo;
 
 namespace {
 
-constexpr int ATPB = 256;
+constexpr int ATPB = 128;  // small blocks: the adjoint kernels run over tens of thousands of cells
 
 struct Tape {
     int64_t n = 0, G = 0, nsteps = 0, every = 0, step0 = 0;
@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
         }
     }
     float acc[3] = {0.f, 0.f, 0.f};
+    const uint32_t n = (uint32_t)kp.n;
     for (int z = lo[2]; z <= hi[2]; ++z) {
         int zz = z;
         if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
@@ -333,15 +334,24 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
             int yy = y;
             if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
             const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-                int xx = x;
-                if (PERIODIC) xx = x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x);
-                const uint32_t k = rowk + (uint32_t)xx;
-                const uint32_t q0 = bin_start(kp.cnt_cur, kp.gstart, k);
-                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), (uint32_t)kp.n);
+            // the row's bins as contiguous ranges of the sorted array (a
+            // periodic row that wraps is two ranges)
+            int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
+            if (PERIODIC && lo[0] < 0) {
+                xa[0] = 0;
+                xa[1] = xb[1] = kp.nb[0] + lo[0];
+            } else if (PERIODIC && hi[0] >= kp.nb[0]) {
+                xb[0] = kp.nb[0] - 1;
+                xa[1] = 0;
+                xb[1] = hi[0] - kp.nb[0];
+            }
+            for (int piece = 0; piece < 2; ++piece) {
+                if (xa[piece] > xb[piece]) continue;
+                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
                 for (uint32_t q = q0; q < q1; ++q) {
                     if (q == (uint32_t)j) continue;
-                    const float4 o = kp.S[q];
+                    const float4 o = __ldg(&kp.S[q]);
                     float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
                     if (PERIODIC)
                         for (int a = 0; a < DIM; ++a) {

@@ -75,7 +75,15 @@ struct FAcc {
 // leave unspecified), and no 64-bit conversion runs per pair (those use the
 // narrow FP64 pipe).
 // ---------------------------------------------------------------------------
-constexpr int LIST_CAP = 24;  // flushed once a lane holds more than LIST_CAP - UNROLL
+// Compile-time tunables of the pair kernels: resident blocks per SM (their
+// register budget is 65536 / (256 x blocks)) and the per-lane list length.
+#ifndef CHEMO_PAIR_BLOCKS
+#define CHEMO_PAIR_BLOCKS 4
+#endif
+#ifndef CHEMO_LIST_CAP
+#define CHEMO_LIST_CAP 24
+#endif
+constexpr int LIST_CAP = CHEMO_LIST_CAP;  // flushed once a lane holds more than LIST_CAP - UNROLL
 constexpr int UNROLL = 8;     // candidates per lane between two warp votes
 
 template <int DIM, bool PERIODIC>
@@ -646,7 +654,7 @@ __device__ __forceinline__ float wrap_axis(float x, float lo, float hi, float L)
 // k_step: the particle part of one step.
 // ---------------------------------------------------------------------------
 template <int DIM, bool PERIODIC, bool WARP>
-__global__ void __launch_bounds__(TPB, 4) k_step(KP kp, int cur)
+__global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
@@ -828,8 +836,11 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
 // proceeds. The kernel also clears cnt_cur (the counts of the state the
 // particle kernel has finished reading), which the next step counts into.
 // ---------------------------------------------------------------------------
-constexpr int SCAN_ITEMS = 8;                       // consecutive groups per thread
-constexpr int SCAN_TILE = TPB * SCAN_ITEMS;         // 2048 groups
+#ifndef CHEMO_SCAN_ITEMS
+#define CHEMO_SCAN_ITEMS 16
+#endif
+constexpr int SCAN_ITEMS = CHEMO_SCAN_ITEMS;        // consecutive groups per thread
+constexpr int SCAN_TILE = TPB * SCAN_ITEMS;         // groups per tile
 constexpr unsigned long long ST_AGG = 1ull, ST_INC = 2ull;
 constexpr int ST_VAL_BITS = 38;
 constexpr unsigned long long ST_VAL_MASK = (1ull << ST_VAL_BITS) - 1ull;
@@ -1242,27 +1253,34 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
                                                       float avg_scale, int tau_mode)
 {
     extern __shared__ float pm[];
+    // threads as 32 columns x 8 rows; the tile is W x W, W = PM_T + 2 nsub <= 56
     const int H = nsub, W = PM_T + 2 * nsub, WW = W * W;
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
     float *A = pm, *B = pm + WW;
     float *Sv = pm + 2 * WW, *Rv = pm + 3 * WW;
     const int gx = kp.g[0], gy = kp.g[1];
     const int x0 = blockIdx.x * PM_T - H, y0 = blockIdx.y * PM_T - H;
     const int64_t lbase = (int64_t)blockIdx.z * gx * gy;  // layer of an ensemble
-    for (int i = threadIdx.x; i < WW; i += PM_TPB) {
-        const int mx = pm_map(x0 + i % W, gx, BC), my = pm_map(y0 + i / W, gy, BC);
-        const int64_t g = lbase + (int64_t)my * gx + mx;
-        float v = cin[g];
-        if (tau_mode && BC != 2) {  // c / tau: tau = 1/2 per wall axis
-            if (mx == 0 || mx == gx - 1) v *= 2.f;
-            if (my == 0 || my == gy - 1) v *= 2.f;
-        }
-        A[i] = v;
-        if (use_src) {
-            Sv[i] = kp.srcg[g];
-            Rv[i] = kp.Rg[g];
+    for (int ty = ly; ty < W; ty += 8) {
+        const int my = pm_map(y0 + ty, gy, BC);
+        const bool ywall = my == 0 || my == gy - 1;
+        for (int tx = lx; tx < W; tx += 32) {
+            const int mx = pm_map(x0 + tx, gx, BC);
+            const int64_t g = lbase + (int64_t)my * gx + mx;
+            float v = cin[g];
+            if (tau_mode && BC != 2) {  // c / tau: tau = 1/2 per wall axis
+                if (mx == 0 || mx == gx - 1) v *= 2.f;
+                if (ywall) v *= 2.f;
+            }
+            const int i = ty * W + tx;
+            A[i] = v;
+            if (use_src) {
+                Sv[i] = kp.srcg[g];
+                Rv[i] = kp.Rg[g];
+            }
         }
     }
-    constexpr int OWN = PM_T * PM_T / PM_TPB;  // output nodes per thread
+    constexpr int OWN = PM_T * PM_T / PM_TPB;  // output nodes per thread: column lx, rows ly + 8 q
     float acc[OWN];
 #pragma unroll
     for (int q = 0; q < OWN; ++q) acc[q] = 0.f;
@@ -1272,42 +1290,41 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
         __syncthreads();
         if (avg) {
 #pragma unroll
-            for (int q = 0; q < OWN; ++q) {
-                const int o = threadIdx.x + PM_TPB * q;
-                acc[q] += A[(o / PM_T + H) * W + o % PM_T + H];
-            }
+            for (int q = 0; q < OWN; ++q) acc[q] += A[(ly + 8 * q + H) * W + lx + H];
         }
-        for (int i = threadIdx.x; i < WW; i += PM_TPB) {
-            const int tx = i % W, ty = i / W;
-            if (tx == 0 || ty == 0 || tx == W - 1 || ty == W - 1) continue;
-            const float c = A[i];
-            const float lap = (A[i - 1] + A[i + 1] - 2.f * c) * ihx + (A[i - W] + A[i + W] - 2.f * c) * ihy;
-            float rhs = Dc * lap - gam * c;
-            float add = 0.f;
-            if (use_src) {
-                rhs -= Rv[i] * c;
-                add = Sv[i] * inv_s;
+        // nodes that can still reach the output tile: [m + 1, W - m - 1)
+        const int lo = m + 1, hi = W - m - 1;
+        for (int ty = lo + ly; ty < hi; ty += 8) {
+            for (int tx = lo + lx; tx < hi; tx += 32) {
+                const int i = ty * W + tx;
+                const float c = A[i];
+                const float lap = (A[i - 1] + A[i + 1] - 2.f * c) * ihx + (A[i - W] + A[i + W] - 2.f * c) * ihy;
+                float rhs = Dc * lap - gam * c;
+                float add = 0.f;
+                if (use_src) {
+                    rhs -= Rv[i] * c;
+                    add = Sv[i] * inv_s;
+                }
+                float out = fmaf(dts, rhs, c + add);
+                if (BC == 1) {  // Dirichlet: wall nodes keep their value
+                    const int X = x0 + tx, Y = y0 + ty;
+                    if (X <= 0 || Y <= 0 || X >= gx - 1 || Y >= gy - 1) out = c;
+                }
+                B[i] = out;
             }
-            float out = fmaf(dts, rhs, c + add);
-            if (BC == 1) {  // Dirichlet: wall nodes keep their value
-                const int X = x0 + tx, Y = y0 + ty;
-                if (X <= 0 || Y <= 0 || X >= gx - 1 || Y >= gy - 1) out = c;
-            }
-            B[i] = out;
         }
         float *tmp = A;
         A = B;
         B = tmp;
     }
     __syncthreads();
+    const int X = blockIdx.x * PM_T + lx;
 #pragma unroll
     for (int q = 0; q < OWN; ++q) {
-        const int o = threadIdx.x + PM_TPB * q;
-        const int ox = o % PM_T, oy = o / PM_T;
-        const int X = blockIdx.x * PM_T + ox, Y = blockIdx.y * PM_T + oy;
+        const int oy = ly + 8 * q;
+        const int Y = blockIdx.y * PM_T + oy;
         if (X >= gx || Y >= gy) continue;
-        float v = A[(oy + H) * W + ox + H];
-        float av = acc[q];
+        float v = A[(oy + H) * W + lx + H];
         if (tau_mode && BC != 2) {
             float t = 1.f;
             if (X == 0 || X == gx - 1) t *= 0.5f;
@@ -1316,7 +1333,7 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
         }
         const int64_t g = lbase + (int64_t)Y * gx + X;
         cout[g] = v;
-        if (avg) avg[g] = avg_first ? av * avg_scale : fmaf(av, avg_scale, avg[g]);
+        if (avg) avg[g] = avg_first ? acc[q] * avg_scale : fmaf(acc[q], avg_scale, avg[g]);
     }
 }
 
@@ -1544,7 +1561,7 @@ __global__ void k_stage_starts(KP kp, uint32_t *__restrict__ out)
 }
 
 template <int DIM, bool PERIODIC, bool WARP>
-__global__ void __launch_bounds__(TPB, 4) k_stage_forces(KP kp, float *__restrict__ F_out, int32_t *__restrict__ count,
+__global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_stage_forces(KP kp, float *__restrict__ F_out, int32_t *__restrict__ count,
                                                       unsigned long long *__restrict__ idsum)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1627,14 +1644,14 @@ __global__ void k_fill(float *p, float v, int64_t n)
 static inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 
 // Pair kernels may need more than the default 48 KB of dynamic shared memory.
-// The pair kernels run 4 blocks per SM (register bound). Ask for just the
+// The pair kernels run CHEMO_PAIR_BLOCKS blocks per SM (register bound). Ask for just the
 // shared memory those blocks need and leave the rest of the SM's 256 KB to
 // L1, which caches the candidate positions.
 template <typename K>
 static void allow_smem(K kernel, size_t bytes)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    const double need = 4.0 * (double)(bytes + 1024) / (228.0 * 1024.0);
+    const double need = (double)CHEMO_PAIR_BLOCKS * (double)(bytes + 1024) / (228.0 * 1024.0);
     const int pct = (int)std::ceil(100.0 * need);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
 }
