@@ -271,7 +271,7 @@ def adjoint_ratio(chemo, wl, devc, stream):
         g = g.detach().contiguous()
         dth = torch.zeros(2 + p["n_species"], dtype=torch.float32, device=devc)
         c0 = torch.zeros(tuple(chemo.grid_shape(p)), dtype=torch.float32, device=devc)
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         for rep in range(2):  # the first pass warms up graphs and allocations
             chemo.chemo_write_state(sim, dpos, dsp, stream=stream)
             chemo.chemo_write_field(sim, c0, stream=stream)
@@ -284,15 +284,18 @@ def adjoint_ratio(chemo, wl, devc, stream):
             chemo.chemo_set_step_index(sim, 0, stream=stream)
             ev[2].record(stream)
             chemo.chemo_record(sim, steps, every, stream=stream)
+            ev[4].record(stream)
             chemo.chemo_gradient(sim, g, dth, stream=stream)
             ev[3].record(stream)
             torch.cuda.synchronize()
         fwd = ev[0].elapsed_time(ev[1])
         both = ev[2].elapsed_time(ev[3])
+        rec = ev[2].elapsed_time(ev[4])
         return {"workload": "adjoint_2d: 2D walls, N=%d two species, %dx%d grid (%d PDE substeps), %d steps, "
                             "checkpoints every %d, loss mean x displacement + soft occupancy (64^2), gradients wrt chi, inter, D_0, D_1"
                             % (n, p["grid"][0], p["grid"][1], chemo.chemo_get_info(sim)["pde_substeps"], steps, every),
-                "forward_ms": fwd, "forward_backward_ms": both, "ratio": both / fwd,
+                "forward_ms": fwd, "forward_backward_ms": both, "record_ms": rec, "gradient_ms": both - rec,
+                "ratio": both / fwd,
                 "gradients_finite": bool(torch.isfinite(dth).all().item())}
     finally:
         sim.close()
@@ -409,6 +412,9 @@ def variants_leg(chemo, wl, devc, stream, steps=200):
             ms = ev[0].elapsed_time(ev[1]) / steps
             out[name] = {"ms_per_step": ms, "particle_steps_per_s": pos.shape[0] / (ms * 1e-3),
                          "launches_per_step": chemo.chemo_get_info(sim)["launches_per_step"]}
+            if name == "baseline":
+                prof = chemo.chemo_profile_steps(sim, 50, stream=stream)
+                out[name]["kernel_ms"] = {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")}
     return out
 
 

@@ -106,6 +106,21 @@ __global__ void k_gather_state(KP kp, float *__restrict__ pos, uint8_t *__restri
     if (sp) sp[id] = (uint8_t)(w >> SP_SHIFT);
 }
 
+// Snapshot of the sorted state and its cell list (one launch for the three
+// copies): S (n float4), the count table (cw words), the group offsets (gw
+// words).
+__global__ void k_snapshot(const float4 *__restrict__ S, int64_t n, const uint32_t *__restrict__ cnt, int64_t cw,
+                           const uint32_t *__restrict__ gst, int64_t gw, float4 *__restrict__ S_out,
+                           uint32_t *__restrict__ cnt_out, uint32_t *__restrict__ gst_out)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + cw + gw; i += stride) {
+        if (i < n) S_out[i] = S[i];
+        else if (i < n + cw) cnt_out[i - n] = cnt[i - n];
+        else gst_out[i - n - cw] = gst[i - n - cw];
+    }
+}
+
 // Transposed Laplacian along one axis at node k (N nodes, stride): with
 // mirror ghosts the wall rows are (-2, 2) so the transpose differs there.
 __device__ __forceinline__ float lapT_axis(const float *__restrict__ mu, int64_t g, int k, int N, int64_t stride,
@@ -295,90 +310,105 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
 }
 
 // Pair term of the adjoint over the cell list of X^n (sorted S):
-// lambda_X^n_i += dt sum_j H_ij (lambda_Y_i - lambda_Y_j).
+// lambda_X^n_i += dt sum_j H_ij (lambda_Y_i - lambda_Y_j). APC threads share
+// a cell (each takes every APC-th candidate of each row range) and sum their
+// parts with shuffles.
+constexpr int APC = 8;
+
 template <int DIM, bool PERIODIC>
 __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restrict__ lamY, float *__restrict__ lamXn)
 {
-    const int64_t j = (int64_t)blockIdx.x * ATPB + threadIdx.x;
-    if (j >= kp.n) return;
-    const float4 me = kp.S[j];
-    const uint32_t w = __float_as_uint(me.w);
-    const int64_t id = w & ID_MASK;
-    if (id >= kp.n) return;
-    const int sp = (int)(w >> SP_SHIFT);
-    float li[3] = {0.f, 0.f, 0.f};
-    for (int a = 0; a < DIM; ++a) li[a] = lamY[id * DIM + a];
-    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    const float pc[3] = {me.x, me.y, me.z};
-    for (int a = 0; a < DIM; ++a) {
-        c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
-        const float f = __fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a];
-        if (kp.search == 2) {
-            lo[a] = f < 0.5f ? c[a] - 1 : c[a];
-            hi[a] = lo[a] + 1;
-        } else {
-            lo[a] = c[a] - 1;
-            hi[a] = c[a] + 1;
-        }
-        if (!PERIODIC) {
-            lo[a] = max(lo[a], 0);
-            hi[a] = min(hi[a], kp.nb[a] - 1);
-        }
-    }
+    const int64_t t = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    const int64_t j = t / APC;
+    const int sub = (int)(t % APC);
     float acc[3] = {0.f, 0.f, 0.f};
-    const uint32_t n = (uint32_t)kp.n;
-    for (int z = lo[2]; z <= hi[2]; ++z) {
-        int zz = z;
-        if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
-        for (int y = lo[1]; y <= hi[1]; ++y) {
-            int yy = y;
-            if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
-            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
-            // the row's bins as contiguous ranges of the sorted array (a
-            // periodic row that wraps is two ranges)
-            int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
-            if (PERIODIC && lo[0] < 0) {
-                xa[0] = 0;
-                xa[1] = xb[1] = kp.nb[0] + lo[0];
-            } else if (PERIODIC && hi[0] >= kp.nb[0]) {
-                xb[0] = kp.nb[0] - 1;
-                xa[1] = 0;
-                xb[1] = hi[0] - kp.nb[0];
+    int64_t id = -1;
+    if (j < kp.n) {
+        const float4 me = kp.S[j];
+        const uint32_t w = __float_as_uint(me.w);
+        id = w & ID_MASK;
+        if (id >= kp.n) id = -1;
+    }
+    if (id >= 0) {
+        const float4 me = kp.S[j];
+        const int sp = (int)(__float_as_uint(me.w) >> SP_SHIFT);
+        float li[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < DIM; ++a) li[a] = lamY[id * DIM + a];
+        int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        const float pc[3] = {me.x, me.y, me.z};
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+            const float f = __fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a];
+            if (kp.search == 2) {
+                lo[a] = f < 0.5f ? c[a] - 1 : c[a];
+                hi[a] = lo[a] + 1;
+            } else {
+                lo[a] = c[a] - 1;
+                hi[a] = c[a] + 1;
             }
-            for (int piece = 0; piece < 2; ++piece) {
-                if (xa[piece] > xb[piece]) continue;
-                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
-                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
-                for (uint32_t q = q0; q < q1; ++q) {
-                    if (q == (uint32_t)j) continue;
-                    const float4 o = __ldg(&kp.S[q]);
-                    float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
-                    if (PERIODIC)
+            if (!PERIODIC) {
+                lo[a] = max(lo[a], 0);
+                hi[a] = min(hi[a], kp.nb[a] - 1);
+            }
+        }
+        const uint32_t n = (uint32_t)kp.n;
+        for (int z = lo[2]; z <= hi[2]; ++z) {
+            int zz = z;
+            if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
+            for (int y = lo[1]; y <= hi[1]; ++y) {
+                int yy = y;
+                if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+                // the row's bins as contiguous ranges of the sorted array (a
+                // periodic row that wraps is two ranges)
+                int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
+                if (PERIODIC && lo[0] < 0) {
+                    xa[0] = 0;
+                    xa[1] = xb[1] = kp.nb[0] + lo[0];
+                } else if (PERIODIC && hi[0] >= kp.nb[0]) {
+                    xb[0] = kp.nb[0] - 1;
+                    xa[1] = 0;
+                    xb[1] = hi[0] - kp.nb[0];
+                }
+                for (int piece = 0; piece < 2; ++piece) {
+                    if (xa[piece] > xb[piece]) continue;
+                    const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
+                    const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
+                    for (uint32_t q = q0 + (uint32_t)sub; q < q1; q += APC) {
+                        if (q == (uint32_t)j) continue;
+                        const float4 o = __ldg(&kp.S[q]);
+                        float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
+                        if (PERIODIC)
+                            for (int a = 0; a < DIM; ++a) {
+                                if (d[a] > kp.halfL[a]) d[a] -= kp.L[a];
+                                else if (d[a] < -kp.halfL[a]) d[a] += kp.L[a];
+                            }
+                        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                        const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+                        if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) continue;
+                        const int64_t jd = __float_as_uint(o.w) & ID_MASK;
+                        if (jd >= kp.n) continue;
+                        const float r = sqrtf(r2), rinv = 1.f / r;
+                        const float e = __expf(-r * kp.inv_eps[st]);
+                        const float f = kp.amp_f[st] * (e - kp.shift[st]);
+                        const float fp = -kp.amp_f[st] * kp.inv_eps[st] * e;
+                        float dl[3], dot = 0.f;
                         for (int a = 0; a < DIM; ++a) {
-                            if (d[a] > kp.halfL[a]) d[a] -= kp.L[a];
-                            else if (d[a] < -kp.halfL[a]) d[a] += kp.L[a];
+                            dl[a] = li[a] - lamY[jd * DIM + a];
+                            dot = fmaf(d[a] * rinv, dl[a], dot);
                         }
-                    const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                    const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
-                    if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) continue;
-                    const int64_t jd = __float_as_uint(o.w) & ID_MASK;
-                    if (jd >= kp.n) continue;
-                    const float r = sqrtf(r2), rinv = 1.f / r;
-                    const float e = __expf(-r * kp.inv_eps[st]);
-                    const float f = kp.amp_f[st] * (e - kp.shift[st]);
-                    const float fp = -kp.amp_f[st] * kp.inv_eps[st] * e;
-                    float dl[3], dot = 0.f;
-                    for (int a = 0; a < DIM; ++a) {
-                        dl[a] = li[a] - lamY[jd * DIM + a];
-                        dot = fmaf(d[a] * rinv, dl[a], dot);
+                        const float s1 = f * rinv, s2 = (fp - f * rinv) * dot;
+                        for (int a = 0; a < DIM; ++a) acc[a] += s1 * dl[a] + s2 * d[a] * rinv;
                     }
-                    const float s1 = f * rinv, s2 = (fp - f * rinv) * dot;
-                    for (int a = 0; a < DIM; ++a) acc[a] += s1 * dl[a] + s2 * d[a] * rinv;
                 }
             }
         }
     }
-    for (int a = 0; a < DIM; ++a) lamXn[id * DIM + a] += kp.dt * acc[a];
+    // the APC threads of a cell are consecutive lanes of one warp
+    for (int o = APC / 2; o > 0; o >>= 1)
+        for (int a = 0; a < DIM; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if (id >= 0 && sub == 0)
+        for (int a = 0; a < DIM; ++a) lamXn[id * DIM + a] += kp.dt * acc[a];
 }
 
 __global__ void k_params_out(const double *dpar, float *out, int np)
@@ -534,14 +564,16 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
             if (G) ATRY(cudaMemcpyAsync(t->seg_c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
             // the sorted state and its cell list, for the pair term of the reverse sweep
             const KP v = eng_view(s);
-            if (n) ATRY(cudaMemcpyAsync(t->seg_S + (size_t)k * n, v.S, (size_t)n * sizeof(float4),
-                                        cudaMemcpyDeviceToDevice, st));
-            ATRY(cudaMemcpyAsync(t->seg_cnt + (size_t)k * t->cwords, v.cnt_cur, t->cwords * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToDevice, st));
-            ATRY(cudaMemcpyAsync(t->seg_gst + (size_t)k * t->gwords, v.gstart, t->gwords * sizeof(uint32_t),
-                                 cudaMemcpyDeviceToDevice, st));
-            if (n) ATRY(cudaMemsetAsync(t->seg_F + (size_t)k * n * dim, 0, (size_t)n * dim * sizeof(float), st));
-            s->kp.F_save = t->seg_F + (size_t)k * n * dim;  // the step's pair force, by id
+            {
+                const int64_t tot = n + (int64_t)t->cwords + (int64_t)t->gwords;
+                const unsigned nb = (unsigned)std::min<int64_t>((tot + ATPB - 1) / ATPB, 152 * 16);
+                k_snapshot<<<nb, ATPB, 0, st>>>(v.S, n, v.cnt_cur, (int64_t)t->cwords, v.gstart, (int64_t)t->gwords,
+                                                t->seg_S + (size_t)k * n, t->seg_cnt + (size_t)k * t->cwords,
+                                                t->seg_gst + (size_t)k * t->gwords);
+                ATRY(cudaGetLastError());
+            }
+            // the step's pair force, by id (the particle kernel writes every cell's)
+            s->kp.F_save = t->seg_F + (size_t)k * n * dim;
             r = eng_enqueue_step(s, st, nullptr);
             s->kp.F_save = nullptr;
             if (r) return r;
@@ -593,11 +625,11 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
                     if (dim == 2) {
-                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<2, false><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     } else {
-                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<3, false><<<blocks(n), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     }
                     ATRY(cudaGetLastError());
                 }

@@ -1232,7 +1232,8 @@ __global__ void __launch_bounds__(256) k_pde_stream(KP kp, const float *__restri
 // substep, never the tile itself.
 // ---------------------------------------------------------------------------
 constexpr int PM_T = 32;
-constexpr int PM_TPB = 256;
+constexpr int PM_TPB = 1024;  // one thread per output node
+constexpr int PM_ROWS = PM_TPB / 32;
 
 __device__ __forceinline__ int pm_map(int k, int N, int bc)
 {
@@ -1253,7 +1254,7 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
                                                       float avg_scale, int tau_mode)
 {
     extern __shared__ float pm[];
-    // threads as 32 columns x 8 rows; the tile is W x W, W = PM_T + 2 nsub <= 56
+    // threads as 32 columns x PM_ROWS rows; the tile is W x W, W = PM_T + 2 nsub <= 56
     const int H = nsub, W = PM_T + 2 * nsub, WW = W * W;
     const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
     float *A = pm, *B = pm + WW;
@@ -1261,7 +1262,7 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
     const int gx = kp.g[0], gy = kp.g[1];
     const int x0 = blockIdx.x * PM_T - H, y0 = blockIdx.y * PM_T - H;
     const int64_t lbase = (int64_t)blockIdx.z * gx * gy;  // layer of an ensemble
-    for (int ty = ly; ty < W; ty += 8) {
+    for (int ty = ly; ty < W; ty += PM_ROWS) {
         const int my = pm_map(y0 + ty, gy, BC);
         const bool ywall = my == 0 || my == gy - 1;
         for (int tx = lx; tx < W; tx += 32) {
@@ -1280,7 +1281,7 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
             }
         }
     }
-    constexpr int OWN = PM_T * PM_T / PM_TPB;  // output nodes per thread: column lx, rows ly + 8 q
+    constexpr int OWN = PM_T * PM_T / PM_TPB;  // output nodes per thread: column lx, rows ly + PM_ROWS q
     float acc[OWN];
 #pragma unroll
     for (int q = 0; q < OWN; ++q) acc[q] = 0.f;
@@ -1290,11 +1291,11 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
         __syncthreads();
         if (avg) {
 #pragma unroll
-            for (int q = 0; q < OWN; ++q) acc[q] += A[(ly + 8 * q + H) * W + lx + H];
+            for (int q = 0; q < OWN; ++q) acc[q] += A[(ly + PM_ROWS * q + H) * W + lx + H];
         }
         // nodes that can still reach the output tile: [m + 1, W - m - 1)
         const int lo = m + 1, hi = W - m - 1;
-        for (int ty = lo + ly; ty < hi; ty += 8) {
+        for (int ty = lo + ly; ty < hi; ty += PM_ROWS) {
             for (int tx = lo + lx; tx < hi; tx += 32) {
                 const int i = ty * W + tx;
                 const float c = A[i];
@@ -1321,7 +1322,7 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
     const int X = blockIdx.x * PM_T + lx;
 #pragma unroll
     for (int q = 0; q < OWN; ++q) {
-        const int oy = ly + 8 * q;
+        const int oy = ly + PM_ROWS * q;
         const int Y = blockIdx.y * PM_T + oy;
         if (X >= gx || Y >= gy) continue;
         float v = A[(oy + H) * W + lx + H];
