@@ -108,3 +108,40 @@ def test_record_leaves_final_state_and_gradient_restores_it():
         np.testing.assert_array_equal(pa2, pa)
         assert chemo.chemo_step_index(a) == 10
         assert torch.isfinite(dth).all()
+
+
+@pytest.mark.parametrize("over", [dict(), dict(boundary=1, pde_bc=2), dict(pde_substeps=3, Dc=5.0)])
+def test_parameter_gradients_3d_match_oracle_finite_differences(over):
+    """The 3D adjoint (transposed 7-point stencil written out, trilinear
+    interpolation Jacobian, 3^3 pair window) against FP64 central finite
+    differences of the oracle."""
+    p = wl.params("clumps_grid_3d", grid=[17, 17, 17], dt=1e-5, diameter=[0.04, 0.06], cutoff_mode=1, **over)
+    pos = wl.uniform_positions(700, 3, p["lo"], p["hi"], seed=31)
+    sp = wl.half_species(700, 2)
+    c0 = wl.random_field(p, seed=32, scale=0.3)
+    nsteps, every = 12, 4
+    dpos = torch.from_numpy(pos).cuda()
+    dsp = torch.from_numpy(sp).cuda()
+    with chemo.chemo_create(p, dpos, dsp) as sim:
+        theta = torch.tensor(adj.theta_of(p), dtype=torch.float64, requires_grad=True)
+        x0 = dpos.clone().requires_grad_(True)
+        xN = adj.ChemoRun.apply(theta, x0, sim, nsteps, every, dsp, torch.from_numpy(c0).cuda())
+        L = adj.mean_x_displacement(xN, x0) + adj.occupancy_loss(xN, NB, p["lo"], p["hi"])
+        L.backward()
+        g = theta.grad.numpy().copy()
+
+    def loss(th):
+        q = adj.with_theta(p, th)
+        xT, _, _, _ = orc.run(q, pos, sp, c0.astype(np.float64), nsteps=nsteps)
+        return adj.loss_numpy(xT, pos, NB, p["lo"], p["hi"])
+
+    theta_np = np.array(adj.theta_of(p))
+    h = 1e-4
+    fd = np.zeros_like(theta_np)
+    for k in range(theta_np.size):
+        tp = theta_np.copy(); tp[k] += h
+        tm = theta_np.copy(); tm[k] -= h
+        fd[k] = (loss(tp) - loss(tm)) / (2 * h)
+    scale = np.abs(fd).max()
+    assert scale > 0
+    assert np.all(np.abs(g - fd) <= 0.03 * np.abs(fd) + 0.01 * scale), (g, fd)
