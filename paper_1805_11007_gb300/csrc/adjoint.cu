@@ -58,7 +58,8 @@ struct Tape {
     float *seg_F = nullptr;             // pair force of each step, by id (n x dim)
     size_t cwords = 0, gwords = 0;      // words of one count table / offset table
     float *dpf = nullptr;               // parameter gradient (float) for the caller
-    double *dpar = nullptr;             // 2 + MAXS accumulators
+    double *dpar = nullptr;             // (2 + MAXS) x pstride per-block partials
+    int64_t pstride = 0;                // blocks of the per-cell kernel
 };
 
 }  // namespace
@@ -156,61 +157,76 @@ __global__ void k_adj_pde(KP kp, const float *__restrict__ mu_in, float *__restr
     lamS[g] = (first ? 0.f : lamS[g]) + m * inv_s;
 }
 
-// Multilinear weights and their gradients at x: for each of the 2^d corners,
-// node indices, weight and d(weight)/dx_a.
+__device__ __forceinline__ int64_t nidx(const KP &kp, const int *k) { return gidx(kp, k[0], k[1], k[2]); }
+
+// Corner m of the 2^d nodes around x: node indices, multilinear weight and
+// its gradient d(weight)/dx_b.
 template <int DIM>
-__device__ __forceinline__ void corners(const KP &kp, const float *x, int node[8][3], float w[8], float dw[8][3])
+__device__ __forceinline__ void corner_of(const KP &kp, const float *x, int m, int node[3], float &w, float dw[3])
 {
     int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
     float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
     for (int a = 0; a < DIM; ++a) gcell(kp, a, x[a], k0[a], k1[a], f[a]);
-    for (int m = 0; m < (1 << DIM); ++m) {
-        float wt = 1.f;
-        for (int a = 0; a < 3; ++a) {
-            const int bit = (m >> a) & 1;
-            node[m][a] = a < DIM ? (bit ? k1[a] : k0[a]) : 0;
-            if (a < DIM) wt *= bit ? f[a] : 1.f - f[a];
+    w = 1.f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int bit = (m >> a) & 1;
+        node[a] = a < DIM ? (bit ? k1[a] : k0[a]) : 0;
+        if (a < DIM) w *= bit ? f[a] : 1.f - f[a];
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float d = 0.f;
+        if (b < DIM) {
+            d = ((m >> b) & 1) ? kp.inv_h[b] : -kp.inv_h[b];
+#pragma unroll
+            for (int a = 0; a < DIM; ++a)
+                if (a != b) d *= ((m >> a) & 1) ? f[a] : 1.f - f[a];
         }
-        w[m] = wt;
-        for (int b = 0; b < 3; ++b) {
-            float d = 0.f;
-            if (b < DIM) {
-                d = ((m >> b) & 1) ? kp.inv_h[b] : -kp.inv_h[b];
-                for (int a = 0; a < DIM; ++a)
-                    if (a != b) d *= ((m >> a) & 1) ? f[a] : 1.f - f[a];
-            }
-            dw[m][b] = d;
-        }
+        dw[b] = d;
     }
 }
 
-__device__ __forceinline__ int64_t nidx(const KP &kp, const int *k) { return gidx(kp, k[0], k[1], k[2]); }
-
-__device__ __forceinline__ void warp_add_double(double v, double *dst)
+// Adds v over the block into the block's own slot dst[blockIdx.x] (no two
+// blocks share a slot; the kernels of successive steps run in order, so no
+// atomics are needed). Every thread of the block must call it.
+__device__ __forceinline__ void block_add_double(double v, double *dst, double *red)
 {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+    const int wid = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[wid] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < ATPB / 32; ++k) s += red[k];
+        dst[blockIdx.x] += s;
+    }
 }
 
-// Per-cell adjoint terms (by id). Reads X^n, X^{n+1}, c^n, lambda_X^{n+1},
-// lambda_S and the step's pair force Fb (f_unit Fb = dF/dinter); writes lambda_Y and the local
-// part of lambda_X^n, scatters the interpolation transpose into lambda_c and
-// accumulates the parameter gradients.
+// Per-cell adjoint terms (by id), one thread per cell. Reads X^n, X^{n+1},
+// c^n, lambda_X^{n+1}, lambda_S and the step's pair force Fb (f_unit Fb =
+// dF/dinter); writes lambda_Y and the local part of lambda_X^n, scatters the
+// interpolation transpose into lambda_c and adds the parameter gradients to
+// the block's slots of dpar.
 template <int DIM>
 __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restrict__ Xn, const float *__restrict__ Xn1,
                                                     const uint8_t *__restrict__ spec, const float *__restrict__ cn,
                                                     const float *__restrict__ lamX1, const float *__restrict__ lamS,
                                                     const float *__restrict__ Fb, float f_unit, float *__restrict__ lamY,
                                                     float *__restrict__ lamXn, float *__restrict__ lamC,
-                                                    unsigned long long step, double *dpar, int has_grid,
-                                                    int lams_over_tau)
+                                                    unsigned long long step, double *dpar, int64_t pstride,
+                                                    int has_grid, int lams_over_tau)
 {
+    __shared__ double red[ATPB / 32];
+    constexpr int NC = 1 << DIM;
     const int64_t i = (int64_t)blockIdx.x * ATPB + threadIdx.x;
     const bool valid = i < kp.n;
-    double d_chi = 0.0, d_int = 0.0, d_D[MAXS];
-    for (int s = 0; s < MAXS; ++s) d_D[s] = 0.0;
+    double d_chi = 0.0, d_int = 0.0, d_Ds = 0.0;  // d_Ds: dL/dD of this cell's species
+    int sp = 0;
     if (valid) {
-        const int sp = spec[i];
+        sp = spec[i];
         float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
         for (int a = 0; a < DIM; ++a) {
             x0[a] = Xn[i * DIM + a];
@@ -219,47 +235,49 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
         }
         // 2. deposit transpose at X^{n+1}
         if (has_grid && kp.src[sp] != 0.f) {
-            int node[8][3];
-            float w[8], dw[8][3];
-            corners<DIM>(kp, x1, node, w, dw);
-            for (int m = 0; m < (1 << DIM); ++m) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                int nd[3];
+                float wm, dwm[3];
+                corner_of<DIM>(kp, x1, m, nd, wm, dwm);
                 float inv_tau = 1.f;
                 if (kp.pde_bc != 2 && !lams_over_tau)  // (already divided by tau when lams_over_tau)
                     for (int a = 0; a < DIM; ++a)
-                        if (node[m][a] == 0 || node[m][a] == kp.g[a] - 1) inv_tau *= 2.f;
-                const float l = lamS[nidx(kp, node[m])] * inv_tau * kp.src[sp];
-                for (int a = 0; a < DIM; ++a) lx[a] = fmaf(l, dw[m][a], lx[a]);
+                        if (nd[a] == 0 || nd[a] == kp.g[a] - 1) inv_tau *= 2.f;
+                const float l = lamS[nidx(kp, nd)] * inv_tau * kp.src[sp];
+                for (int a = 0; a < DIM; ++a) lx[a] = fmaf(l, dwm[a], lx[a]);
             }
         }
-        // forward quantities at X^n: gradient interpolation, noise, pre-boundary Y
+        // forward quantities at X^n: gradient interpolation and its Jacobian
         const float chem = kp.chem[sp];
         float G[3] = {0.f, 0.f, 0.f}, J[3][3] = {{0.f}};
-        int node[8][3];
-        float w[8], dw[8][3];
         const bool interp = has_grid && kp.chem_mode == 0;
         if (kp.chem_mode == 1) {
             for (int a = 0; a < DIM; ++a) G[a] = kp.fixed_g[a];
         } else if (interp) {
-            corners<DIM>(kp, x0, node, w, dw);
-            for (int m = 0; m < (1 << DIM); ++m)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                int nd[3];
+                float wm, dwm[3];
+                corner_of<DIM>(kp, x0, m, nd, wm, dwm);
                 for (int a = 0; a < DIM; ++a) {
-                    int kp1[3] = {node[m][0], node[m][1], node[m][2]}, km1[3] = {node[m][0], node[m][1], node[m][2]};
-                    kp1[a] = gnbr(kp, a, node[m][a] + 1);
-                    km1[a] = gnbr(kp, a, node[m][a] - 1);
+                    int kp1[3] = {nd[0], nd[1], nd[2]}, km1[3] = {nd[0], nd[1], nd[2]};
+                    kp1[a] = gnbr(kp, a, nd[a] + 1);
+                    km1[a] = gnbr(kp, a, nd[a] - 1);
                     const float ga = (cn[nidx(kp, kp1)] - cn[nidx(kp, km1)]) * kp.inv_2h[a];
-                    G[a] = fmaf(w[m], ga, G[a]);
-                    for (int b = 0; b < DIM; ++b) J[a][b] = fmaf(dw[m][b], ga, J[a][b]);
+                    G[a] = fmaf(wm, ga, G[a]);
+                    for (int b = 0; b < DIM; ++b) J[a][b] = fmaf(dwm[b], ga, J[a][b]);
                 }
+            }
         }
-        const uint32_t id = (uint32_t)i;
-        const uint4 rw = cell_words(kp, id, step, TAG_MOVE);
+        // noise and the pre-boundary position Y (reflection signs)
+        const uint4 rw = cell_words(kp, (uint32_t)i, step, TAG_MOVE);
         const float2 n01 = box_muller(rw.x, rw.y);
         const float xi[3] = {n01.x, n01.y, DIM == 3 ? box_muller(rw.z, rw.w).x : 0.f};
         const float amp = kp.noise[sp];
         float sgn[3] = {1.f, 1.f, 1.f};
         for (int a = 0; a < DIM; ++a) {
-            const float Fa = Fb[i * DIM + a];
-            float y = x0[a] + kp.dt * (Fa + chem * G[a]) + amp * xi[a];
+            float y = x0[a] + kp.dt * (Fb[i * DIM + a] + chem * G[a]) + amp * xi[a];
             if (!kp.periodic) {
                 for (int it = 0; it < 16 && (y < kp.lo[a] || y > kp.hi[a]); ++it) {
                     y = y < kp.lo[a] ? 2.f * kp.lo[a] - y : 2.f * kp.hi[a] - y;
@@ -267,7 +285,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
                 }
             }
         }
-        // 3. boundary, 4. local terms, 5. parameters
+        // 3. boundary, 4. local terms
         float ly[3] = {0.f, 0.f, 0.f};
         for (int a = 0; a < DIM; ++a) {
             ly[a] = sgn[a] * lx[a];
@@ -282,18 +300,25 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
             }
             lamXn[i * DIM + b] = t;
         }
+        // interpolation transpose onto the nodes
         if (interp && chem != 0.f) {
-            for (int m = 0; m < (1 << DIM); ++m)
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                int nd[3];
+                float wm, dwm[3];
+                corner_of<DIM>(kp, x0, m, nd, wm, dwm);
                 for (int a = 0; a < DIM; ++a) {
-                    const float coef = kp.dt * chem * w[m] * ly[a] * kp.inv_2h[a];
+                    const float coef = kp.dt * chem * wm * ly[a] * kp.inv_2h[a];
                     if (coef == 0.f) continue;
-                    int kp1[3] = {node[m][0], node[m][1], node[m][2]}, km1[3] = {node[m][0], node[m][1], node[m][2]};
-                    kp1[a] = gnbr(kp, a, node[m][a] + 1);
-                    km1[a] = gnbr(kp, a, node[m][a] - 1);
+                    int kp1[3] = {nd[0], nd[1], nd[2]}, km1[3] = {nd[0], nd[1], nd[2]};
+                    kp1[a] = gnbr(kp, a, nd[a] + 1);
+                    km1[a] = gnbr(kp, a, nd[a] - 1);
                     atomicAdd(&lamC[nidx(kp, kp1)], coef);
                     atomicAdd(&lamC[nidx(kp, km1)], -coef);
                 }
+            }
         }
+        // 5. parameters
         double gl = 0.0, fl = 0.0, xl = 0.0;
         for (int a = 0; a < DIM; ++a) {
             gl += (double)G[a] * ly[a];
@@ -302,11 +327,12 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
         }
         d_chi = (double)kp.dt * (double)kp.chemotactic_f[sp] * gl;
         d_int = (double)kp.dt * fl;
-        if (amp > 0.f) d_D[sp] = (double)kp.dt / (double)amp * xl;  // d sqrt(2 D dt)/dD = dt / sqrt(2 D dt)
+        if (amp > 0.f) d_Ds = (double)kp.dt / (double)amp * xl;  // d sqrt(2 D dt)/dD = dt / sqrt(2 D dt)
     }
-    warp_add_double(d_chi, &dpar[0]);
-    warp_add_double(d_int, &dpar[1]);
-    for (int s = 0; s < kp.ns; ++s) warp_add_double(d_D[s], &dpar[2 + s]);
+    // parameter partials: slot blockIdx.x of each parameter's row of dpar
+    block_add_double(d_chi, dpar, red);
+    block_add_double(d_int, dpar + pstride, red);
+    for (int s = 0; s < kp.ns; ++s) block_add_double(s == sp ? d_Ds : 0.0, dpar + (2 + s) * pstride, red);
 }
 
 // Pair term of the adjoint over the cell list of X^n (sorted S):
@@ -411,10 +437,15 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
         for (int a = 0; a < DIM; ++a) lamXn[id * DIM + a] += kp.dt * acc[a];
 }
 
-__global__ void k_params_out(const double *dpar, float *out, int np)
+// Sums each parameter's row of per-block partials (one warp per parameter).
+__global__ void k_params_out(const double *dpar, int64_t pstride, float *out, int np)
 {
-    const int i = threadIdx.x;
-    if (i < np) out[i] = (float)dpar[i];
+    const int p = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (p >= np) return;
+    double s = 0.0;
+    for (int64_t b = lane; b < pstride; b += 32) s += dpar[p * pstride + b];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) out[p] = (float)s;
 }
 
 unsigned blocks(int64_t n) { return (unsigned)((n + ATPB - 1) / ATPB); }
@@ -535,7 +566,8 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         t->seg_gst = (uint32_t *)p;
         if ((r = talloc(t, &p, E * pb))) return r;
         t->seg_F = (float *)p;
-        if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS)))) return r;
+        t->pstride = (int64_t)blocks(std::max<int64_t>(n, 1));
+        if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS) * (size_t)t->pstride))) return r;
         t->dpar = (double *)p;
         if ((r = talloc(t, &p, sizeof(float) * (2 + MAXS)))) return r;
         t->dpf = (float *)p;
@@ -547,7 +579,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         if (dL_dc_final) ATRY(cudaMemcpyAsync(t->lamC[lc], dL_dc_final, (size_t)G * sizeof(float), in_kind, st));
         else ATRY(cudaMemsetAsync(t->lamC[lc], 0, gb, st));
     }
-    ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS), st));
+    ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS) * (size_t)t->pstride, st));
     // the pair force is linear in inter: dF/dinter = F / inter (the cell list
     // is not built for the cutoff when inter = 0, and dL/dinter is then 0)
     const float f_unit = s->prm.inter != 0.f ? 1.f / s->prm.inter : 0.f;
@@ -617,11 +649,11 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                 if (dim == 2)
                     k_adj_cells<2><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             G ? 1 : 0, kp.pde_multi);
+                                                             t->pstride, G ? 1 : 0, kp.pde_multi);
                 else
                     k_adj_cells<3><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             G ? 1 : 0, kp.pde_multi);
+                                                             t->pstride, G ? 1 : 0, kp.pde_multi);
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
                     if (dim == 2) {
@@ -640,7 +672,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     // outputs
     const int np = 2 + t->ns;
     float *dpf = t->dpf;
-    k_params_out<<<1, 32, 0, st>>>(t->dpar, dpf, np);
+    k_params_out<<<1, 32 * (2 + MAXS), 0, st>>>(t->dpar, t->pstride, dpf, np);
     ATRY(cudaGetLastError());
     const cudaMemcpyKind out_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     ATRY(cudaMemcpyAsync(dL_dparams, dpf, sizeof(float) * np, out_kind, st));
