@@ -252,8 +252,11 @@ void fill_model(const chemo_params &p, KP &kp)
         smax = std::max(smax, (double)std::fabs(kp.kde_src[s]));
         rmax = std::max(rmax, (double)std::fabs(kp.kde_cons[s]));
     }
-    kp.kde_qs = (float)std::ldexp(smax > 0.0 ? smax : 1.0, -32);
-    kp.kde_qr = (float)std::ldexp(rmax > 0.0 ? rmax : 1.0, -32);
+    kp.kde_qs = (float)std::ldexp(smax > 0.0 ? smax : 1.0, -24);
+    kp.kde_qr = (float)std::ldexp(rmax > 0.0 ? rmax : 1.0, -24);
+    double kr = 0.0;
+    for (int s = 0; s < MAXS; ++s) kr = std::max(kr, kp.kde_r2[s] > 0.f ? std::sqrt((double)kp.kde_r2[s]) : 0.0);
+    kp.kde_rmax = (float)(kr * (1.0 + 1e-4));  // margin over the rounding of bin edges
     kp.kde_qs_inv = (float)(1.0 / (double)kp.kde_qs);
     kp.kde_qr_inv = (float)(1.0 / (double)kp.kde_qr);
     kp.dt = (float)p.dt;

@@ -75,7 +75,8 @@ struct KP {
     float kde_c[MAXS];           // 1 / (2 sigma_s^2)
     float kde_src[MAXS];         // dt k_s (2 pi sigma_s^2)^(-d/2)
     float kde_cons[MAXS];        // kappa_s (2 pi sigma_s^2)^(-d/2)
-    float kde_qs, kde_qs_inv;    // fixed-point quantum of the source sum (2^-32 of its largest term)
+    float kde_rmax;              // largest truncation radius over the species
+    float kde_qs, kde_qs_inv;    // fixed-point quantum of the source sum (2^-24 of its largest term)
     float kde_qr, kde_qr_inv;    // the same for the consumption sum
     float hgrid[3];              // grid spacing per axis
     double lo_d[3], hgrid_d[3];  // box corner and grid spacing in double (node positions)

@@ -1428,10 +1428,18 @@ __global__ void __launch_bounds__(TPB) k_hard_sphere(KP kp)
 // listing of Sect. 3): node l gathers, through the cell list of the sorted
 // state, the cells within kde_range bandwidths, K_s(x) = (2 pi sigma_s^2)^
 // (-d/2) exp(-|x|^2 / (2 sigma_s^2)), and writes the source dt sum k_s K_s
-// and the consumption sum kappa_s K_s. The sums are exact (int64 fixed point,
-// 2^-32 of the largest term), so the result does not depend on the order of
-// the cells inside a bin.
+// and the consumption sum kappa_s K_s. Only the bins that meet the sphere of
+// the largest truncation radius are visited: rows farther away are skipped
+// and each row is cut to one contiguous x-range. The sums are exact (32-bit
+// fixed point, 2^-24 of the largest term, folded into 64 bits every 64
+// terms), so the result does not depend on the order of the cells in a bin.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ float kde_gap(float p, float lo, float b, int k, int c)
+{
+    if (k == c) return 0.f;
+    return k < c ? p - (lo + (float)(k + 1) * b) : (lo + (float)k * b) - p;
+}
+
 template <int DIM, bool PERIODIC>
 __global__ void __launch_bounds__(TPB) k_kde(KP kp, float *__restrict__ S_out, float *__restrict__ R_out)
 {
@@ -1452,8 +1460,9 @@ __global__ void __launch_bounds__(TPB) k_kde(KP kp, float *__restrict__ S_out, f
         nlo[a] = (float)(v - (double)node[a]);
     }
     const float4 me = make_float4(node[0], node[1], node[2], 0.f);
-    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     const int W = kp.kde_win;
+    const float R = kp.kde_rmax, R2 = R * R;
+    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     for (int a = 0; a < DIM; ++a) {
         c[a] = bin_axis(node[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
         lo[a] = c[a] - W;
@@ -1463,18 +1472,39 @@ __global__ void __launch_bounds__(TPB) k_kde(KP kp, float *__restrict__ S_out, f
             hi[a] = min(hi[a], kp.nb[a] - 1);
         }
     }
-    if (DIM == 2) lo[2] = hi[2] = min(max(iz, 0), kp.layers - 1);
+    if (DIM == 2) lo[2] = hi[2] = c[2] = min(max(iz, 0), kp.layers - 1);
     long long accS = 0, accR = 0;
+    int accS32 = 0, accR32 = 0, nterm = 0;
     const uint32_t n = (uint32_t)kp.n;
     for (int z = lo[2]; z <= hi[2]; ++z) {
+        const float gz = DIM == 3 ? kde_gap(node[2], kp.lo[2], kp.bside[2], z, c[2]) : 0.f;
         const int zz = (PERIODIC && DIM == 3) ? (z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z)) : z;
         for (int y = lo[1]; y <= hi[1]; ++y) {
+            const float gyv = kde_gap(node[1], kp.lo[1], kp.bside[1], y, c[1]);
+            const float g2 = gyv * gyv + gz * gz;
+            if (!(g2 < R2)) continue;  // the row misses the sphere
             const int yy = PERIODIC ? (y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y)) : y;
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-                const int xx = PERIODIC ? (x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x)) : x;
-                const uint32_t k = bin_key(kp, xx, yy, zz);
-                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, k), n);
-                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), n);
+            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+            // x-bins that meet the sphere's section with this row
+            const float ext = sqrtf(R2 - g2) + 1e-4f * kp.bside[0];  // margin over the rounding of bin edges
+            int x0 = (int)floorf((node[0] - ext - kp.lo[0]) * kp.inv_b[0]);
+            int x1 = (int)floorf((node[0] + ext - kp.lo[0]) * kp.inv_b[0]);
+            x0 = max(x0, lo[0]);
+            x1 = min(x1, hi[0]);
+            int xa[2] = {x0, 0}, xb[2] = {x1, -1};
+            if (PERIODIC && x0 < 0) {
+                xa[0] = 0;
+                xa[1] = x0 + kp.nb[0];
+                xb[1] = kp.nb[0] - 1;
+            } else if (PERIODIC && x1 >= kp.nb[0]) {
+                xb[0] = kp.nb[0] - 1;
+                xa[1] = 0;
+                xb[1] = x1 - kp.nb[0];
+            }
+            for (int piece = 0; piece < 2; ++piece) {
+                if (xa[piece] > xb[piece]) continue;
+                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
                 for (uint32_t q = q0; q < q1; ++q) {
                     const float4 o = __ldg(&kp.S[q]);
                     const int s = (int)(__float_as_uint(o.w) >> SP_SHIFT);
@@ -1486,12 +1516,19 @@ __global__ void __launch_bounds__(TPB) k_kde(KP kp, float *__restrict__ S_out, f
                     r2 = DIM == 3 ? fmaf(dx, dx, fmaf(dy, dy, dz * dz)) : fmaf(dx, dx, dy * dy);
                     if (!(r2 < kp.kde_r2[s])) continue;
                     const float e = __expf(-r2 * kp.kde_c[s]);
-                    accS += __float2ll_rn(kp.kde_src[s] * e * kp.kde_qs_inv);
-                    accR += __float2ll_rn(kp.kde_cons[s] * e * kp.kde_qr_inv);
+                    accS32 += __float2int_rn(kp.kde_src[s] * e * kp.kde_qs_inv);
+                    accR32 += __float2int_rn(kp.kde_cons[s] * e * kp.kde_qr_inv);
+                    if (++nterm == 64) {  // terms are below 2^24: 64 of them fit an int32
+                        accS += accS32;
+                        accR += accR32;
+                        accS32 = accR32 = nterm = 0;
+                    }
                 }
             }
         }
     }
+    accS += accS32;
+    accR += accR32;
     S_out[g] = (float)((double)accS * (double)kp.kde_qs);
     if (R_out) R_out[g] = (float)((double)accR * (double)kp.kde_qr);
 }
