@@ -1346,54 +1346,74 @@ __global__ void __launch_bounds__(PM_TPB) k_pde_multi(KP kp, const float *__rest
 // again. The corrected cells go to U with their bins counted for the next
 // sort (as after the particle kernel).
 // ---------------------------------------------------------------------------
+constexpr int HS_TPC = 4;  // threads per cell of the correction (consecutive lanes)
+
 template <int DIM, bool PERIODIC>
 __global__ void __launch_bounds__(TPB) k_hard_sphere(KP kp)
 {
-    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
-    if (j >= kp.n) return;
-    const float4 me = kp.S[j];
+    const int64_t t = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const int64_t j = t / HS_TPC;
+    const int sub = (int)(t % HS_TPC);
+    const bool valid = j < kp.n;
+    const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
     const int sp = (int)(w >> SP_SHIFT);
-    int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    const float pc[3] = {me.x, me.y, me.z};
-    for (int a = 0; a < DIM; ++a) {
-        c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
-        lo[a] = c[a] - 1;
-        hi[a] = c[a] + 1;
-        if (!PERIODIC) {
-            lo[a] = max(lo[a], 0);
-            hi[a] = min(hi[a], kp.nb[a] - 1);
-        }
-    }
-    if (DIM == 2) lo[2] = hi[2] = layer_of(kp, me);
     float acc[3] = {0.f, 0.f, 0.f};
-    const uint32_t n = (uint32_t)kp.n;
-    for (int z = lo[2]; z <= hi[2]; ++z) {
-        const int zz = (PERIODIC && DIM == 3) ? (z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z)) : z;
-        for (int y = lo[1]; y <= hi[1]; ++y) {
-            const int yy = PERIODIC ? (y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y)) : y;
-            for (int x = lo[0]; x <= hi[0]; ++x) {
-                const int xx = PERIODIC ? (x < 0 ? x + kp.nb[0] : (x >= kp.nb[0] ? x - kp.nb[0] : x)) : x;
-                const uint32_t k = bin_key(kp, xx, yy, zz);
-                const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, k), n);
-                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, k + 1), n);
-                for (uint32_t q = q0; q < q1; ++q) {
-                    if (q == (uint32_t)j) continue;
-                    const float4 o = __ldg(&kp.S[q]);
-                    float dx, dy, dz, r2;
-                    pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
-                    const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
-                    const float contact = kp.hs_contact[st];
-                    if (!(r2 > 0.f) || !(r2 < contact * contact)) continue;
-                    const float r = sqrtf(r2);
-                    const float move = 2.f * (contact - r) * kp.hs_share[st] / r;
-                    acc[0] = fmaf(move, dx, acc[0]);
-                    acc[1] = fmaf(move, dy, acc[1]);
-                    if (DIM == 3) acc[2] = fmaf(move, dz, acc[2]);
+    if (valid) {
+        int c[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        const float pc[3] = {me.x, me.y, me.z};
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+            lo[a] = c[a] - 1;
+            hi[a] = c[a] + 1;
+            if (!PERIODIC) {
+                lo[a] = max(lo[a], 0);
+                hi[a] = min(hi[a], kp.nb[a] - 1);
+            }
+        }
+        if (DIM == 2) lo[2] = hi[2] = layer_of(kp, me);
+        const uint32_t n = (uint32_t)kp.n;
+        for (int z = lo[2]; z <= hi[2]; ++z) {
+            const int zz = (PERIODIC && DIM == 3) ? (z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z)) : z;
+            for (int y = lo[1]; y <= hi[1]; ++y) {
+                const int yy = PERIODIC ? (y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y)) : y;
+                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+                // the row's bins as contiguous ranges (a wrapped periodic row is two)
+                int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
+                if (PERIODIC && lo[0] < 0) {
+                    xa[0] = 0;
+                    xa[1] = xb[1] = kp.nb[0] + lo[0];
+                } else if (PERIODIC && hi[0] >= kp.nb[0]) {
+                    xb[0] = kp.nb[0] - 1;
+                    xa[1] = 0;
+                    xb[1] = hi[0] - kp.nb[0];
+                }
+                for (int piece = 0; piece < 2; ++piece) {
+                    if (xa[piece] > xb[piece]) continue;
+                    const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
+                    const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
+                    for (uint32_t q = q0 + (uint32_t)sub; q < q1; q += HS_TPC) {
+                        if (q == (uint32_t)j) continue;
+                        const float4 o = __ldg(&kp.S[q]);
+                        float dx, dy, dz, r2;
+                        pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                        const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+                        const float contact = kp.hs_contact[st];
+                        if (!(r2 > 0.f) || !(r2 < contact * contact)) continue;
+                        const float r = sqrtf(r2);
+                        const float move = 2.f * (contact - r) * kp.hs_share[st] / r;
+                        acc[0] = fmaf(move, dx, acc[0]);
+                        acc[1] = fmaf(move, dy, acc[1]);
+                        if (DIM == 3) acc[2] = fmaf(move, dz, acc[2]);
+                    }
                 }
             }
         }
     }
+    // the HS_TPC threads of a cell are consecutive lanes of one warp
+    for (int o = HS_TPC / 2; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    if (!valid || sub != 0) return;
     const float x1 = me.x + acc[0], y1 = me.y + acc[1], z1 = DIM == 3 ? me.z + acc[2] : me.z;
     float xb, yb, zb;
     if (PERIODIC) {
@@ -1905,7 +1925,7 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
 cudaError_t launch_hard_sphere(const KP &kp, cudaStream_t st, int *launches)
 {
     if (kp.n == 0) return cudaSuccess;
-    const unsigned nb = blocks_for(kp.n);
+    const unsigned nb = blocks_for(kp.n * HS_TPC);
     if (kp.dim == 2) {
         if (kp.periodic) k_hard_sphere<2, true><<<nb, TPB, 0, st>>>(kp);
         else k_hard_sphere<2, false><<<nb, TPB, 0, st>>>(kp);
