@@ -84,7 +84,10 @@ struct FAcc {
 #define CHEMO_LIST_CAP 24
 #endif
 constexpr int LIST_CAP = CHEMO_LIST_CAP;  // flushed once a lane holds more than LIST_CAP - UNROLL
-constexpr int UNROLL = 8;     // candidates per lane between two warp votes
+#ifndef CHEMO_UNROLL
+#define CHEMO_UNROLL 4
+#endif
+constexpr int UNROLL = CHEMO_UNROLL;  // candidates per lane between two warp votes
 
 template <int DIM, bool PERIODIC>
 struct RowCap {

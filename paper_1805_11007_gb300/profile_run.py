@@ -8,8 +8,9 @@ sequence at a time, or ``chemo_step_n`` with CUDA graphs) and prints one line
 with the elapsed time. The kernels each step launches, in order: ``k_step``
 (pair force, drift, move, counts of the next cell list), ``k_scan`` (offsets),
 ``k_scatter`` (counting sort, fused deposit) and the PDE substeps
-(``k_pde_stream``); with ``--workload adjoint_2d --adjoint 1`` the run is
-recorded and followed by one ``chemo_gradient``.
+(``k_pde_stream`` / ``k_pde_multi``); with ``--workload adjoint_2d --adjoint 1``
+the run is recorded and followed by one ``chemo_gradient``; ``ensemble_2d``
+runs its replicates as one batched simulation.
 """
 from __future__ import annotations
 
@@ -34,15 +35,22 @@ def main(argv=None):
     a = ap.parse_args(argv)
     if not torch.cuda.is_available():
         raise SystemExit("profile_run needs a CUDA device")
-    p, pos, sp = wl.initial_state(a.workload, n=a.n)
+    dev = torch.device("cuda:0")
+    if wl.WORKLOADS[a.workload].get("replicates"):
+        # an ensemble: all replicates in one batched simulation
+        p, sizes, pos, sp = wl.ensemble_state(a.workload)
+    else:
+        p, pos, sp = wl.initial_state(a.workload, n=a.n)
+        sizes = None
     if a.search_mode is not None:
         p = dict(p, search_mode=a.search_mode)
-    dev = torch.device("cuda:0")
     dpos = torch.from_numpy(pos).to(dev)
     dsp = torch.from_numpy(sp).to(dev)
-    with chemo.chemo_create(p, dpos, dsp) as sim:
+    sim0 = chemo.chemo_create(p, dpos, dsp) if sizes is None else chemo.chemo_create_batch(p, sizes, dpos, dsp)
+    with sim0 as sim:
         if p.get("chem_mode", 0) == 0:
-            chemo.chemo_write_field(sim, torch.zeros(chemo.grid_shape(p), dtype=torch.float32, device=dev))
+            shape = tuple(chemo.grid_shape(p)) if sizes is None else (len(sizes),) + tuple(chemo.grid_shape(p))
+            chemo.chemo_write_field(sim, torch.zeros(shape, dtype=torch.float32, device=dev))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         if a.adjoint:
