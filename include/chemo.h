@@ -110,7 +110,7 @@ typedef struct chemo_params {
                                     substep only) */
     int32_t warp_runs;           /* search_mode 1: a warp whose 32 cells fall in at most
                                     this many bins searches them together, a sparser warp
-                                    searches per lane (0 = 8; 1..32) */
+                                    searches per lane (0 = 12; 1..32) */
     int32_t move_scheme;         /* 0 Euler-Maruyama (Eq. (2)); 1 tamed Euler (Sect. 3.2):
                                     drift increment dt a / (1 + dt |a|), a the whole drift */
     int32_t hard_sphere;         /* 1: after the move, overlapping pairs (closer than
@@ -179,7 +179,7 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
  * `trial_steps` steps (after 4 warm-up steps) of the given (batched) particle
  * set for each candidate: search_mode 1 (3^d bins, side r_c x {1, 1.25, 1.5,
  * 2}), 2 (2^d bins, side 2 r_c x {1, 1.25}) and 3 (3^d per lane, side r_c x
- * {1, 1.5}), then for mode 1 warp_runs {4, 16, 32}, then the PDE overlap on
+ * {1, 1.5}), then for mode 1 warp_runs {4, 8, 32}, then the PDE overlap on
  * and off; the results do not depend on the choice. *best_out receives
  * params with bin_side, search_mode, warp_runs and pde_overlap set to the
  * fastest candidate, *best_ms_out (if non-NULL) its device time per step.

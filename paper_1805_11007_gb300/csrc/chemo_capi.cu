@@ -359,7 +359,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
     kp.bin_slots = slots;
     kp.ngroups = slots / 8;
     kp.search = search;
-    kp.warp_runs = p.warp_runs > 0 ? p.warp_runs : 8;
+    kp.warp_runs = p.warp_runs > 0 ? p.warp_runs : 12;
     return CHEMO_OK;
 }
 
@@ -846,7 +846,7 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
     if (best < 0) return last_err ? last_err : fail(CHEMO_EINVAL, "no admissible candidate");
     chemo_params q = cands[(size_t)best];
     if (q.search_mode == 1) {  // how sparse a warp may be and still search together
-        const int runs[3] = {4, 16, 32};
+        const int runs[3] = {4, 8, 32};
         for (int v : runs) {
             chemo_params c = q;
             c.warp_runs = v;

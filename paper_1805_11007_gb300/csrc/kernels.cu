@@ -81,7 +81,7 @@ struct FAcc {
 #define CHEMO_PAIR_BLOCKS 4
 #endif
 #ifndef CHEMO_LIST_CAP
-#define CHEMO_LIST_CAP 24
+#define CHEMO_LIST_CAP 16
 #endif
 constexpr int LIST_CAP = CHEMO_LIST_CAP;  // flushed once a lane holds more than LIST_CAP - UNROLL
 #ifndef CHEMO_UNROLL
