@@ -100,8 +100,8 @@ typedef struct chemo_params {
     uint64_t seed;               /* Philox4x32-10 key (seed lo, seed hi) */
     int32_t track_displacement;  /* keep the unwrapped displacement (Sect. 4, MSD) */
     float bin_side;              /* cell-list bin side (0 = automatic) */
-    int32_t search_mode;         /* 0 automatic, 1 3^d bins of side >= r_c searched by
-                                    the warp together, 2 2^d bins of side >= 2 r_c,
+    int32_t search_mode;         /* 0 automatic (= 3), 1 3^d bins of side >= r_c searched
+                                    by the warp together, 2 2^d bins of side >= 2 r_c,
                                     3 3^d bins searched by each lane alone (the
                                     results are identical; only the speed differs) */
     int32_t bin_order;           /* 0 or 1: row-major bins, x fastest (2, Z-order: ENOTSUP) */

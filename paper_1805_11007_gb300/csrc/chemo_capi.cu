@@ -293,7 +293,10 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
                 contact = std::max(contact, 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]));
     const double rc = std::max(pairs ? rc_force : 0.0, contact);
     const bool search_on = rc > 0.0;
-    int search = (p.search_mode == 0 || !pairs) ? 1 : p.search_mode;
+    // automatic: the 3^d window searched per lane (fastest on average over the
+    // clump and ensemble workloads; the warp search wins only in the densest
+    // states and is left to the autotuner)
+    int search = !pairs ? 1 : (p.search_mode == 0 ? 3 : p.search_mode);
     kp.pairs = pairs ? 1 : 0;
     double bmin;
     if (search_on) {

@@ -81,11 +81,14 @@ struct FAcc {
 #define CHEMO_PAIR_BLOCKS 4
 #endif
 #ifndef CHEMO_LIST_CAP
-#define CHEMO_LIST_CAP 16
+#define CHEMO_LIST_CAP 24
 #endif
 constexpr int LIST_CAP = CHEMO_LIST_CAP;  // flushed once a lane holds more than LIST_CAP - UNROLL
 #ifndef CHEMO_UNROLL
-#define CHEMO_UNROLL 4
+#define CHEMO_UNROLL 8
+#endif
+#ifndef CHEMO_BATCH_LOADS
+#define CHEMO_BATCH_LOADS 1
 #endif
 constexpr int UNROLL = CHEMO_UNROLL;  // candidates per lane between two warp votes
 
@@ -232,9 +235,31 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
     bool more = q < qe;
     while (__any_sync(0xffffffffu, more)) {
         if (more) {
+            const uint32_t m = min((uint32_t)UNROLL, qe - q);
+#if CHEMO_BATCH_LOADS
+            // a chunk of up to UNROLL candidates from one range, all loaded
+            // before any is tested
+            float4 ob[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if ((uint32_t)u >= m) break;
+                const float4 o = ob[u];
+                const uint32_t qq = q + (uint32_t)u;
+                float dx, dy, dz, r2;
+                pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
+                const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
+                if (r2 < rc2 && r2 > 0.f && qq != self) {
+                    lst[nl++ * 32] = qq;
+                    count += 1;
+                    if (STATS) idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
+                }
+            }
+#else
             // a chunk of up to UNROLL candidates from one range; the next
             // candidate is loaded while the current one is tested
-            const uint32_t m = min((uint32_t)UNROLL, qe - q);
             float4 o = __ldg(&S[q]);
             for (uint32_t u = 0; u < m; ++u) {
                 const uint32_t qq = q + u;
@@ -250,6 +275,7 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                 }
                 o = on;
             }
+#endif
             q += m;
             if (q >= qe) {
                 while (q >= qe && r < nr) {
