@@ -230,12 +230,13 @@ int chemo_record(chemo_sim *sim, int64_t nsteps, int32_t every, void *stream);
  * dL/dinter, dL/dD_0 .. dL/dD_{n_species-1}] and, if dL_dpos0 is non-NULL,
  * dL/dpos of the recorded run's initial state. The noise is frozen (the same
  * Philox counters as the forward run); each segment between checkpoints is
- * re-run forward before its reverse sweep (Sect. 2 model: pair force Jacobian,
+ * re-run forward before its reverse sweep, the re-run of the segment before
+ * it overlapping that sweep on a second stream (Sect. 2 model: pair force Jacobian,
  * interpolation Jacobian, reflection signs, deposit and PDE transposes). The
  * cutoff jump and the reflection kinks are not differentiated (measure-zero
  * events). dL/dinter is 0 when inter = 0 (no pair force, no cell list for
- * its cutoff). Memory: per segment the states, fields, sorted states, cell
- * lists and pair forces of `every` steps. The simulation is left at the
+ * its cutoff). Memory: two segments' states, fields, sorted states, cell
+ * lists and pair forces of `every` steps each. The simulation is left at the
  * final state of the recorded run. Synchronises `stream` when mem_kind is
  * HOST. EINVAL if no run is recorded. */
 int chemo_gradient(chemo_sim *sim, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,

@@ -24,7 +24,9 @@
 // not differentiated.
 //
 // Memory: checkpoints of (X, c) every `every` steps; each segment is re-run
-// forward to store its states before its reverse sweep.
+// forward to store its states before its reverse sweep. The re-run of segment
+// s - 1 (one stream, the simulation's buffers) overlaps the reverse sweep of
+// segment s (a second stream, the tape's buffers), with two segment buffers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,22 +42,32 @@ namespace {
 
 constexpr int ATPB = 128;  // small blocks: the adjoint kernels run over tens of thousands of cells
 
+// States of one segment, stored by its forward re-run for its reverse sweep.
+struct SegBuf {
+    float *pos = nullptr;     // (every + 1) x n x dim, by id
+    float *c = nullptr;       // every x G
+    float4 *S = nullptr;      // sorted state at the start of each step
+    uint32_t *cnt = nullptr;  // its bin counts (packed 16-bit)
+    uint32_t *gst = nullptr;  // its group offsets
+    float *F = nullptr;       // pair force of each step, by id (n x dim)
+};
+
 struct Tape {
     int64_t n = 0, G = 0, nsteps = 0, every = 0, step0 = 0;
     int nseg = 0, dim = 0, ns = 0;
     std::vector<void *> allocs;
     std::vector<float *> ck_pos, ck_c;  // checkpoints: positions by id (n x dim), field
     uint8_t *species = nullptr;         // species by id
-    float *seg_pos = nullptr;           // (every + 1) x n x dim
-    float *seg_c = nullptr;             // every x G
+    // two segment buffers: segment s - 1 is re-run into one while the
+    // reverse sweep of segment s reads the other (two streams)
+    SegBuf sb[2];
+    cudaStream_t s_fwd = nullptr, s_rev = nullptr;
+    cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
+    cudaEvent_t ev_start = nullptr, ev_fwd_end = nullptr, ev_rev_end = nullptr;
     float *lamX[2] = {nullptr, nullptr};  // n x dim by id
     float *lamY = nullptr;              // n x dim by id
     float *lamC[2] = {nullptr, nullptr};  // G
     float *lamS = nullptr;              // G
-    float4 *seg_S = nullptr;            // sorted state at the start of each step of the segment
-    uint32_t *seg_cnt = nullptr;        // its bin counts (packed 16-bit)
-    uint32_t *seg_gst = nullptr;        // its group offsets
-    float *seg_F = nullptr;             // pair force of each step, by id (n x dim)
     size_t cwords = 0, gwords = 0;      // words of one count table / offset table
     float *dpf = nullptr;               // parameter gradient (float) for the caller
     double *dpar = nullptr;             // (2 + MAXS) x pstride per-block partials
@@ -69,7 +81,14 @@ struct chemo_tape : Tape {};
 void chemo_tape_free(chemo_tape *t)
 {
     if (!t) return;
+    if (t->s_fwd) cudaStreamSynchronize(t->s_fwd);
+    if (t->s_rev) cudaStreamSynchronize(t->s_rev);
     for (void *p : t->allocs) cudaFree(p);
+    for (cudaEvent_t e : {t->ev_ready[0], t->ev_ready[1], t->ev_done[0], t->ev_done[1], t->ev_start, t->ev_fwd_end,
+                          t->ev_rev_end})
+        if (e) cudaEventDestroy(e);
+    if (t->s_fwd) cudaStreamDestroy(t->s_fwd);
+    if (t->s_rev) cudaStreamDestroy(t->s_rev);
     delete t;
 }
 
@@ -539,11 +558,35 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     const size_t gb = (size_t)std::max<int64_t>(G, 1) * sizeof(float);
     void *p;
     int r;
-    if (!t->seg_pos) {
-        if ((r = talloc(t, &p, pb * (size_t)(t->every + 1)))) return r;
-        t->seg_pos = (float *)p;
-        if ((r = talloc(t, &p, gb * (size_t)t->every))) return r;
-        t->seg_c = (float *)p;
+    if (!t->sb[0].pos) {
+        const KP &k0 = s->kp;
+        t->cwords = (size_t)k0.bin_slots / 2;
+        t->gwords = ((size_t)k0.ngroups + 1 + 3) & ~(size_t)3;
+        const size_t E = (size_t)t->every;
+        for (int b = 0; b < 2; ++b) {
+            SegBuf &B = t->sb[b];
+            if ((r = talloc(t, &p, pb * (E + 1)))) return r;
+            B.pos = (float *)p;
+            if ((r = talloc(t, &p, gb * E))) return r;
+            B.c = (float *)p;
+            if ((r = talloc(t, &p, E * (size_t)std::max<int64_t>(n, 1) * sizeof(float4)))) return r;
+            B.S = (float4 *)p;
+            if ((r = talloc(t, &p, E * t->cwords * sizeof(uint32_t)))) return r;
+            B.cnt = (uint32_t *)p;
+            if ((r = talloc(t, &p, E * t->gwords * sizeof(uint32_t)))) return r;
+            B.gst = (uint32_t *)p;
+            if ((r = talloc(t, &p, E * pb))) return r;
+            B.F = (float *)p;
+        }
+        ATRY(cudaStreamCreateWithFlags(&t->s_fwd, cudaStreamNonBlocking));
+        ATRY(cudaStreamCreateWithFlags(&t->s_rev, cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b) {
+            ATRY(cudaEventCreateWithFlags(&t->ev_ready[b], cudaEventDisableTiming));
+            ATRY(cudaEventCreateWithFlags(&t->ev_done[b], cudaEventDisableTiming));
+        }
+        ATRY(cudaEventCreateWithFlags(&t->ev_start, cudaEventDisableTiming));
+        ATRY(cudaEventCreateWithFlags(&t->ev_fwd_end, cudaEventDisableTiming));
+        ATRY(cudaEventCreateWithFlags(&t->ev_rev_end, cudaEventDisableTiming));
         for (int k = 0; k < 2; ++k) {
             if ((r = talloc(t, &p, pb))) return r;
             t->lamX[k] = (float *)p;
@@ -554,18 +597,6 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         t->lamY = (float *)p;
         if ((r = talloc(t, &p, gb))) return r;
         t->lamS = (float *)p;
-        const KP &k0 = s->kp;
-        t->cwords = (size_t)k0.bin_slots / 2;
-        t->gwords = ((size_t)k0.ngroups + 1 + 3) & ~(size_t)3;
-        const size_t E = (size_t)t->every;
-        if ((r = talloc(t, &p, E * (size_t)std::max<int64_t>(n, 1) * sizeof(float4)))) return r;
-        t->seg_S = (float4 *)p;
-        if ((r = talloc(t, &p, E * t->cwords * sizeof(uint32_t)))) return r;
-        t->seg_cnt = (uint32_t *)p;
-        if ((r = talloc(t, &p, E * t->gwords * sizeof(uint32_t)))) return r;
-        t->seg_gst = (uint32_t *)p;
-        if ((r = talloc(t, &p, E * pb))) return r;
-        t->seg_F = (float *)p;
         t->pstride = (int64_t)blocks(std::max<int64_t>(n, 1));
         if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS) * (size_t)t->pstride))) return r;
         t->dpar = (double *)p;
@@ -573,51 +604,71 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         t->dpf = (float *)p;
     }
     const cudaMemcpyKind in_kind = mem_kind == CHEMO_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    // two streams after the caller's: re-runs on s_fwd, reverse sweeps on s_rev
+    cudaStream_t sf = t->s_fwd, sr = t->s_rev;
+    ATRY(cudaEventRecord(t->ev_start, st));
+    ATRY(cudaStreamWaitEvent(sf, t->ev_start, 0));
+    ATRY(cudaStreamWaitEvent(sr, t->ev_start, 0));
     int lx = 0, lc = 0;
-    if (n) ATRY(cudaMemcpyAsync(t->lamX[lx], dL_dpos_final, (size_t)n * dim * sizeof(float), in_kind, st));
+    if (n) ATRY(cudaMemcpyAsync(t->lamX[lx], dL_dpos_final, (size_t)n * dim * sizeof(float), in_kind, sr));
     if (G) {
-        if (dL_dc_final) ATRY(cudaMemcpyAsync(t->lamC[lc], dL_dc_final, (size_t)G * sizeof(float), in_kind, st));
-        else ATRY(cudaMemsetAsync(t->lamC[lc], 0, gb, st));
+        if (dL_dc_final) ATRY(cudaMemcpyAsync(t->lamC[lc], dL_dc_final, (size_t)G * sizeof(float), in_kind, sr));
+        else ATRY(cudaMemsetAsync(t->lamC[lc], 0, gb, sr));
     }
-    ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS) * (size_t)t->pstride, st));
+    ATRY(cudaMemsetAsync(t->dpar, 0, sizeof(double) * (2 + MAXS) * (size_t)t->pstride, sr));
     // the pair force is linear in inter: dF/dinter = F / inter (the cell list
     // is not built for the cutoff when inter = 0, and dL/dinter is then 0)
     const float f_unit = s->prm.inter != 0.f ? 1.f / s->prm.inter : 0.f;
     const int64_t end_step = s->step;
+    // restores segment seg's checkpoint and re-runs it on sf, storing its states in B
+    auto rerun = [&](int seg, SegBuf &B) -> int {
+        const int64_t n0 = (int64_t)seg * t->every;
+        const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
+        int rr;
+        if ((rr = eng_ingest(s, t->ck_pos[seg], t->species, nullptr, CHEMO_MEM_DEVICE, sf))) return rr;
+        if (G) ATRY(cudaMemcpyAsync(cur_field(s), t->ck_c[seg], gb, cudaMemcpyDeviceToDevice, sf));
+        if ((rr = chemo_set_step_index(s, t->step0 + n0, sf))) return rr;
+        for (int64_t k = 0; k < len; ++k) {
+            if ((rr = gather(s, B.pos + (size_t)k * n * dim, nullptr, sf))) return rr;
+            if (G) ATRY(cudaMemcpyAsync(B.c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, sf));
+            // the sorted state and its cell list, for the pair term of the reverse sweep
+            const KP v = eng_view(s);
+            const int64_t tot = n + (int64_t)t->cwords + (int64_t)t->gwords;
+            const unsigned nb = (unsigned)std::min<int64_t>((tot + ATPB - 1) / ATPB, 152 * 16);
+            k_snapshot<<<nb, ATPB, 0, sf>>>(v.S, n, v.cnt_cur, (int64_t)t->cwords, v.gstart, (int64_t)t->gwords,
+                                            B.S + (size_t)k * n, B.cnt + (size_t)k * t->cwords,
+                                            B.gst + (size_t)k * t->gwords);
+            ATRY(cudaGetLastError());
+            // the step's pair force, by id (the particle kernel writes every cell's)
+            s->kp.F_save = B.F + (size_t)k * n * dim;
+            rr = eng_enqueue_step(s, sf, nullptr);
+            s->kp.F_save = nullptr;
+            if (rr) return rr;
+        }
+        return gather(s, B.pos + (size_t)len * n * dim, nullptr, sf);
+    };
+    if ((r = rerun(t->nseg - 1, t->sb[(t->nseg - 1) & 1]))) return r;
+    ATRY(cudaEventRecord(t->ev_ready[(t->nseg - 1) & 1], sf));
     for (int seg = t->nseg - 1; seg >= 0; --seg) {
         const int64_t n0 = (int64_t)seg * t->every;
         const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
-        // restore the checkpoint and re-run the segment, storing its states
-        if ((r = eng_ingest(s, t->ck_pos[seg], t->species, nullptr, CHEMO_MEM_DEVICE, st))) return r;
-        if (G) ATRY(cudaMemcpyAsync(cur_field(s), t->ck_c[seg], gb, cudaMemcpyDeviceToDevice, st));
-        if ((r = chemo_set_step_index(s, t->step0 + n0, stream))) return r;
-        for (int64_t k = 0; k < len; ++k) {
-            if ((r = gather(s, t->seg_pos + (size_t)k * n * dim, nullptr, st))) return r;
-            if (G) ATRY(cudaMemcpyAsync(t->seg_c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
-            // the sorted state and its cell list, for the pair term of the reverse sweep
-            const KP v = eng_view(s);
-            {
-                const int64_t tot = n + (int64_t)t->cwords + (int64_t)t->gwords;
-                const unsigned nb = (unsigned)std::min<int64_t>((tot + ATPB - 1) / ATPB, 152 * 16);
-                k_snapshot<<<nb, ATPB, 0, st>>>(v.S, n, v.cnt_cur, (int64_t)t->cwords, v.gstart, (int64_t)t->gwords,
-                                                t->seg_S + (size_t)k * n, t->seg_cnt + (size_t)k * t->cwords,
-                                                t->seg_gst + (size_t)k * t->gwords);
-                ATRY(cudaGetLastError());
-            }
-            // the step's pair force, by id (the particle kernel writes every cell's)
-            s->kp.F_save = t->seg_F + (size_t)k * n * dim;
-            r = eng_enqueue_step(s, st, nullptr);
-            s->kp.F_save = nullptr;
-            if (r) return r;
+        const SegBuf &B = t->sb[seg & 1];
+        if (seg >= 1) {
+            // re-run the previous segment into the other buffer once the reverse
+            // sweep that last read it (segment seg + 1) is done
+            const int ob = (seg - 1) & 1;
+            if (seg + 1 <= t->nseg - 1) ATRY(cudaStreamWaitEvent(sf, t->ev_done[ob], 0));
+            if ((r = rerun(seg - 1, t->sb[ob]))) return r;
+            ATRY(cudaEventRecord(t->ev_ready[ob], sf));
         }
-        if ((r = gather(s, t->seg_pos + (size_t)len * n * dim, nullptr, st))) return r;
-        // reverse sweep over the segment
+        ATRY(cudaStreamWaitEvent(sr, t->ev_ready[seg & 1], 0));
+        // reverse sweep over the segment (stream sr)
         for (int64_t k = len - 1; k >= 0; --k) {
             const unsigned long long step = (unsigned long long)(t->step0 + n0 + k);
-            const float *Xn = t->seg_pos + (size_t)k * n * dim;
-            const float *Xn1 = t->seg_pos + (size_t)(k + 1) * n * dim;
-            const float *cn = G ? t->seg_c + (size_t)k * G : nullptr;
-            KP kp = eng_view(s);
+            const float *Xn = B.pos + (size_t)k * n * dim;
+            const float *Xn1 = B.pos + (size_t)(k + 1) * n * dim;
+            const float *cn = G ? B.c + (size_t)k * G : nullptr;
+            KP kp = eng_view(s);  // constants only: the buffers come from B
             // 1. PDE transpose (substeps), lambda_S
             if (G && kp.pde_multi) {
                 // 2D: the transpose of the mirror-ghost operator is tau L tau^-1, so
@@ -627,48 +678,54 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                 for (int l = 0; l < kp.pde_launches; ++l) {
                     const int nsub = (left + (kp.pde_launches - l) - 1) / (kp.pde_launches - l);
                     ATRY(launch_pde_multi(kp, t->lamC[lc], t->lamC[lc ^ 1], nsub, 0, t->lamS, l == 0,
-                                          1.f / (float)kp.substeps, 1, st));
+                                          1.f / (float)kp.substeps, 1, sr));
                     left -= nsub;
                     lc ^= 1;
                 }
             } else if (G) {
                 const int ss = kp.substeps;
                 for (int m = 0; m < ss; ++m) {
-                    k_adj_pde<<<blocks(G), ATPB, 0, st>>>(kp, t->lamC[lc], t->lamC[lc ^ 1], t->lamS, 1.f / ss, m == 0);
+                    k_adj_pde<<<blocks(G), ATPB, 0, sr>>>(kp, t->lamC[lc], t->lamC[lc ^ 1], t->lamS, 1.f / ss, m == 0);
                     ATRY(cudaGetLastError());
                     lc ^= 1;
                 }
             }
             // the cell list of X^n and its pair force, saved by the re-run
-            kp.S = t->seg_S + (size_t)k * n;
-            kp.cnt_cur = t->seg_cnt + (size_t)k * t->cwords;
-            kp.gstart = t->seg_gst + (size_t)k * t->gwords;
-            const float *Fk = t->seg_F + (size_t)k * n * dim;
+            kp.S = B.S + (size_t)k * n;
+            kp.cnt_cur = B.cnt + (size_t)k * t->cwords;
+            kp.gstart = B.gst + (size_t)k * t->gwords;
+            const float *Fk = B.F + (size_t)k * n * dim;
             // 2-5. per-cell terms, then the pair term
             if (n) {
                 if (dim == 2)
-                    k_adj_cells<2><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
+                    k_adj_cells<2><<<blocks(n), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
                                                              t->pstride, G ? 1 : 0, kp.pde_multi);
                 else
-                    k_adj_cells<3><<<blocks(n), ATPB, 0, st>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
+                    k_adj_cells<3><<<blocks(n), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
                                                              t->pstride, G ? 1 : 0, kp.pde_multi);
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
                     if (dim == 2) {
-                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     } else {
-                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, st>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     }
                     ATRY(cudaGetLastError());
                 }
             }
             lx ^= 1;
         }
+        ATRY(cudaEventRecord(t->ev_done[seg & 1], sr));
     }
+    // join both streams back into the caller's
+    ATRY(cudaEventRecord(t->ev_fwd_end, sf));
+    ATRY(cudaEventRecord(t->ev_rev_end, sr));
+    ATRY(cudaStreamWaitEvent(st, t->ev_fwd_end, 0));
+    ATRY(cudaStreamWaitEvent(st, t->ev_rev_end, 0));
     // outputs
     const int np = 2 + t->ns;
     float *dpf = t->dpf;

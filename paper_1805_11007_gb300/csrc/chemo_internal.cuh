@@ -310,7 +310,10 @@ cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches);
 cudaError_t launch_scatter(const KP &kp, int cur, int advance_step, cudaStream_t st, int *launches);
 cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches);
 // Substeps per launch of the temporal-blocked 2D PDE kernel (its halo width).
-constexpr int PDE_MULTI_MAX = 12;
+#ifndef CHEMO_PDE_MULTI_MAX
+#define CHEMO_PDE_MULTI_MAX 12
+#endif
+constexpr int PDE_MULTI_MAX = CHEMO_PDE_MULTI_MAX;
 // Runs `nsub` substeps of the 2D PDE in one launch from cin to cout (c grids
 // of kp); use_src adds the source / consumption grids; avg (nullable)
 // receives (avg_first) or accumulates avg_scale times the sum of the
