@@ -94,7 +94,7 @@ FP32_LANES = 152 * 128
 
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
 # traffic field; None where the kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": 61.91e6, "k_pde": 93.35e6, "k_scan": 34.70e6, "k_scatter": 45.09e6}
+NCU_TRAFFIC_BYTES = {"k_step": 61.85e6, "k_pde": 94.10e6, "k_scan": 34.88e6, "k_scatter": 45.06e6}
 
 
 # ---------------------------------------------------------------------------
