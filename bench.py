@@ -84,17 +84,20 @@ def measured_peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# FP32 operations of one in-cutoff pair interaction (Sect. 3.2 force): the
-# difference vector (3), r^2 (5), rsqrt, r, -r/eps, exp, minus the shift,
-# times inter/eps, times 1/r, the fixed-point scale, and the three components
-# (3): 20 operations, an FMA counted as 2.
-FLOP_PER_PAIR = 20.0
+# FP32 operations of one in-cutoff pair (Sect. 3.2 force), evaluated once per
+# unordered pair (Newton's third law): the difference vector (3), r^2 (5),
+# rsqrt, r, -r/eps, exp, minus the shift, times inter/eps, times 1/r, the
+# fixed-point scale and the three components (3): 20 operations, an FMA
+# counted as 2; plus d additions of the negated term to the partner.
+def flop_per_pair(dim: int) -> float:
+    return 20.0 + dim
 # FP32 lanes of GB300: 152 SMs x 128 lanes, an FMA (2 flop) per lane per cycle.
 FP32_LANES = 152 * 128
 
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
-# traffic field; None where the kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": 61.85e6, "k_pde": 94.10e6, "k_scan": 34.88e6, "k_scatter": 45.06e6}
+# traffic field ("k_step": the particle kernels of one step together); None
+# where a kernel changed after the capture.
+NCU_TRAFFIC_BYTES = {"k_step": None, "k_pde": 94.10e6, "k_scan": 34.88e6, "k_scatter": None}
 
 
 # ---------------------------------------------------------------------------
@@ -512,9 +515,13 @@ def main():
     kern = {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter")}
     dom = max(kern, key=kern.get)
     if dom == "k_step":
-        # the particle kernel is bound by the pair arithmetic, not by HBM
-        achieved = FLOP_PER_PAIR * pairs_per_step / (kern[dom] * 1e-3) / 1e12
-        roofline = {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+        # the particle kernels are bound by the pair search, not by HBM; the
+        # algorithmic work is each unordered in-cutoff pair once (pairs_per_step
+        # counts every pair for both of its cells)
+        achieved = flop_per_pair(p["dim"]) * 0.5 * pairs_per_step / (kern[dom] * 1e-3) / 1e12
+        half = info["search_mode"] == 4
+        roofline = {"kernel": "k_pairs_half + k_step" if half else dom, "bound": "alu", "achieved": achieved,
+                    "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": achieved / fp32_peak,
                     "peak_source": "FP32 lanes x 2 x SM max clock (%d x 2 x %.0f MHz)" % (FP32_LANES, sm_mhz)}
     else:

@@ -100,10 +100,13 @@ typedef struct chemo_params {
     uint64_t seed;               /* Philox4x32-10 key (seed lo, seed hi) */
     int32_t track_displacement;  /* keep the unwrapped displacement (Sect. 4, MSD) */
     float bin_side;              /* cell-list bin side (0 = automatic) */
-    int32_t search_mode;         /* 0 automatic (= 3), 1 3^d bins of side >= r_c searched
+    int32_t search_mode;         /* 0 automatic (= 4), 1 3^d bins of side >= r_c searched
                                     by the warp together, 2 2^d bins of side >= 2 r_c,
-                                    3 3^d bins searched by each lane alone (the
-                                    results are identical; only the speed differs) */
+                                    3 3^d bins searched by each lane alone, 4 the upper
+                                    half of the 3^d window per lane, each pair once and
+                                    its term added to both cells (exact integer sums; an
+                                    extra launch and 8 bytes per cell and axis). The
+                                    results are identical; only the speed differs */
     int32_t bin_order;           /* 0 or 1: row-major bins, x fastest (2, Z-order: ENOTSUP) */
     int32_t pde_overlap;         /* 0 automatic, 1 run the PDE after the particle kernels,
                                     2 run it concurrently with the particle kernel (one
@@ -127,7 +130,7 @@ typedef struct chemo_params {
 typedef struct chemo_info {
     int64_t n;                   /* particles */
     int32_t dim;
-    int32_t search_mode;         /* 1, 2 or 3, as resolved */
+    int32_t search_mode;         /* 1, 2, 3 or 4, as resolved */
     int32_t nbins[3];            /* bins per axis */
     int64_t bin_slots;           /* entries of the bin table: pitch * nbins[1] * nbins[2] */
     float bin_side[3];
@@ -178,8 +181,9 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
  * paper, which leaves the bin size to the user, Sect. 3.1). Times
  * `trial_steps` steps (after 4 warm-up steps) of the given (batched) particle
  * set for each candidate: search_mode 1 (3^d bins, side r_c x {1, 1.25, 1.5,
- * 2}), 2 (2^d bins, side 2 r_c x {1, 1.25}) and 3 (3^d per lane, side r_c x
- * {1, 1.5}), then for mode 1 warp_runs {4, 8, 32}, then the PDE overlap on
+ * 2}), 2 (2^d bins, side 2 r_c x {1, 1.25}), 3 (3^d per lane, side r_c x
+ * {1, 1.5}) and 4 (half window, side r_c x {1, 1.25, 1.5}), then for mode 1
+ * warp_runs {4, 8, 32}, then the PDE overlap on
  * and off; the results do not depend on the choice. *best_out receives
  * params with bin_side, search_mode, warp_runs and pde_overlap set to the
  * fastest candidate, *best_ms_out (if non-NULL) its device time per step.

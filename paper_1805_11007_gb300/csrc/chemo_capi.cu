@@ -133,7 +133,7 @@ int check_params(const chemo_params &p)
     if (p.cutoff_mode != 0 && p.cutoff_mode != 1) return fail(CHEMO_EINVAL, "cutoff_mode must be 0 or 1");
     if (!(p.cutoff_factor >= 0.f)) return fail(CHEMO_EINVAL, "cutoff_factor must be >= 0");
     if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
-    if (p.search_mode < 0 || p.search_mode > 3) return fail(CHEMO_EINVAL, "search_mode must be 0, 1, 2 or 3");
+    if (p.search_mode < 0 || p.search_mode > 4) return fail(CHEMO_EINVAL, "search_mode must be 0, 1, 2, 3 or 4");
     if (p.warp_runs < 0 || p.warp_runs > 32) return fail(CHEMO_EINVAL, "warp_runs must be 0..32");
     if (p.move_scheme != 0 && p.move_scheme != 1) return fail(CHEMO_EINVAL, "move_scheme must be 0 or 1");
     if (p.hard_sphere != 0 && p.hard_sphere != 1) return fail(CHEMO_EINVAL, "hard_sphere must be 0 or 1");
@@ -293,10 +293,10 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
                 contact = std::max(contact, 0.5 * ((double)p.diameter[s] + (double)p.diameter[t]));
     const double rc = std::max(pairs ? rc_force : 0.0, contact);
     const bool search_on = rc > 0.0;
-    // automatic: the 3^d window searched per lane (fastest on average over the
-    // clump and ensemble workloads; the warp search wins only in the densest
-    // states and is left to the autotuner)
-    int search = !pairs ? 1 : (p.search_mode == 0 ? 3 : p.search_mode);
+    // automatic: the upper half of the 3^d window searched per lane, each pair
+    // once (fastest on the clump, walls and ensemble workloads; the warp search
+    // wins only in the densest states and is left to the autotuner)
+    int search = !pairs ? 1 : (p.search_mode == 0 ? 4 : p.search_mode);
     kp.pairs = pairs ? 1 : 0;
     double bmin;
     if (search_on) {
@@ -704,6 +704,15 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
     ALLOC(kp.S, N * sizeof(float4));
     ALLOC(kp.U, N * sizeof(float4));
     ALLOC(kp.slot, N * sizeof(uint32_t));
+    kp.Fh = nullptr;
+    if (kp.pairs && kp.search == 4) {  // half-window force sums, cleared by each step's particle kernel
+        const size_t fb = N * (size_t)(kp.dim == 3 ? 4 : 2) * sizeof(long long);
+        ALLOC(kp.Fh, fb);
+        if (cudaMemsetAsync(kp.Fh, 0, fb, st) != cudaSuccess) {
+            chemo_destroy(s);
+            return fail(CHEMO_ECUDA, "create: clearing the force sums failed");
+        }
+    }
     kp.dS = kp.dU = nullptr;
     if (params->track_displacement) {
         ALLOC(kp.dS, N * sizeof(float4));
@@ -767,7 +776,7 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
         return r;
     }
     // launches per step: particles, scan, scatter, and the PDE substeps
-    s->launches_per_step = (n > 0 ? 1 : 0) + 2 + (kp.has_grid ? kp.pde_launches : 0) +
+    s->launches_per_step = (n > 0 ? (kp.pairs && kp.search == 4 ? 2 : 1) : 0) + 2 + (kp.has_grid ? kp.pde_launches : 0) +
                            (kp.hard_sphere ? (n > 0 ? 3 : 2) : 0) + (kp.kde && kp.has_grid ? 1 : 0);
     *out = s;
     return CHEMO_OK;
@@ -814,10 +823,11 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
     const double rc = max_cutoff(*params);
     std::vector<chemo_params> cands;
     if (rc > 0.0 && params->inter != 0.f) {
-        // bin side factors of each search mode (1: 3^d warp, 2: 2^d, 3: 3^d per lane)
-        const double fac[3][4] = {{1.0, 1.25, 1.5, 2.0}, {1.0, 1.25, 0.0, 0.0}, {1.0, 1.5, 0.0, 0.0}};
-        const int nf[3] = {4, 2, 2};
-        for (int mode = 1; mode <= 3; ++mode) {
+        // bin side factors of each search mode (1: 3^d warp, 2: 2^d, 3: 3^d per
+        // lane, 4: half of the 3^d window per lane)
+        const double fac[4][4] = {{1.0, 1.25, 1.5, 2.0}, {1.0, 1.25, 0.0, 0.0}, {1.0, 1.5, 0.0, 0.0}, {1.0, 1.25, 1.5, 0.0}};
+        const int nf[4] = {4, 2, 2, 3};
+        for (int mode = 1; mode <= 4; ++mode) {
             const double bmin = (mode == 2 ? 2.0 : 1.0) * rc * (1.0 + 1.0 / 4096.0);
             for (int k = 0; k < nf[mode - 1]; ++k) {
                 chemo_params q = *params;

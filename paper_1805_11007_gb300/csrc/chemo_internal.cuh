@@ -30,7 +30,8 @@ constexpr uint32_t TAG_REACT = 2u;
 struct KP {
     // particles and cell list
     int64_t n;
-    int dim, periodic, search;  // search 1: 3^d bins >= r_c (warp), 2: 2^d bins >= 2 r_c, 3: 3^d (per lane)
+    int dim, periodic, search;  // search 1: 3^d bins >= r_c (warp), 2: 2^d bins >= 2 r_c, 3: 3^d (per lane),
+                                // 4: upper half of the 3^d window (per lane, each pair once)
     int warp_runs;              // search 1: warps with at most this many bins search together
     int pairs;                  // 0: no pair interaction (inter = 0 or zero range)
     float lo[3], hi[3], L[3], halfL[3];
@@ -117,6 +118,14 @@ struct KP {
     unsigned long long *step;    // absolute index of the step being computed
     unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
     float *F_save;               // non-NULL: the particle kernel stores each cell's pair force (by id)
+    long long *Fh;               // search mode 4 (set iff pairs and mode 4): pair-force sums in fixed
+                                 // point, FhStride per sorted cell; NULL = the full-window search
+};
+
+// stride of the half-window force sums (x, y[, z] and padding to 16 bytes)
+template <int DIM>
+struct FhStride {
+    static constexpr int value = DIM == 3 ? 4 : 2;
 };
 
 // ---------------------------------------------------------------------------

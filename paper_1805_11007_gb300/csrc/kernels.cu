@@ -586,6 +586,187 @@ constexpr size_t pair_smem()
 // differences at the nodes, mirror ghosts at walls, then multilinear
 // interpolation, Sect. 3.6). Also returns the interpolated c.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Half-window search (search mode 4). Every unordered pair is found once, by
+// the cell whose window holds the other in its upper half: the rows at
+// (dz, dy) > (0, 0) in lexicographic order with all their bins, and in its own
+// row the next bin and the cells of its own bin that follow it in the sorted
+// array (3D: 4 rows and a part of the own row, against 9 rows; 2D: 1 row and a
+// part, against 3). Each term is added to the finder and, negated, to the
+// partner with a 64-bit integer atomic. The quantised term is odd in the
+// difference vector (negated differences give the same distance, and
+// round-to-nearest-even is odd), and integer sums do not depend on the order
+// of the additions, so each cell's force is the full window's bit for bit.
+// Needs at least 3 bins on a periodic axis (then the 3^d offsets are distinct
+// bins and each pair of bins is visited from one side only).
+// ---------------------------------------------------------------------------
+template <int DIM, bool PERIODIC>
+__device__ __forceinline__ void flush_half(const KP &kp, const SmemTables &t, const uint32_t *lst, int nl, float4 me,
+                                           int row, FAcc &F)
+{
+    constexpr int FS = FhStride<DIM>::value;
+    const int m = __reduce_max_sync(0xffffffffu, nl);
+    int ax = 0, ay = 0, az = 0;
+    for (int i = 0; i < m; ++i) {
+        if (i < nl) {
+            const uint32_t qq = lst[i * 32];
+            const float4 o = __ldg(&kp.S[qq]);
+            float dx, dy, dz, r2;
+            pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+            const int st = row + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+            const float rinv = rsqrtf(r2);
+            const float r = r2 * rinv;
+            const float f = t.amp_f[st] * (__expf(-r * t.inv_eps[st]) - t.shift[st]);
+            const float sq = (f * rinv) * kp.fq_inv;
+            const int tx = __float2int_rn(sq * dx), ty = __float2int_rn(sq * dy);
+            ax += tx;
+            ay += ty;
+            unsigned long long *pf = reinterpret_cast<unsigned long long *>(kp.Fh) + (size_t)qq * FS;
+            atomicAdd(pf + 0, (unsigned long long)(long long)(-tx));
+            atomicAdd(pf + 1, (unsigned long long)(long long)(-ty));
+            if (DIM == 3) {
+                const int tz = __float2int_rn(sq * dz);
+                az += tz;
+                atomicAdd(pf + 2, (unsigned long long)(long long)(-tz));
+            }
+        }
+    }
+    F.x += ax;
+    F.y += ay;
+    F.z += az;
+}
+
+template <int DIM, bool PERIODIC>
+__global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
+    load_tables(kp, t);
+    __syncthreads();
+    constexpr int FS = FhStride<DIM>::value;
+    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const bool valid = j < kp.n;
+    const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int sp = (int)(__float_as_uint(me.w) >> SP_SHIFT);
+    const int lane = threadIdx.x & 31;
+    unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, false>();
+    uint2 *rng = reinterpret_cast<uint2 *>(wbuf) + lane;
+    uint32_t *lst = reinterpret_cast<uint32_t *>(wbuf + (size_t)32 * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) + lane;
+    const uint32_t *__restrict__ cnt = kp.cnt_cur;
+    const uint32_t *__restrict__ gst = kp.gstart;
+    const uint32_t n = (uint32_t)kp.n;
+    const float rs2 = kp.rsp2[sp];
+    int nr = 0;
+    if (valid) {
+        int c[3] = {0, 0, 0};
+        float f[3] = {0.f, 0.f, 0.f};
+        const float pc[3] = {me.x, me.y, me.z};
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+            c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+            f[a] = fminf(fmaxf(__fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a], 0.f), 1.f);
+        }
+        if (DIM == 2) c[2] = layer_of(kp, me);  // rows of the particle's own layer
+        // rows (oy, oz) of the upper half: the own row (0, 0), then (1, 0),
+        // then (-1..1, 1) in 3D
+        constexpr int NROWS = DIM == 3 ? 5 : 2;
+        for (int k = 0; k < NROWS; ++k) {
+            const int oy = k == 0 ? 0 : (k == 1 ? 1 : k - 3);
+            const int oz = k < 2 ? 0 : 1;
+            int y = c[1] + oy, z = c[2] + oz;
+            if (PERIODIC) {
+                y = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+                if (DIM == 3) z = z >= kp.nb[2] ? z - kp.nb[2] : z;
+            } else if (y < 0 || y >= kp.nb[1] || (DIM == 3 && z >= kp.nb[2])) {
+                continue;
+            }
+            const float gyz = (DIM == 3 ? gap2(oz, f[2], kp.bside[2]) : 0.f) + gap2(oy, f[1], kp.bside[1]);
+            if (gyz >= rs2) continue;  // the whole row is out of reach
+            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)y + (uint32_t)kp.nb[1] * (uint32_t)z);
+            int x0 = k == 0 ? c[0] : c[0] - 1, x1 = c[0] + 1;
+            if (!PERIODIC) {
+                x0 = max(x0, 0);
+                x1 = min(x1, kp.nb[0] - 1);
+            }
+            if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
+            if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
+            if (PERIODIC && x0 < 0) {
+                const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
+                rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
+                x0 = 0;
+            }
+            if (PERIODIC && x1 >= kp.nb[0]) {
+                rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
+                x1 = kp.nb[0] - 1;
+            }
+            if (x0 <= x1) {
+                // the own row starts after this cell: the cells of its bin
+                // before it found the pair themselves
+                const uint32_t b0 = k == 0 ? (uint32_t)j + 1u : bin_start(cnt, gst, rowk + x0);
+                rng[nr++ * 32] = make_uint2(b0, bin_start(cnt, gst, rowk + x1 + 1));
+            }
+        }
+    }
+    const float4 *__restrict__ S = kp.S;
+    const int row = sp * MAXS;
+    const bool two = kp.ns <= 2;
+    const float rc2_0 = t.rc2[row], rc2_1 = t.rc2[row + 1];
+    FAcc F = {0ll, 0ll, 0ll};
+    int count = 0, nl = 0, r = 0;
+    uint32_t q = 0, qe = 0;
+    while (q >= qe && r < nr) {
+        const uint2 g = rng[r++ * 32];
+        q = g.x;
+        qe = min(g.y, n);  // offsets are trusted only up to n
+    }
+    bool more = q < qe;
+    while (__any_sync(0xffffffffu, more)) {
+        if (more) {
+            const uint32_t m = min((uint32_t)UNROLL, qe - q);
+            float4 ob[UNROLL];
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < UNROLL; ++u) {
+                if ((uint32_t)u >= m) break;
+                const float4 o = ob[u];
+                float dx, dy, dz, r2;
+                pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+                const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
+                const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
+                if (r2 < rc2 && r2 > 0.f) {
+                    lst[nl++ * 32] = q + (uint32_t)u;
+                    count += 1;
+                }
+            }
+            q += m;
+            if (q >= qe) {
+                while (q >= qe && r < nr) {
+                    const uint2 g = rng[r++ * 32];
+                    q = g.x;
+                    qe = min(g.y, n);
+                }
+                more = q < qe;
+            }
+        }
+        if (__any_sync(0xffffffffu, nl > LIST_CAP - UNROLL)) {
+            flush_half<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
+            nl = 0;
+        }
+    }
+    flush_half<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
+    if (kp.pair_count) {  // profiling only: each pair found here is an in-cutoff pair of both cells
+        const int wsum = __reduce_add_sync(0xffffffffu, count);
+        if (lane == 0 && wsum) atomicAdd(kp.pair_count, 2ull * (unsigned long long)wsum);
+    }
+    if (valid && (F.x | F.y | F.z)) {
+        unsigned long long *pf = reinterpret_cast<unsigned long long *>(kp.Fh) + (size_t)j * FS;
+        atomicAdd(pf + 0, (unsigned long long)F.x);
+        atomicAdd(pf + 1, (unsigned long long)F.y);
+        if (DIM == 3) atomicAdd(pf + 2, (unsigned long long)F.z);
+    }
+}
+
 template <int DIM>
 __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restrict__ c, float4 p, float &cval)
 {
@@ -706,14 +887,23 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
     int npairs = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs) {  // warp-synchronous: every lane takes part
+    if (kp.pairs && kp.Fh) {
+        // summed by the half-window kernel (the scatter clears them for the next step)
+        if (valid) {
+            constexpr int FS = FhStride<DIM>::value;
+            const longlong2 a = reinterpret_cast<const longlong2 *>(kp.Fh + (size_t)j * FS)[0];
+            const long long az = DIM == 3 ? kp.Fh[(size_t)j * FS + 2] : 0ll;
+            F = make_float3(__ll2float_rn(a.x) * kp.fq, __ll2float_rn(a.y) * kp.fq,
+                            DIM == 3 ? __ll2float_rn(az) * kp.fq : 0.f);
+        }
+    } else if (kp.pairs) {  // warp-synchronous: every lane takes part
         unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, WARP>();
         if (WARP)
             F = pair_force_warp<DIM, PERIODIC, false>(kp, t, wbuf, (uint32_t)j, me, sp, valid, npairs, ids_unused);
         else
             F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused, wbuf);
     }
-    if (kp.pair_count) {  // profiling only: in-cutoff pairs of this step
+    if (kp.pair_count && !kp.Fh) {  // profiling only: in-cutoff pairs of this step
         const int wsum = __reduce_add_sync(0xffffffffu, npairs);
         if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
     }
@@ -1064,6 +1254,14 @@ __global__ void __launch_bounds__(TPB) k_scatter(KP kp, int cur, int advance)
     }
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (j >= kp.n) return;
+    if (kp.Fh) {
+        // half-window force sums, read by the particle kernel: cleared here for
+        // the next step (a kernel that stores them without loading them first;
+        // clearing right after the load in the particle kernel stalled it)
+        longlong2 *pf = reinterpret_cast<longlong2 *>(kp.Fh + (size_t)j * FhStride<DIM>::value);
+        pf[0] = make_longlong2(0ll, 0ll);
+        if (DIM == 3) pf[1] = make_longlong2(0ll, 0ll);
+    }
     const float4 u = kp.U[j];
     const uint32_t dst = bin_start(kp.cnt_nxt, kp.gstart, key_of(kp, u)) + kp.slot[j];
     if ((int64_t)dst >= kp.n) {
@@ -1683,6 +1881,23 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_stage_forces(KP kp, 
     if (idsum) idsum[id] = ids;
 }
 
+// The half-window kernel's force sums by id (search mode 4), cleared after
+// (a test entry point: the step clears them in the scatter).
+template <int DIM>
+__global__ void k_stage_take_half(KP kp, float *__restrict__ F_out)
+{
+    constexpr int FS = FhStride<DIM>::value;
+    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (j >= kp.n) return;
+    const int64_t id = gid_of(kp, kp.S[j]);
+    long long *pf = kp.Fh + (size_t)j * FS;
+    for (int a = 0; a < DIM; ++a) {
+        const long long v = pf[a];
+        pf[a] = 0ll;
+        if (id < kp.n) F_out[id * DIM + a] = __ll2float_rn(v) * kp.fq;
+    }
+}
+
 template <int DIM>
 __global__ void k_stage_drift(KP kp, int cur, float *__restrict__ out)
 {
@@ -1762,6 +1977,10 @@ static void pair_kernel_attributes()
     if (done) return;
     pair_kernel_attributes_of<false>();
     pair_kernel_attributes_of<true>();
+    allow_smem(k_pairs_half<2, false>, pair_smem<2, false, false>());
+    allow_smem(k_pairs_half<2, true>, pair_smem<2, true, false>());
+    allow_smem(k_pairs_half<3, false>, pair_smem<3, false, false>());
+    allow_smem(k_pairs_half<3, true>, pair_smem<3, true, false>());
     done = true;
 }
 
@@ -1769,13 +1988,17 @@ static void pair_kernel_attributes()
 template <int DIM, bool PERIODIC, bool W>
 static void step_launch(const KP &kp, int cur, cudaStream_t st)
 {
-    k_step<DIM, PERIODIC, W><<<(unsigned)((kp.n + TPB - 1) / TPB), TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
+    const unsigned nb = (unsigned)((kp.n + TPB - 1) / TPB);
+    if (kp.pairs && kp.Fh)
+        k_pairs_half<DIM, PERIODIC><<<nb, TPB, pair_smem<DIM, PERIODIC, false>(), st>>>(kp);
+    k_step<DIM, PERIODIC, W><<<nb, TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
 }
 
 cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
     if (kp.n == 0) return cudaSuccess;
     pair_kernel_attributes();
+    if (launches && kp.pairs && kp.Fh) ++*launches;
     const bool w = kp.search == 1;
     if (kp.dim == 2) {
         if (kp.periodic) w ? step_launch<2, true, true>(kp, cur, st) : step_launch<2, true, false>(kp, cur, st);
@@ -1948,6 +2171,16 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
         else w ? STAGE_F(3, false, true) : STAGE_F(3, false, false);
     }
 #undef STAGE_F
+    if (kp.pairs && kp.Fh) {
+        // the forces of the half-window kernel replace the full window's
+        // (the counts and id sums stay the full window's)
+#define HALF_F(D, P) k_pairs_half<D, P><<<nb, TPB, pair_smem<D, P, false>(), st>>>(kp)
+        if (kp.dim == 2) kp.periodic ? HALF_F(2, true) : HALF_F(2, false);
+        else kp.periodic ? HALF_F(3, true) : HALF_F(3, false);
+#undef HALF_F
+        if (kp.dim == 2) k_stage_take_half<2><<<nb, TPB, 0, st>>>(kp, F);
+        else k_stage_take_half<3><<<nb, TPB, 0, st>>>(kp, F);
+    }
     return cudaGetLastError();
 }
 

@@ -90,6 +90,10 @@ extern "C" int chemo_forces_noalloc(const chemo_params *params, int64_t n, const
                                                  "(box too large for the cutoff); use chemo_create instead");
     if (n == 0) return CHEMO_OK;
     if (!pos || !species || !F_out) return chemo_internal_fail(CHEMO_EINVAL, "pos, species and F_out are required");
+    // the half window needs a buffer of force sums: the full 3^d window per
+    // lane gives the same forces bit for bit
+    if (kp.search == 4) kp.search = 3;
+    kp.Fh = nullptr;
     void *base = nullptr;
     if (int r = scratch_address(&base)) return r;
     unsigned char *b = static_cast<unsigned char *>(base);

@@ -12,7 +12,8 @@ Parameter dicts use the model's parameter names (the C-ABI field names):
     chi, inter, cutoff_factor, cutoff_mode, chem_mode (0 grid, 1 fixed
     gradient), fixed_grad, grid, Dc, gamma, pde_bc (0 Neumann, 1 Dirichlet,
     2 periodic), pde_substeps (0 auto), dt, seed, track_displacement,
-    bin_side (0 auto), search_mode (0 auto, 1 3^d, 2 2^d).
+    bin_side (0 auto), search_mode (0 auto, 1 3^d warp, 2 2^d, 3 3^d per lane,
+    4 half of the 3^d window).
 
 Workloads (the paper's Fig. 1-3 model with the sizes of the GPU benchmarks):
 

@@ -161,7 +161,7 @@ def test_autotune_choice_leaves_particles_unchanged():
     p, s, pos, sp, c0 = _ens([3000, 5000, 800], **DENSE)
     best, ms = chemo.chemo_autotune(p, s, pos, sp, trial_steps=3)
     assert ms > 0.0
-    assert best["search_mode"] in (1, 2, 3)
+    assert best["search_mode"] in (1, 2, 3, 4)
     out = []
     for q in (p, best):
         with _batch(q, s, pos, sp, c0) as sim:

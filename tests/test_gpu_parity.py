@@ -179,6 +179,10 @@ STEP_CASES = [
     ("clumps_grid_3d", dict(grid=[40, 44, 36], diameter=[0.01, 0.02], search_mode=2), 60013, 5),
     # large steps that reflect more than once
     ("walls_grid_2d", dict(grid=[64, 64, 1], D=[3000.0, 2000.0], dt=1e-4), 5003, 0),
+    # half-window pair search (each pair once, integer atomics for the partner)
+    ("walls_grid_2d", dict(grid=[128, 128, 1], search_mode=4), 20011, 2),
+    ("walls_grid_2d", dict(grid=[96, 80, 1], boundary=1, pde_bc=2, diameter=[0.004, 0.008], search_mode=4), 12007, 0),
+    ("clumps_grid_3d", dict(grid=[48, 48, 48], diameter=[0.01, 0.02], search_mode=4), 60013, 0),
 ]
 
 
@@ -375,13 +379,14 @@ def test_set_params_changes_model_constants():
     ("clumps_grid_3d", dict(grid=[32, 32, 32], boundary=1, pde_bc=2)),
 ])
 def test_warp_and_lane_search_agree_bitwise(name, over):
-    """The warp-cooperative 3^d search and the per-lane 2^d search round
-    every pair term the same way and sum exactly: identical forces, counts
-    and neighbour id sums."""
+    """The warp-cooperative 3^d search, the per-lane 2^d and 3^d searches and
+    the half window (each pair once, the partner's share by integer atomics)
+    round every pair term the same way and sum exactly: identical forces,
+    counts and neighbour id sums."""
     p, pos, sp = wl.initial_state(name, n=30011, **over)
     outs = []
-    # 2^d per lane; 3^d warp search always; 3^d hybrid (default); 3^d per lane
-    for mode, runs in ((2, 0), (1, 32), (1, 0), (3, 0)):
+    # 2^d per lane; 3^d warp search always; 3^d hybrid; 3^d per lane; half window
+    for mode, runs in ((2, 0), (1, 32), (1, 0), (3, 0), (4, 0)):
         with make_sim(dict(p, search_mode=mode, warp_runs=runs), pos, sp) as sim:
             assert chemo.chemo_get_info(sim)["search_mode"] == mode
             outs.append(gpu_forces(sim))
@@ -400,9 +405,60 @@ def test_warp_search_dense_cluster_bitwise():
     pos = (0.5 + 0.004 * rng.standard_normal((4000, 2))).astype(np.float32)
     sp = wl.half_species(4000, 2)
     outs = []
-    for mode, runs in ((3, 0), (1, 32)):
+    for mode, runs in ((3, 0), (1, 32), (4, 0)):
         with make_sim(dict(p, search_mode=mode, warp_runs=runs), pos, sp) as sim:
             outs.append(gpu_forces(sim))
     for a, b in zip(outs[0], outs[1]):
         np.testing.assert_array_equal(a, b)
     assert_forces_match(p, outs[1][0], outs[1][1], outs[1][2], pos, sp)
+
+
+@pytest.mark.parametrize("name,over", [
+    ("walls_grid_2d", dict(grid=[64, 64, 1])),
+    ("walls_grid_2d", dict(boundary=1, pde_bc=2, grid=[64, 64, 1])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32], diameter=[0.01, 0.02])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32], diameter=[0.01, 0.03], boundary=1, pde_bc=2)),
+])
+def test_half_window_step_bitwise(name, over):
+    """A whole step with the half window equals the per-lane 3^d search's bit
+    for bit (the forces are the same integers); the partner sums are cleared
+    by the step, so a second step agrees too."""
+    p, pos, sp = wl.initial_state(name, n=30011, **over)
+    c0 = wl.random_field(p, seed=3, scale=0.3) if p["chem_mode"] == 0 else None
+    outs = []
+    for mode in (3, 4):
+        with make_sim(dict(p, search_mode=mode), pos, sp, c0) as sim:
+            info = chemo.chemo_get_info(sim)
+            assert info["search_mode"] == mode
+            chemo.chemo_step(sim)
+            outs.append(chemo.read_state_host(sim)[0])
+            chemo.chemo_step(sim)
+            chemo.chemo_check(sim)
+            outs.append(chemo.read_state_host(sim)[0])
+    np.testing.assert_array_equal(outs[0], outs[2])
+    assert np.abs(outs[1] - outs[3]).max() <= 1e-6  # the deposit's float atomics round in any order
+
+
+def test_half_window_many_steps_fixed_gradient_bitwise():
+    """No chemical field (fixed gradient): every step is exact integer force
+    sums and counter-based noise, so 37 graph-replayed steps of the half
+    window repeat the per-lane search bit for bit, and a dense cluster of
+    thousands of cells in a few bins (long lists, many atomics on the same
+    partners) gives the same force as the per-lane search."""
+    p, pos, sp = wl.initial_state("periodic_fixed_gradient_2d", n=20011)
+    outs = []
+    for mode in (3, 4):
+        with make_sim(dict(p, search_mode=mode), pos, sp) as sim:
+            chemo.chemo_step_n(sim, 37)
+            outs.append(chemo.read_state_host(sim)[0])
+    np.testing.assert_array_equal(outs[0], outs[1])
+    q = wl.params("walls_grid_2d", grid=[16, 16, 1], chem_mode=1, fixed_grad=[1.0, 0.0, 0.0])
+    rng = np.random.default_rng(11)
+    pos = np.clip(0.5 + 0.004 * rng.standard_normal((4000, 2)), 0.0, 1.0).astype(np.float32)
+    sp = wl.half_species(4000, 2)
+    outs = []
+    for mode in (3, 4):
+        with make_sim(dict(q, search_mode=mode), pos, sp) as sim:
+            chemo.chemo_step_n(sim, 3)
+            outs.append(chemo.read_state_host(sim)[0])
+    np.testing.assert_array_equal(outs[0], outs[1])
