@@ -863,8 +863,14 @@ __device__ __forceinline__ float wrap_axis(float x, float lo, float hi, float L)
 // ---------------------------------------------------------------------------
 // k_step: the particle part of one step.
 // ---------------------------------------------------------------------------
-template <int DIM, bool PERIODIC, bool WARP>
-__global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
+#ifndef CHEMO_MOVE_BLOCKS
+#define CHEMO_MOVE_BLOCKS 6
+#endif
+// HALF: the pair force was summed by the half-window kernel; this instance
+// holds no search code (fewer registers, small shared memory, more warps to
+// hide the latency of the gathers).
+template <int DIM, bool PERIODIC, bool WARP, bool HALF = false>
+__global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
@@ -887,25 +893,27 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
     int npairs = 0;
     unsigned long long ids_unused = 0ull;
     float3 F = make_float3(0.f, 0.f, 0.f);
-    if (kp.pairs && kp.Fh) {
+    if constexpr (HALF) {
         // summed by the half-window kernel (the scatter clears them for the next step)
-        if (valid) {
+        if (valid && kp.pairs) {
             constexpr int FS = FhStride<DIM>::value;
             const longlong2 a = reinterpret_cast<const longlong2 *>(kp.Fh + (size_t)j * FS)[0];
             const long long az = DIM == 3 ? kp.Fh[(size_t)j * FS + 2] : 0ll;
             F = make_float3(__ll2float_rn(a.x) * kp.fq, __ll2float_rn(a.y) * kp.fq,
                             DIM == 3 ? __ll2float_rn(az) * kp.fq : 0.f);
         }
-    } else if (kp.pairs) {  // warp-synchronous: every lane takes part
-        unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, WARP>();
-        if (WARP)
-            F = pair_force_warp<DIM, PERIODIC, false>(kp, t, wbuf, (uint32_t)j, me, sp, valid, npairs, ids_unused);
-        else
-            F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused, wbuf);
-    }
-    if (kp.pair_count && !kp.Fh) {  // profiling only: in-cutoff pairs of this step
-        const int wsum = __reduce_add_sync(0xffffffffu, npairs);
-        if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
+    } else {
+        if (kp.pairs) {  // warp-synchronous: every lane takes part
+            unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, WARP>();
+            if (WARP)
+                F = pair_force_warp<DIM, PERIODIC, false>(kp, t, wbuf, (uint32_t)j, me, sp, valid, npairs, ids_unused);
+            else
+                F = pair_force<DIM, PERIODIC, false>(kp, t, (uint32_t)j, me, sp, valid, npairs, ids_unused, wbuf);
+        }
+        if (kp.pair_count) {  // profiling only: in-cutoff pairs of this step
+            const int wsum = __reduce_add_sync(0xffffffffu, npairs);
+            if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
+        }
     }
     if (!valid) return;
     if (kp.F_save) {  // recorded for the adjoint
@@ -1989,9 +1997,12 @@ template <int DIM, bool PERIODIC, bool W>
 static void step_launch(const KP &kp, int cur, cudaStream_t st)
 {
     const unsigned nb = (unsigned)((kp.n + TPB - 1) / TPB);
-    if (kp.pairs && kp.Fh)
+    if (kp.pairs && kp.Fh) {
         k_pairs_half<DIM, PERIODIC><<<nb, TPB, pair_smem<DIM, PERIODIC, false>(), st>>>(kp);
-    k_step<DIM, PERIODIC, W><<<nb, TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
+        k_step<DIM, PERIODIC, false, true><<<nb, TPB, sizeof(SmemTables), st>>>(kp, cur);
+    } else {
+        k_step<DIM, PERIODIC, W><<<nb, TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
+    }
 }
 
 cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches)
