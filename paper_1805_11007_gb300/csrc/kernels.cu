@@ -734,10 +734,7 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
                 pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
                 const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
                 const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
-                if (r2 < rc2 && r2 > 0.f) {
-                    lst[nl++ * 32] = q + (uint32_t)u;
-                    count += 1;
-                }
+                if (r2 < rc2 && r2 > 0.f) lst[nl++ * 32] = q + (uint32_t)u;
             }
             q += m;
             if (q >= qe) {
@@ -751,10 +748,12 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
         }
         if (__any_sync(0xffffffffu, nl > LIST_CAP - UNROLL)) {
             flush_half<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
+            count += nl;
             nl = 0;
         }
     }
     flush_half<DIM, PERIODIC>(kp, t, lst, nl, me, row, F);
+    count += nl;
     if (kp.pair_count) {  // profiling only: each pair found here is an in-cutoff pair of both cells
         const int wsum = __reduce_add_sync(0xffffffffu, count);
         if (lane == 0 && wsum) atomicAdd(kp.pair_count, 2ull * (unsigned long long)wsum);
