@@ -175,8 +175,30 @@ def cpu_baseline_full(p, pos, sp, budget_s=12.0, max_steps=10):
         if time.perf_counter() - t0 > budget_s:
             break
     el = time.perf_counter() - t0
-    return {"value": pos.shape[0] * steps / el, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
-            "sample": "%d full steps of the %d-cell 3D clump workload (FP64 oracle, OpenMP)" % (steps, pos.shape[0])}
+    out = {"value": pos.shape[0] * steps / el, "unit": UNIT, "cores": orc.get_threads(), "kind": "oracle",
+           "sample": "%d full steps of the %d-cell 3D clump workload (FP64 oracle, OpenMP)" % (steps, pos.shape[0])}
+    # the same oracle on one host thread, over a self-similar 1/64 sample
+    # (same cell density and nodes per cell) for about 3 s
+    try:
+        orc.set_threads(1)
+        q, qpos, qsp = scaled_sample(1.0 / 64.0, BASE_SEED)
+        x = qpos.astype(np.float64)
+        s = qsp.copy()
+        c = np.zeros(orc.grid_shape(q))
+        t0 = time.perf_counter()
+        k = 0
+        while k < 5:
+            x, s, c, _ = orc.step(q, x, s, c, step_index=k)
+            k += 1
+            if time.perf_counter() - t0 > 3.0:
+                break
+        el1 = time.perf_counter() - t0
+        out["one_thread"] = {"value": qpos.shape[0] * k / el1, "unit": UNIT, "cores": 1,
+                             "sample": "%d steps of a self-similar %d-cell sample of the clump workload (%d^3 grid)"
+                                       % (k, qpos.shape[0], q["grid"][0])}
+    finally:
+        orc.set_threads(th)
+    return out
 
 
 def scaled_sample(frac, seed):
