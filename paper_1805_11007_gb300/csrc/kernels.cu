@@ -234,17 +234,20 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
     }
     bool more = q < qe;
     while (__any_sync(0xffffffffu, more)) {
-        if (more) {
-            const uint32_t m = min((uint32_t)UNROLL, qe - q);
 #if CHEMO_BATCH_LOADS
-            // a chunk of up to UNROLL candidates from one range, all loaded
-            // before any is tested
+        // a chunk of up to UNROLL candidates from one range, all loaded
+        // before any is tested; past the end of its range a lane tests a
+        // far-away sentinel (no pair), so the chunk ends at the warp's longest
+        {
+            const uint32_t m = more ? min((uint32_t)UNROLL, qe - q) : 0u;
+            const uint32_t mw = __reduce_max_sync(0xffffffffu, m);
             float4 ob[UNROLL];
 #pragma unroll
-            for (int u = 0; u < UNROLL; ++u) ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < UNROLL; ++u)
+                ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
 #pragma unroll
             for (int u = 0; u < UNROLL; ++u) {
-                if ((uint32_t)u >= m) break;
+                if ((uint32_t)u >= mw) break;
                 const float4 o = ob[u];
                 const uint32_t qq = q + (uint32_t)u;
                 float dx, dy, dz, r2;
@@ -257,7 +260,12 @@ __device__ __forceinline__ float3 pair_force(const KP &kp, const SmemTables &t, 
                     if (STATS) idsum += (unsigned long long)(__float_as_uint(o.w) & ID_MASK);
                 }
             }
+        }
+        if (more) {
+            const uint32_t m = min((uint32_t)UNROLL, qe - q);
 #else
+        if (more) {
+            const uint32_t m = min((uint32_t)UNROLL, qe - q);
             // a chunk of up to UNROLL candidates from one range; the next
             // candidate is loaded while the current one is tested
             float4 o = __ldg(&S[q]);
@@ -721,21 +729,27 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
     }
     bool more = q < qe;
     while (__any_sync(0xffffffffu, more)) {
+        // a chunk of up to UNROLL candidates per lane, all loaded before any
+        // is tested; past the end of its range a lane tests a far-away
+        // sentinel (no pair), so the chunk ends at the warp's longest
+        // (a branch the whole warp takes together)
+        const uint32_t m = more ? min((uint32_t)UNROLL, qe - q) : 0u;
+        const uint32_t mw = __reduce_max_sync(0xffffffffu, m);
+        float4 ob[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u)
+            ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+#pragma unroll
+        for (int u = 0; u < UNROLL; ++u) {
+            if ((uint32_t)u >= mw) break;
+            const float4 o = ob[u];
+            float dx, dy, dz, r2;
+            pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
+            const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
+            const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
+            if (r2 < rc2 && r2 > 0.f) lst[nl++ * 32] = q + (uint32_t)u;
+        }
         if (more) {
-            const uint32_t m = min((uint32_t)UNROLL, qe - q);
-            float4 ob[UNROLL];
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) ob[u] = (uint32_t)u < m ? __ldg(&S[q + u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-            for (int u = 0; u < UNROLL; ++u) {
-                if ((uint32_t)u >= m) break;
-                const float4 o = ob[u];
-                float dx, dy, dz, r2;
-                pair_delta<DIM, PERIODIC>(kp, me, o, dx, dy, dz, r2);
-                const uint32_t so = __float_as_uint(o.w) >> SP_SHIFT;
-                const float rc2 = two ? (so ? rc2_1 : rc2_0) : t.rc2[row + (int)so];
-                if (r2 < rc2 && r2 > 0.f) lst[nl++ * 32] = q + (uint32_t)u;
-            }
             q += m;
             if (q >= qe) {
                 while (q >= qe && r < nr) {
