@@ -1136,18 +1136,32 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
     const int64_t NG = kp.ngroups;
     const int64_t g0 = (int64_t)tile * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
 
-    uint32_t v[SCAN_ITEMS];
+    // group totals of the tile, read (and the other count buffer cleared)
+    // with consecutive threads on consecutive groups, then taken back from
+    // shared memory as SCAN_ITEMS consecutive groups per thread (one padding
+    // word per 32 keeps both passes free of bank conflicts)
+    __shared__ uint32_t s_v[SCAN_TILE + SCAN_TILE / 32];
     const uint4 *src = reinterpret_cast<const uint4 *>(kp.cnt_nxt);  // one uint4 per group
     uint4 *clr = reinterpret_cast<uint4 *>(kp.cnt_cur);
+    const int64_t tbase = (int64_t)tile * SCAN_TILE;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-        const int64_t g = g0 + i;
-        v[i] = 0u;
+        const int k = i * TPB + (int)threadIdx.x;
+        const int64_t g = tbase + k;
+        uint32_t s = 0u;
         if (g < NG) {
             const uint4 q = __ldcs(src + g);
-            v[i] = halfsum(q.x) + halfsum(q.y) + halfsum(q.z) + halfsum(q.w);
+            s = halfsum(q.x) + halfsum(q.y) + halfsum(q.z) + halfsum(q.w);
             clr[g] = make_uint4(0u, 0u, 0u, 0u);
         }
+        s_v[k + (k >> 5)] = s;
+    }
+    __syncthreads();
+    uint32_t v[SCAN_ITEMS];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const int k = (int)threadIdx.x * SCAN_ITEMS + i;
+        v[i] = s_v[k + (k >> 5)];
     }
     uint32_t tsum = 0;
 #pragma unroll
