@@ -1081,6 +1081,8 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
 #endif
 constexpr int SCAN_ITEMS = CHEMO_SCAN_ITEMS;        // consecutive groups per thread
 constexpr int SCAN_TILE = TPB * SCAN_ITEMS;         // groups per tile
+// the tile status table is allocated for tiles of at least 2048 groups
+static_assert(SCAN_TILE >= 2048, "scan tiles smaller than the tile table allows");
 constexpr unsigned long long ST_AGG = 1ull, ST_INC = 2ull;
 constexpr int ST_VAL_BITS = 38;
 constexpr unsigned long long ST_VAL_MASK = (1ull << ST_VAL_BITS) - 1ull;
