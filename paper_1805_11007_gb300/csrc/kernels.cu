@@ -644,6 +644,66 @@ __device__ __forceinline__ void flush_half(const KP &kp, const SmemTables &t, co
     F.z += az;
 }
 
+// Ranges of the upper half of the 3^d window of the cell `me` (sorted index
+// j): the rows at (dz, dy) > (0, 0) in lexicographic order with all their
+// bins, in its own row the next bin and the cells of its own bin after it.
+// Calls push(first, end) for each range of sorted indices.
+template <int DIM, bool PERIODIC, typename Push>
+__device__ __forceinline__ void stage_half(const KP &kp, float4 me, int sp, uint32_t j, Push &&push)
+{
+    const uint32_t *__restrict__ cnt = kp.cnt_cur;
+    const uint32_t *__restrict__ gst = kp.gstart;
+    const float rs2 = kp.rsp2[sp];
+    int c[3] = {0, 0, 0};
+    float f[3] = {0.f, 0.f, 0.f};
+    const float pc[3] = {me.x, me.y, me.z};
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
+        f[a] = fminf(fmaxf(__fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a], 0.f), 1.f);
+    }
+    if (DIM == 2) c[2] = layer_of(kp, me);  // rows of the particle's own layer
+    // rows (oy, oz) of the upper half: the own row (0, 0), then (1, 0),
+    // then (-1..1, 1) in 3D
+    constexpr int NROWS = DIM == 3 ? 5 : 2;
+    for (int k = 0; k < NROWS; ++k) {
+        const int oy = k == 0 ? 0 : (k == 1 ? 1 : k - 3);
+        const int oz = k < 2 ? 0 : 1;
+        int y = c[1] + oy, z = c[2] + oz;
+        if (PERIODIC) {
+            y = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+            if (DIM == 3) z = z >= kp.nb[2] ? z - kp.nb[2] : z;
+        } else if (y < 0 || y >= kp.nb[1] || (DIM == 3 && z >= kp.nb[2])) {
+            continue;
+        }
+        const float gyz = (DIM == 3 ? gap2(oz, f[2], kp.bside[2]) : 0.f) + gap2(oy, f[1], kp.bside[1]);
+        if (gyz >= rs2) continue;  // the whole row is out of reach
+        const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)y + (uint32_t)kp.nb[1] * (uint32_t)z);
+        int x0 = k == 0 ? c[0] : c[0] - 1, x1 = c[0] + 1;
+        if (!PERIODIC) {
+            x0 = max(x0, 0);
+            x1 = min(x1, kp.nb[0] - 1);
+        }
+        if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
+        if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
+        if (PERIODIC && x0 < 0) {
+            const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
+            push(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
+            x0 = 0;
+        }
+        if (PERIODIC && x1 >= kp.nb[0]) {
+            push(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
+            x1 = kp.nb[0] - 1;
+        }
+        if (x0 <= x1) {
+            // the own row starts after this cell: the cells of its bin
+            // before it found the pair themselves
+            const uint32_t b0 = k == 0 ? j + 1u : bin_start(cnt, gst, rowk + x0);
+            push(b0, bin_start(cnt, gst, rowk + x1 + 1));
+        }
+    }
+}
+
 template <int DIM, bool PERIODIC>
 __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
 {
@@ -660,61 +720,11 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
     unsigned char *wbuf = smem + sizeof(SmemTables) + (threadIdx.x >> 5) * warp_region<DIM, PERIODIC, false>();
     uint2 *rng = reinterpret_cast<uint2 *>(wbuf) + lane;
     uint32_t *lst = reinterpret_cast<uint32_t *>(wbuf + (size_t)32 * RowCap<DIM, PERIODIC>::value * sizeof(uint2)) + lane;
-    const uint32_t *__restrict__ cnt = kp.cnt_cur;
-    const uint32_t *__restrict__ gst = kp.gstart;
     const uint32_t n = (uint32_t)kp.n;
-    const float rs2 = kp.rsp2[sp];
     int nr = 0;
-    if (valid) {
-        int c[3] = {0, 0, 0};
-        float f[3] = {0.f, 0.f, 0.f};
-        const float pc[3] = {me.x, me.y, me.z};
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-            c[a] = bin_axis(pc[a], kp.lo[a], kp.inv_b[a], kp.nb[a]);
-            f[a] = fminf(fmaxf(__fmul_rn(__fsub_rn(pc[a], kp.lo[a]), kp.inv_b[a]) - (float)c[a], 0.f), 1.f);
-        }
-        if (DIM == 2) c[2] = layer_of(kp, me);  // rows of the particle's own layer
-        // rows (oy, oz) of the upper half: the own row (0, 0), then (1, 0),
-        // then (-1..1, 1) in 3D
-        constexpr int NROWS = DIM == 3 ? 5 : 2;
-        for (int k = 0; k < NROWS; ++k) {
-            const int oy = k == 0 ? 0 : (k == 1 ? 1 : k - 3);
-            const int oz = k < 2 ? 0 : 1;
-            int y = c[1] + oy, z = c[2] + oz;
-            if (PERIODIC) {
-                y = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
-                if (DIM == 3) z = z >= kp.nb[2] ? z - kp.nb[2] : z;
-            } else if (y < 0 || y >= kp.nb[1] || (DIM == 3 && z >= kp.nb[2])) {
-                continue;
-            }
-            const float gyz = (DIM == 3 ? gap2(oz, f[2], kp.bside[2]) : 0.f) + gap2(oy, f[1], kp.bside[1]);
-            if (gyz >= rs2) continue;  // the whole row is out of reach
-            const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)y + (uint32_t)kp.nb[1] * (uint32_t)z);
-            int x0 = k == 0 ? c[0] : c[0] - 1, x1 = c[0] + 1;
-            if (!PERIODIC) {
-                x0 = max(x0, 0);
-                x1 = min(x1, kp.nb[0] - 1);
-            }
-            if (x0 < c[0] && gyz + gap2(-1, f[0], kp.bside[0]) >= rs2) x0 = c[0];
-            if (x1 > c[0] && gyz + gap2(1, f[0], kp.bside[0]) >= rs2) x1 = c[0];
-            if (PERIODIC && x0 < 0) {
-                const uint32_t kk = rowk + (uint32_t)(kp.nb[0] - 1);
-                rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, kk), bin_start(cnt, gst, kk + 1));
-                x0 = 0;
-            }
-            if (PERIODIC && x1 >= kp.nb[0]) {
-                rng[nr++ * 32] = make_uint2(bin_start(cnt, gst, rowk), bin_start(cnt, gst, rowk + 1));
-                x1 = kp.nb[0] - 1;
-            }
-            if (x0 <= x1) {
-                // the own row starts after this cell: the cells of its bin
-                // before it found the pair themselves
-                const uint32_t b0 = k == 0 ? (uint32_t)j + 1u : bin_start(cnt, gst, rowk + x0);
-                rng[nr++ * 32] = make_uint2(b0, bin_start(cnt, gst, rowk + x1 + 1));
-            }
-        }
-    }
+    if (valid) stage_half<DIM, PERIODIC>(kp, me, sp, (uint32_t)j, [&](uint32_t x0, uint32_t x1) {
+        rng[nr++ * 32] = make_uint2(x0, x1);
+    });
     const float4 *__restrict__ S = kp.S;
     const int row = sp * MAXS;
     const bool two = kp.ns <= 2;
