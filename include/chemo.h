@@ -228,6 +228,18 @@ int chemo_read_field(chemo_sim *sim, float *c_out, int mem_kind, void *stream);
  * otherwise. */
 int chemo_record(chemo_sim *sim, int64_t nsteps, int32_t every, void *stream);
 
+/* chemo_record that also keeps, during the run, the states the reverse sweep
+ * reads (positions, fields, sorted states with their cell lists, pair
+ * forces) for the latest segments that fit in store_bytes of device memory
+ * (store_bytes < 0: every segment; 0: none, which is chemo_record). The
+ * gradient re-runs only the other segments, so with every segment stored it
+ * is the reverse sweep alone. The checkpoints are taken as in chemo_record.
+ * A stored segment is stepped launch by launch (no graph replay). Memory per
+ * stored segment: every x (n x (8 d + 16) + 4 grid_nodes + 4 x the cell
+ * list's words) bytes, plus n x 4 d. Errors: as chemo_record; ENOMEM if the
+ * stored segments do not fit. */
+int chemo_record_stored(chemo_sim *sim, int64_t nsteps, int32_t every, int64_t store_bytes, void *stream);
+
 /* Vector-Jacobian product (adjoint) of the last recorded run: given
  * dL/dpos of its final state (n x dim by id) and optionally dL/dc of its
  * final field (grid_nodes, NULL = 0), returns dL_dparams = [dL/dchi,

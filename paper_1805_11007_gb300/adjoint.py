@@ -44,14 +44,14 @@ def with_theta(params: dict, theta) -> dict:
 
 class ChemoRun(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, pos0, sim, nsteps, every, species, c0=None, step0=0):
+    def forward(ctx, theta, pos0, sim, nsteps, every, species, c0=None, step0=0, store_bytes=0):
         params = with_theta(sim.params, theta.detach().cpu().tolist())
         chemo.chemo_set_params(sim, params)
         chemo.chemo_write_state(sim, pos0.detach().contiguous(), species)
         if c0 is not None:
             chemo.chemo_write_field(sim, c0)
         chemo.chemo_set_step_index(sim, step0)
-        chemo.chemo_record(sim, int(nsteps), int(every))
+        chemo.chemo_record(sim, int(nsteps), int(every), store_bytes=int(store_bytes))
         out = torch.empty_like(pos0)
         chemo.chemo_read_state(sim, out, None, None)
         ctx.sim = sim
@@ -66,7 +66,7 @@ class ChemoRun(torch.autograd.Function):
         dtheta = torch.zeros(ctx.ntheta, dtype=torch.float32, device=g.device)
         dpos0 = torch.zeros_like(g)
         chemo.chemo_gradient(sim, g.detach().contiguous().float(), dtheta, None, dpos0)
-        return dtheta.to(device=ctx.theta_device, dtype=ctx.theta_dtype), dpos0, None, None, None, None, None, None
+        return dtheta.to(device=ctx.theta_device, dtype=ctx.theta_dtype), dpos0, None, None, None, None, None, None, None
 
 
 def mean_x_displacement(pos: torch.Tensor, pos0: torch.Tensor) -> torch.Tensor:

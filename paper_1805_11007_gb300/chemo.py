@@ -172,6 +172,7 @@ def _declare(L):
         "chemo_read_state": ([vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_read_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_record": ([vp, i64, i32, vp], ctypes.c_int),
+        "chemo_record_stored": ([vp, i64, i32, i64, vp], ctypes.c_int),
         "chemo_gradient": ([vp, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_set_params": ([vp, PP], ctypes.c_int),
         "chemo_step_index": ([vp], i64),
@@ -367,8 +368,15 @@ def chemo_read_field(sim: Sim, c_out, stream=None):
     _check(lib().chemo_read_field(_h(sim), cp, k, _stream(stream)), "chemo_read_field")
 
 
-def chemo_record(sim: Sim, nsteps: int, every: int, stream=None):
-    _check(lib().chemo_record(_h(sim), int(nsteps), int(every), _stream(stream)), "chemo_record")
+def chemo_record(sim: Sim, nsteps: int, every: int, stream=None, store_bytes: int = 0):
+    """Recorded run for chemo_gradient, checkpoints every `every` steps; the
+    latest segments whose states fit in store_bytes (< 0: all) are kept and
+    not re-run by the gradient."""
+    if store_bytes:
+        _check(lib().chemo_record_stored(_h(sim), int(nsteps), int(every), int(store_bytes), _stream(stream)),
+               "chemo_record_stored")
+    else:
+        _check(lib().chemo_record(_h(sim), int(nsteps), int(every), _stream(stream)), "chemo_record")
 
 
 def chemo_gradient(sim: Sim, dL_dpos_final, dL_dparams, dL_dc_final=None, dL_dpos0=None, stream=None):

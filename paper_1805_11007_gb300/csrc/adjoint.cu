@@ -61,6 +61,9 @@ struct Tape {
     // two segment buffers: segment s - 1 is re-run into one while the
     // reverse sweep of segment s reads the other (two streams)
     SegBuf sb[2];
+    SegBuf sb_all;  // the block behind sb[0], sb[1] (2 every steps, 2 (every + 1) position slots)
+    // segments whose states the recorded run stored (pos == NULL: re-run)
+    std::vector<SegBuf> stored;
     cudaStream_t s_fwd = nullptr, s_rev = nullptr;
     cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr, ev_fwd_end = nullptr, ev_rev_end = nullptr;
@@ -124,21 +127,6 @@ __global__ void k_gather_state(KP kp, float *__restrict__ pos, uint8_t *__restri
     pos[id * kp.dim + 1] = u.y;
     if (kp.dim == 3) pos[id * kp.dim + 2] = u.z;
     if (sp) sp[id] = (uint8_t)(w >> SP_SHIFT);
-}
-
-// Snapshot of the sorted state and its cell list (one launch for the three
-// copies): S (n float4), the count table (cw words), the group offsets (gw
-// words).
-__global__ void k_snapshot(const float4 *__restrict__ S, int64_t n, const uint32_t *__restrict__ cnt, int64_t cw,
-                           const uint32_t *__restrict__ gst, int64_t gw, float4 *__restrict__ S_out,
-                           uint32_t *__restrict__ cnt_out, uint32_t *__restrict__ gst_out)
-{
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n + cw + gw; i += stride) {
-        if (i < n) S_out[i] = S[i];
-        else if (i < n + cw) cnt_out[i - n] = cnt[i - n];
-        else gst_out[i - n - cw] = gst[i - n - cw];
-    }
 }
 
 // Transposed Laplacian along one axis at node k (N nodes, stride): with
@@ -502,7 +490,67 @@ float *cur_field(chemo_sim *s) { return s->kp.has_grid ? s->kp.c[s->cur] : nullp
 
 }  // namespace
 
+namespace {
+
+// Device memory of one segment's stored states.
+size_t segment_bytes(const chemo_tape *t)
+{
+    const size_t E = (size_t)t->every, n1 = (size_t)std::max<int64_t>(t->n, 1);
+    const size_t pb = n1 * t->dim * sizeof(float), gb = (size_t)std::max<int64_t>(t->G, 1) * sizeof(float);
+    return pb * (E + 1) + gb * E + E * n1 * sizeof(float4) + E * (t->cwords + t->gwords) * sizeof(uint32_t) + E * pb +
+           6 * 256;
+}
+
+// Buffers for the stored states of E steps (E + 1 position slots).
+int alloc_steps(chemo_tape *t, SegBuf &B, size_t E)
+{
+    const size_t n1 = (size_t)std::max<int64_t>(t->n, 1);
+    const size_t pb = n1 * t->dim * sizeof(float), gb = (size_t)std::max<int64_t>(t->G, 1) * sizeof(float);
+    void *p;
+    int r;
+    if ((r = talloc(t, &p, pb * (E + 1)))) return r;
+    B.pos = (float *)p;
+    if ((r = talloc(t, &p, gb * E))) return r;
+    B.c = (float *)p;
+    if ((r = talloc(t, &p, E * n1 * sizeof(float4)))) return r;
+    B.S = (float4 *)p;
+    if ((r = talloc(t, &p, E * t->cwords * sizeof(uint32_t)))) return r;
+    B.cnt = (uint32_t *)p;
+    if ((r = talloc(t, &p, E * t->gwords * sizeof(uint32_t)))) return r;
+    B.gst = (uint32_t *)p;
+    if ((r = talloc(t, &p, E * pb))) return r;
+    B.F = (float *)p;
+    return CHEMO_OK;
+}
+
+// Points the particle kernel's tape at B for the steps step0 .. step0 + len - 1:
+// each of those steps writes the positions before it, the field, the sorted
+// state with its cell list and the pair force.
+void set_tape(chemo_sim *s, const chemo_tape *t, const SegBuf &B, int64_t step0, int64_t len)
+{
+    KP::TapeOut &tp = s->kp.tape;
+    tp = KP::TapeOut{};
+    tp.pos = B.pos;
+    tp.c = B.c;
+    tp.F = B.F;
+    tp.S = B.S;
+    tp.cnt = B.cnt;
+    tp.gst = B.gst;
+    tp.s0 = (unsigned long long)step0;
+    tp.nk = (unsigned long long)len;
+    tp.cwords = (int64_t)t->cwords;
+    tp.gwords = (int64_t)t->gwords;
+}
+
+
+}  // namespace
+
 extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *stream)
+{
+    return chemo_record_stored(s, nsteps, every, 0, stream);
+}
+
+extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, int64_t store_bytes, void *stream)
 {
     if (!s || nsteps < 0 || every < 1) return eng_fail(CHEMO_EINVAL, "chemo_record: bad arguments");
     if (int r = check_adjoint_model(s)) return r;
@@ -520,6 +568,13 @@ extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *s
     t->dim = kp.dim;
     t->ns = kp.ns;
     t->nseg = (int)((nsteps + every - 1) / every);
+    t->cwords = (size_t)kp.bin_slots / 2;
+    t->gwords = ((size_t)kp.ngroups + 1 + 3) & ~(size_t)3;
+    // the latest segments whose states fit in store_bytes are stored now
+    // and not re-run by the gradient (the reverse sweep starts with them)
+    const size_t sbytes = segment_bytes(t);
+    const int64_t nstore = store_bytes < 0 ? t->nseg : std::min<int64_t>(t->nseg, store_bytes / (int64_t)sbytes);
+    t->stored.assign((size_t)t->nseg, SegBuf{});
     const size_t pb = (size_t)std::max<int64_t>(t->n, 1) * kp.dim * sizeof(float);
     const size_t gb = (size_t)std::max<int64_t>(t->G, 1) * sizeof(float);
     void *p;
@@ -532,15 +587,50 @@ extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *s
     }
     if ((r = talloc(t, &p, (size_t)std::max<int64_t>(t->n, 1)))) return r;
     t->species = (uint8_t *)p;
-    // forward with checkpoints at the start of every segment and at the end
-    for (int k = 0; k <= t->nseg; ++k) {
-        if ((r = gather(s, t->ck_pos[k], k == 0 ? t->species : nullptr, st))) return r;
-        if (t->G) ATRY(cudaMemcpyAsync(t->ck_c[k], cur_field(s), gb, cudaMemcpyDeviceToDevice, st));
-        if (k == t->nseg) break;
-        const int64_t len = std::min<int64_t>(every, nsteps - (int64_t)k * every);
-        if ((r = chemo_step_n(s, len, stream))) return r;
+    // the stored segments are the last nstore: steps k0 .. nsteps - 1 of the
+    // run, kept in one block; each stored segment is a view into it
+    const int fs = t->nseg - (int)nstore;
+    const int64_t k0 = (int64_t)fs * every, nk = nsteps - k0;
+    SegBuf all{};
+    if (nstore > 0) {
+        if ((r = alloc_steps(t, all, (size_t)nk))) return r;
+        const size_t n1 = (size_t)std::max<int64_t>(t->n, 1), g1 = (size_t)std::max<int64_t>(t->G, 1);
+        for (int k = fs; k < t->nseg; ++k) {
+            const size_t o = (size_t)((int64_t)k * every - k0);
+            SegBuf &B = t->stored[(size_t)k];
+            B.pos = all.pos + o * n1 * t->dim;
+            B.c = all.c + o * g1;
+            B.S = all.S + o * n1;
+            B.cnt = all.cnt + o * t->cwords;
+            B.gst = all.gst + o * t->gwords;
+            B.F = all.F + o * n1 * t->dim;
+        }
     }
-    return CHEMO_OK;
+    // forward with checkpoints at the start of every segment and at the end;
+    // over the stored steps the particle kernel writes the tape (indexed by
+    // the device's step counter, so the graphs of chemo_step_n replay it:
+    // they are captured afresh with the tape set and dropped after)
+    int rc = CHEMO_OK;
+    for (int k = 0; k <= t->nseg && rc == CHEMO_OK; ++k) {
+        if ((rc = gather(s, t->ck_pos[k], k == 0 ? t->species : nullptr, st))) break;
+        if (t->G && cudaMemcpyAsync(t->ck_c[k], cur_field(s), gb, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            rc = eng_fail(CHEMO_ECUDA, "chemo_record: checkpoint copy failed");
+            break;
+        }
+        if (k == t->nseg) break;
+        if (k == fs) {
+            eng_drop_graphs(s);
+            set_tape(s, t, all, t->step0 + k0, nk);
+        }
+        const int64_t len = std::min<int64_t>(every, nsteps - (int64_t)k * every);
+        rc = chemo_step_n(s, len, stream);
+    }
+    if (nstore > 0) {
+        s->kp.tape = KP::TapeOut{};
+        eng_drop_graphs(s);
+        if (rc == CHEMO_OK) rc = gather(s, all.pos + (size_t)nk * t->n * t->dim, nullptr, st);
+    }
+    return rc;
 }
 
 extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
@@ -558,26 +648,25 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     const size_t gb = (size_t)std::max<int64_t>(G, 1) * sizeof(float);
     void *p;
     int r;
-    if (!t->sb[0].pos) {
-        const KP &k0 = s->kp;
-        t->cwords = (size_t)k0.bin_slots / 2;
-        t->gwords = ((size_t)k0.ngroups + 1 + 3) & ~(size_t)3;
-        const size_t E = (size_t)t->every;
+    bool rerun_any = false;
+    for (const SegBuf &B : t->stored) rerun_any = rerun_any || !B.pos;
+    if (rerun_any && !t->sb[0].pos) {
+        // one block for both buffers, so that one tape (slot = step mod
+        // 2 every) serves every re-run and its graphs are captured once
+        const size_t E = (size_t)t->every, n1 = (size_t)std::max<int64_t>(n, 1), g1 = (size_t)std::max<int64_t>(G, 1);
+        if ((r = alloc_steps(t, t->sb_all, 2 * E + 1))) return r;
         for (int b = 0; b < 2; ++b) {
             SegBuf &B = t->sb[b];
-            if ((r = talloc(t, &p, pb * (E + 1)))) return r;
-            B.pos = (float *)p;
-            if ((r = talloc(t, &p, gb * E))) return r;
-            B.c = (float *)p;
-            if ((r = talloc(t, &p, E * (size_t)std::max<int64_t>(n, 1) * sizeof(float4)))) return r;
-            B.S = (float4 *)p;
-            if ((r = talloc(t, &p, E * t->cwords * sizeof(uint32_t)))) return r;
-            B.cnt = (uint32_t *)p;
-            if ((r = talloc(t, &p, E * t->gwords * sizeof(uint32_t)))) return r;
-            B.gst = (uint32_t *)p;
-            if ((r = talloc(t, &p, E * pb))) return r;
-            B.F = (float *)p;
+            const SegBuf &A = t->sb_all;
+            B.pos = A.pos + (size_t)b * (E + 1) * n1 * dim;
+            B.c = A.c + (size_t)b * E * g1;
+            B.S = A.S + (size_t)b * E * n1;
+            B.cnt = A.cnt + (size_t)b * E * t->cwords;
+            B.gst = A.gst + (size_t)b * E * t->gwords;
+            B.F = A.F + (size_t)b * E * n1 * dim;
         }
+    }
+    if (!t->s_fwd) {
         ATRY(cudaStreamCreateWithFlags(&t->s_fwd, cudaStreamNonBlocking));
         ATRY(cudaStreamCreateWithFlags(&t->s_rev, cudaStreamNonBlocking));
         for (int b = 0; b < 2; ++b) {
@@ -621,6 +710,8 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     const float f_unit = s->prm.inter != 0.f ? 1.f / s->prm.inter : 0.f;
     const int64_t end_step = s->step;
     // restores segment seg's checkpoint and re-runs it on sf, storing its states in B
+    // (the particle kernel writes the states into buffer seg mod 2 through
+    // the periodic tape, so chemo_step_n replays its graphs for every re-run)
     auto rerun = [&](int seg, SegBuf &B) -> int {
         const int64_t n0 = (int64_t)seg * t->every;
         const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
@@ -628,40 +719,59 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         if ((rr = eng_ingest(s, t->ck_pos[seg], t->species, nullptr, CHEMO_MEM_DEVICE, sf))) return rr;
         if (G) ATRY(cudaMemcpyAsync(cur_field(s), t->ck_c[seg], gb, cudaMemcpyDeviceToDevice, sf));
         if ((rr = chemo_set_step_index(s, t->step0 + n0, sf))) return rr;
-        for (int64_t k = 0; k < len; ++k) {
-            if ((rr = gather(s, B.pos + (size_t)k * n * dim, nullptr, sf))) return rr;
-            if (G) ATRY(cudaMemcpyAsync(B.c + (size_t)k * G, cur_field(s), gb, cudaMemcpyDeviceToDevice, sf));
-            // the sorted state and its cell list, for the pair term of the reverse sweep
-            const KP v = eng_view(s);
-            const int64_t tot = n + (int64_t)t->cwords + (int64_t)t->gwords;
-            const unsigned nb = (unsigned)std::min<int64_t>((tot + ATPB - 1) / ATPB, 152 * 16);
-            k_snapshot<<<nb, ATPB, 0, sf>>>(v.S, n, v.cnt_cur, (int64_t)t->cwords, v.gstart, (int64_t)t->gwords,
-                                            B.S + (size_t)k * n, B.cnt + (size_t)k * t->cwords,
-                                            B.gst + (size_t)k * t->gwords);
-            ATRY(cudaGetLastError());
-            // the step's pair force, by id (the particle kernel writes every cell's)
-            s->kp.F_save = B.F + (size_t)k * n * dim;
-            rr = eng_enqueue_step(s, sf, nullptr);
-            s->kp.F_save = nullptr;
-            if (rr) return rr;
-        }
+        if ((rr = chemo_step_n(s, len, sf))) return rr;
         return gather(s, B.pos + (size_t)len * n * dim, nullptr, sf);
     };
-    if ((r = rerun(t->nseg - 1, t->sb[(t->nseg - 1) & 1]))) return r;
-    ATRY(cudaEventRecord(t->ev_ready[(t->nseg - 1) & 1], sf));
+    // the tape points into this recording while re-runs are enqueued: cleared
+    // (and the graphs that hold it dropped) on every way out
+    struct TapeGuard {
+        chemo_sim *s;
+        bool on;
+        ~TapeGuard()
+        {
+            if (on) {
+                s->kp.tape = KP::TapeOut{};
+                eng_drop_graphs(s);
+            }
+        }
+    } guard{s, false};
+    if (rerun_any) {
+        eng_drop_graphs(s);
+        KP::TapeOut &tp = s->kp.tape;
+        tp = KP::TapeOut{};
+        tp.pos = t->sb_all.pos;
+        tp.c = t->sb_all.c;
+        tp.F = t->sb_all.F;
+        tp.S = t->sb_all.S;
+        tp.cnt = t->sb_all.cnt;
+        tp.gst = t->sb_all.gst;
+        tp.s0 = (unsigned long long)t->step0;
+        tp.period = tp.nk = 2ull * (unsigned long long)t->every;
+        tp.pos_gap = (unsigned long long)t->every;
+        tp.cwords = (int64_t)t->cwords;
+        tp.gwords = (int64_t)t->gwords;
+        guard.on = true;
+    }
+    auto is_stored = [&](int seg) { return t->stored[(size_t)seg].pos != nullptr; };
+    bool sb_used[2] = {false, false};  // a reverse sweep has read the buffer (wait for it before refilling)
+    if (!is_stored(t->nseg - 1)) {
+        if ((r = rerun(t->nseg - 1, t->sb[(t->nseg - 1) & 1]))) return r;
+        ATRY(cudaEventRecord(t->ev_ready[(t->nseg - 1) & 1], sf));
+    }
     for (int seg = t->nseg - 1; seg >= 0; --seg) {
         const int64_t n0 = (int64_t)seg * t->every;
         const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
-        const SegBuf &B = t->sb[seg & 1];
-        if (seg >= 1) {
-            // re-run the previous segment into the other buffer once the reverse
-            // sweep that last read it (segment seg + 1) is done
+        const bool stored = is_stored(seg);
+        const SegBuf &B = stored ? t->stored[(size_t)seg] : t->sb[seg & 1];
+        if (seg >= 1 && !is_stored(seg - 1)) {
+            // re-run the previous segment into its buffer once the reverse
+            // sweep that last read that buffer is done
             const int ob = (seg - 1) & 1;
-            if (seg + 1 <= t->nseg - 1) ATRY(cudaStreamWaitEvent(sf, t->ev_done[ob], 0));
+            if (sb_used[ob]) ATRY(cudaStreamWaitEvent(sf, t->ev_done[ob], 0));
             if ((r = rerun(seg - 1, t->sb[ob]))) return r;
             ATRY(cudaEventRecord(t->ev_ready[ob], sf));
         }
-        ATRY(cudaStreamWaitEvent(sr, t->ev_ready[seg & 1], 0));
+        if (!stored) ATRY(cudaStreamWaitEvent(sr, t->ev_ready[seg & 1], 0));
         // reverse sweep over the segment (stream sr)
         for (int64_t k = len - 1; k >= 0; --k) {
             const unsigned long long step = (unsigned long long)(t->step0 + n0 + k);
@@ -719,7 +829,15 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
             }
             lx ^= 1;
         }
-        ATRY(cudaEventRecord(t->ev_done[seg & 1], sr));
+        if (!stored) {
+            ATRY(cudaEventRecord(t->ev_done[seg & 1], sr));
+            sb_used[seg & 1] = true;
+        }
+    }
+    if (guard.on) {  // every re-run is enqueued
+        s->kp.tape = KP::TapeOut{};
+        eng_drop_graphs(s);
+        guard.on = false;
     }
     // join both streams back into the caller's
     ATRY(cudaEventRecord(t->ev_fwd_end, sf));

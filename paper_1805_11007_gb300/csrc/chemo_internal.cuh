@@ -117,7 +117,20 @@ struct KP {
     uint32_t *err;               // latched error bits
     unsigned long long *step;    // absolute index of the step being computed
     unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
-    float *F_save;               // non-NULL: the particle kernel stores each cell's pair force (by id)
+    // adjoint recording (pos == NULL: off): the particle kernel stores, for
+    // steps s0 .. s0 + nk - 1 (absolute indices; with period > 0 step s goes
+    // to slot (s - s0) mod period, nk = period), the positions before the
+    // step and the pair force (by id, [k][id][dim]), the sorted state
+    // ([k][n]), its count table and group offsets ([k][cwords], [k][gwords])
+    // and the field c^n ([k][G]). With pos_gap > 0 the position slots skip
+    // one after every pos_gap steps (room for a segment's final positions).
+    struct TapeOut {
+        float *pos, *c, *F;
+        float4 *S;
+        uint32_t *cnt, *gst;
+        unsigned long long s0, nk, period, pos_gap;
+        int64_t cwords, gwords;
+    } tape;
     long long *Fh;               // search mode 4 (set iff pairs and mode 4): pair-force sums in fixed
                                  // point, FhStride per sorted cell; NULL = the full-window search
 };

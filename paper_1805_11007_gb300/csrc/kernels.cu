@@ -905,6 +905,17 @@ __global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
             kp.Rg[g] = 0.f;
         }
     }
+    // adjoint recording: this step's count table, group offsets and field
+    unsigned long long tk = kp.tape.pos ? *kp.step - kp.tape.s0 : ~0ull;
+    if (kp.tape.pos && kp.tape.period) tk %= kp.tape.period;
+    const bool taping = tk < kp.tape.nk;
+    if (taping) {
+        const int64_t stride = (int64_t)gridDim.x * TPB;
+        for (int64_t i = j; i < kp.tape.cwords; i += stride) kp.tape.cnt[(int64_t)tk * kp.tape.cwords + i] = kp.cnt_cur[i];
+        for (int64_t i = j; i < kp.tape.gwords; i += stride) kp.tape.gst[(int64_t)tk * kp.tape.gwords + i] = kp.gstart[i];
+        if (kp.has_grid)
+            for (int64_t i = j; i < kp.G; i += stride) kp.tape.c[(int64_t)tk * kp.G + i] = kp.c[cur][i];
+    }
     __syncthreads();
     const bool valid = j < kp.n;
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -939,11 +950,18 @@ __global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
         }
     }
     if (!valid) return;
-    if (kp.F_save) {  // recorded for the adjoint
+    if (taping) {  // recorded for the adjoint: the state before the move and the pair force
         const int64_t gi = gid_of(kp, me);
-        kp.F_save[gi * DIM + 0] = F.x;
-        kp.F_save[gi * DIM + 1] = F.y;
-        if (DIM == 3) kp.F_save[gi * DIM + 2] = F.z;
+        const int64_t r = ((int64_t)tk * kp.n + gi) * DIM;
+        const int64_t ps = (int64_t)tk + (kp.tape.pos_gap ? (int64_t)(tk / kp.tape.pos_gap) : 0);
+        const int64_t rp = (ps * kp.n + gi) * DIM;
+        kp.tape.pos[rp + 0] = me.x;
+        kp.tape.pos[rp + 1] = me.y;
+        if (DIM == 3) kp.tape.pos[rp + 2] = me.z;
+        kp.tape.F[r + 0] = F.x;
+        kp.tape.F[r + 1] = F.y;
+        if (DIM == 3) kp.tape.F[r + 2] = F.z;
+        kp.tape.S[(int64_t)tk * kp.n + j] = me;
     }
     const unsigned long long step = *kp.step;
 

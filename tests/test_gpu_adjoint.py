@@ -145,3 +145,45 @@ def test_parameter_gradients_3d_match_oracle_finite_differences(over):
     scale = np.abs(fd).max()
     assert scale > 0
     assert np.all(np.abs(g - fd) <= 0.03 * np.abs(fd) + 0.01 * scale), (g, fd)
+
+
+def _segment_bytes(info, n, dim, every):
+    """Device memory of one stored segment, from the layout chemo_record_stored
+    documents (with the allocator's rounding)."""
+    words = info["bin_slots"] // 2 + ((info["bin_slots"] // 8 + 1 + 3) & ~3)
+    return every * (n * (8 * dim + 16) + 4 * info["grid_nodes"] + 4 * words) + n * 4 * dim + 6 * 256
+
+
+@pytest.mark.parametrize("over", [dict(), dict(boundary=1, pde_bc=2, pde_substeps=5, Dc=20.0)])
+def test_stored_segments_give_the_checkpointed_gradient(over):
+    """Segments stored during the record (all of them, or the latest two that
+    fit in a budget) give the gradient of the fully checkpointed run: the
+    stored states are those the re-run computes (to the rounding of the
+    deposit's float atomics)."""
+    p, pos, sp, c0 = _setup(n=1200, **over)
+    nsteps, every = 23, 4  # 6 segments, the last one short
+    dpos = torch.from_numpy(pos).cuda()
+    dsp = torch.from_numpy(sp).cuda()
+    dc0 = torch.from_numpy(c0).cuda()
+    out = []
+    with chemo.chemo_create(p, dpos, dsp) as sim:
+        seg = _segment_bytes(chemo.chemo_get_info(sim), dpos.shape[0], 2, every)
+        for store in (0, -1, 2 * seg + seg // 2):
+            chemo.chemo_write_state(sim, dpos, dsp)
+            chemo.chemo_write_field(sim, dc0)
+            chemo.chemo_set_step_index(sim, 0)
+            chemo.chemo_record(sim, nsteps, every, store_bytes=store)
+            xT = torch.zeros_like(dpos)
+            chemo.chemo_read_state(sim, xT, None, None)
+            g = torch.zeros_like(dpos)
+            g[:, 0] = 1.0 / dpos.shape[0]
+            g[:, 1] = torch.linspace(-1.0, 1.0, dpos.shape[0], device="cuda") / dpos.shape[0]
+            dth = torch.zeros(4, dtype=torch.float32, device="cuda")
+            dx0 = torch.zeros_like(dpos)
+            chemo.chemo_gradient(sim, g, dth, None, dx0)
+            assert chemo.chemo_step_index(sim) == nsteps
+            out.append((xT.cpu().numpy(), dth.cpu().numpy().astype(np.float64), dx0.cpu().numpy().astype(np.float64)))
+    for xT, dth, dx0 in out[1:]:
+        assert np.abs(xT - out[0][0]).max() <= 1e-5
+        np.testing.assert_allclose(dth, out[0][1], rtol=1e-3, atol=1e-6 * np.abs(out[0][1]).max())
+        assert np.abs(dx0 - out[0][2]).max() <= 1e-3 * np.abs(out[0][2]).max() + 1e-9
