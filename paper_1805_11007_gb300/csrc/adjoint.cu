@@ -65,6 +65,8 @@ struct Tape {
     // segments whose states the recorded run stored (pos == NULL: re-run)
     std::vector<SegBuf> stored;
     cudaStream_t s_fwd = nullptr, s_rev = nullptr;
+    cudaStream_t s_pair = nullptr;  // pair term of step k beside the PDE transpose of step k - 1
+    cudaEvent_t ev_cells = nullptr, ev_pairs = nullptr;
     cudaEvent_t ev_ready[2] = {nullptr, nullptr}, ev_done[2] = {nullptr, nullptr};
     cudaEvent_t ev_start = nullptr, ev_fwd_end = nullptr, ev_rev_end = nullptr;
     float *lamX[2] = {nullptr, nullptr};  // n x dim by id
@@ -86,12 +88,14 @@ void chemo_tape_free(chemo_tape *t)
     if (!t) return;
     if (t->s_fwd) cudaStreamSynchronize(t->s_fwd);
     if (t->s_rev) cudaStreamSynchronize(t->s_rev);
+    if (t->s_pair) cudaStreamSynchronize(t->s_pair);
     for (void *p : t->allocs) cudaFree(p);
     for (cudaEvent_t e : {t->ev_ready[0], t->ev_ready[1], t->ev_done[0], t->ev_done[1], t->ev_start, t->ev_fwd_end,
-                          t->ev_rev_end})
+                          t->ev_rev_end, t->ev_cells, t->ev_pairs})
         if (e) cudaEventDestroy(e);
     if (t->s_fwd) cudaStreamDestroy(t->s_fwd);
     if (t->s_rev) cudaStreamDestroy(t->s_rev);
+    if (t->s_pair) cudaStreamDestroy(t->s_pair);
     delete t;
 }
 
@@ -676,6 +680,9 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         ATRY(cudaEventCreateWithFlags(&t->ev_start, cudaEventDisableTiming));
         ATRY(cudaEventCreateWithFlags(&t->ev_fwd_end, cudaEventDisableTiming));
         ATRY(cudaEventCreateWithFlags(&t->ev_rev_end, cudaEventDisableTiming));
+        ATRY(cudaStreamCreateWithFlags(&t->s_pair, cudaStreamNonBlocking));
+        ATRY(cudaEventCreateWithFlags(&t->ev_cells, cudaEventDisableTiming));
+        ATRY(cudaEventCreateWithFlags(&t->ev_pairs, cudaEventDisableTiming));
         for (int k = 0; k < 2; ++k) {
             if ((r = talloc(t, &p, pb))) return r;
             t->lamX[k] = (float *)p;
@@ -758,6 +765,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         if ((r = rerun(t->nseg - 1, t->sb[(t->nseg - 1) & 1]))) return r;
         ATRY(cudaEventRecord(t->ev_ready[(t->nseg - 1) & 1], sf));
     }
+    bool pairs_pending = false;  // a pair term on s_pair that sr has not waited for
     for (int seg = t->nseg - 1; seg >= 0; --seg) {
         const int64_t n0 = (int64_t)seg * t->every;
         const int64_t len = std::min<int64_t>(t->every, t->nsteps - n0);
@@ -805,8 +813,15 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
             kp.cnt_cur = B.cnt + (size_t)k * t->cwords;
             kp.gstart = B.gst + (size_t)k * t->gwords;
             const float *Fk = B.F + (size_t)k * n * dim;
-            // 2-5. per-cell terms, then the pair term
+            // 2-5. per-cell terms, then the pair term; the pair term only adds
+            // to lambda_X^n and reads lambda_Y, so it runs on its own stream
+            // beside the next (earlier) step's PDE transpose, and the next
+            // per-cell kernel (which rewrites lambda_Y) waits for it
             if (n) {
+                if (pairs_pending) {
+                    ATRY(cudaStreamWaitEvent(sr, t->ev_pairs, 0));
+                    pairs_pending = false;
+                }
                 if (dim == 2)
                     k_adj_cells<2><<<blocks(n), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
@@ -817,17 +832,26 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                                                              t->pstride, G ? 1 : 0, kp.pde_multi);
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
+                    cudaStream_t sp2 = t->s_pair;
+                    ATRY(cudaEventRecord(t->ev_cells, sr));
+                    ATRY(cudaStreamWaitEvent(sp2, t->ev_cells, 0));
                     if (dim == 2) {
-                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     } else {
-                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, sr>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     }
                     ATRY(cudaGetLastError());
+                    ATRY(cudaEventRecord(t->ev_pairs, sp2));
+                    pairs_pending = true;
                 }
             }
             lx ^= 1;
+        }
+        if (pairs_pending) {  // the segment's buffer is free once its last pair term is done
+            ATRY(cudaStreamWaitEvent(sr, t->ev_pairs, 0));
+            pairs_pending = false;
         }
         if (!stored) {
             ATRY(cudaEventRecord(t->ev_done[seg & 1], sr));
