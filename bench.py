@@ -91,6 +91,12 @@ def measured_peaks():
 # counted as 2; plus d additions of the negated term to the partner.
 def flop_per_pair(dim: int) -> float:
     return 20.0 + dim
+
+
+# FP32 operations of a candidate distance test that finds no pair (the cell
+# list's candidates of the neighbouring bins, Sect. 3.1): the difference
+# vector (3) and r^2 (5).
+FLOP_PER_TEST = 8.0
 # FP32 lanes of GB300: 152 SMs x 128 lanes, an FMA (2 flop) per lane per cycle.
 FP32_LANES = 152 * 128
 
@@ -558,7 +564,11 @@ def main():
         # the particle kernels are bound by the pair search, not by HBM; the
         # algorithmic work is each unordered in-cutoff pair once (pairs_per_step
         # counts every pair for both of its cells)
-        achieved = flop_per_pair(p["dim"]) * 0.5 * pairs_per_step / (kern[dom] * 1e-3) / 1e12
+        # plus 8 per candidate test that found no pair (counted by the
+        # half-window kernel while profiling)
+        unordered = 0.5 * pairs_per_step
+        rejected = max(prof.get("tests_per_step", 0.0) - unordered, 0.0)
+        achieved = (flop_per_pair(p["dim"]) * unordered + FLOP_PER_TEST * rejected) / (kern[dom] * 1e-3) / 1e12
         half = info["search_mode"] == 4
         roofline = {"kernel": "k_pairs_half + k_step" if half else dom, "bound": "alu", "achieved": achieved,
                     "peak": fp32_peak, "unit": "TFLOP/s",
@@ -572,7 +582,8 @@ def main():
                     "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                     else "fallback 6.8 TB/s"}
     roofline.update({"traffic": NCU_TRAFFIC_BYTES.get(dom), "kernel_ms": kern, "step_ms_profiled": prof["step"],
-                     "profiled_steps": nprof, "pairs_per_step": pairs_per_step})
+                     "profiled_steps": nprof, "pairs_per_step": pairs_per_step,
+                     "tests_per_step": prof.get("tests_per_step")})
     floor_bytes = 42.0 * n + 8.0 * G * s
     step_floor = {"bytes_per_step": floor_bytes, "achieved_GBps": floor_bytes / (ms_per_step * 1e-3) / 1e9,
                   "frac": floor_bytes / (ms_per_step * 1e-3) / 1e9 / hbm}

@@ -279,10 +279,11 @@ int chemo_get_info(const chemo_sim *sim, chemo_info *info);
  * same streams and overlap), with a CUDA event pair around every kernel on
  * the stream it runs on. Returns in kernel_ms[CHEMO_PROF_SLOTS]: the mean
  * device time (ms) per step of the particle kernel, the PDE (all substeps),
- * the scan, the scatter + deposit, and of a whole step; the last slot holds
- * the mean number of in-cutoff pair interactions per step (each ordered
- * pair counted once per cell). Synchronises `stream`. */
-#define CHEMO_PROF_SLOTS 6
+ * the scan, the scatter + deposit, and of a whole step; then the mean number
+ * of in-cutoff pair interactions per step (each ordered pair counted once
+ * per cell) and the mean number of candidate distance tests per step of the
+ * half-window search (0 for the other searches). Synchronises `stream`. */
+#define CHEMO_PROF_SLOTS 7
 int chemo_profile_steps(chemo_sim *sim, int64_t nsteps, float *kernel_ms, void *stream);
 
 /* Releases every resource of sim (NULL is ignored). Synchronises the device

@@ -412,8 +412,8 @@ def chemo_get_info(sim: Sim) -> dict:
             for name, _ in chemo_info._fields_}
 
 
-PROF_SLOTS = 6
-PROF_NAMES = ("k_step", "k_pde", "k_scan", "k_scatter", "step", "pairs_per_step")
+PROF_SLOTS = 7
+PROF_NAMES = ("k_step", "k_pde", "k_scan", "k_scatter", "step", "pairs_per_step", "tests_per_step")
 
 
 def chemo_profile_steps(sim: Sim, nsteps: int, stream=None) -> dict:

@@ -733,6 +733,7 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
     kp.err = ctl + 2;
     kp.step = reinterpret_cast<unsigned long long *>(ctl + 4);
     kp.pair_count = nullptr;  // set only while profiling (ctl + 8)
+    kp.test_count = nullptr;  // set only while profiling (ctl + 10)
     if (replicates > 1) {
         int64_t *lo;
         ALLOC(lo, off.size() * sizeof(int64_t));
@@ -1088,7 +1089,7 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     const bool variants = s->kp.hard_sphere || s->kp.kde;
     // in-cutoff pairs are counted into ctl + 8 while profiling
     unsigned long long *pc = reinterpret_cast<unsigned long long *>(s->kp.tile_ctr + 8);
-    CUDA_TRY(cudaMemsetAsync(pc, 0, sizeof(unsigned long long), st));
+    CUDA_TRY(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));  // pairs, candidate tests
     // event pairs per step: particle, pde, scan, scatter, whole step
     std::vector<cudaEvent_t> ev((size_t)nsteps * 10, nullptr);
     for (auto &e : ev)
@@ -1101,6 +1102,7 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     for (int64_t k = 0; k < nsteps && r == CHEMO_OK; ++k) {
         KP kp = view(s);
         kp.pair_count = pc;
+        kp.test_count = pc + 1;
         cudaEvent_t *e = &ev[(size_t)k * 10];
         cudaError_t err = cudaEventRecord(e[8], st);
         if (fused && !overlap) {
@@ -1158,9 +1160,12 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
             }
         }
         for (int q = 0; q < 5; ++q) kernel_ms[q] = (float)(acc[q] / (double)nsteps);
-        unsigned long long npairs = 0;
-        if (cudaMemcpy(&npairs, pc, sizeof(npairs), cudaMemcpyDeviceToHost) == cudaSuccess)
-            kernel_ms[5] = (float)((double)npairs / (double)nsteps);
+        unsigned long long cnt[2] = {0ull, 0ull};
+        kernel_ms[5] = kernel_ms[6] = 0.f;
+        if (cudaMemcpy(cnt, pc, sizeof(cnt), cudaMemcpyDeviceToHost) == cudaSuccess) {
+            kernel_ms[5] = (float)((double)cnt[0] / (double)nsteps);
+            kernel_ms[6] = (float)((double)cnt[1] / (double)nsteps);
+        }
     }
     for (auto &x : ev) cudaEventDestroy(x);
     return r;

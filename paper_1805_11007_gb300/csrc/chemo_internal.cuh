@@ -117,6 +117,7 @@ struct KP {
     uint32_t *err;               // latched error bits
     unsigned long long *step;    // absolute index of the step being computed
     unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
+    unsigned long long *test_count;  // non-NULL while profiling: candidate tests of the half window
     // adjoint recording (pos == NULL: off): the particle kernel stores, for
     // steps s0 .. s0 + nk - 1 (absolute indices; with period > 0 step s goes
     // to slot (s - s0) mod period, nk = period), the positions before the

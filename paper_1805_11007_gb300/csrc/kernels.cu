@@ -731,6 +731,7 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
     const float rc2_0 = t.rc2[row], rc2_1 = t.rc2[row + 1];
     FAcc F = {0ll, 0ll, 0ll};
     int count = 0, nl = 0, r = 0;
+    uint32_t tests = 0;  // candidates tested (profiling)
     uint32_t q = 0, qe = 0;
     while (q >= qe && r < nr) {
         const uint2 g = rng[r++ * 32];
@@ -744,6 +745,7 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
         // sentinel (no pair), so the chunk ends at the warp's longest
         // (a branch the whole warp takes together)
         const uint32_t m = more ? min((uint32_t)UNROLL, qe - q) : 0u;
+        tests += m;
         const uint32_t mw = __reduce_max_sync(0xffffffffu, m);
         float4 ob[UNROLL];
 #pragma unroll
@@ -781,6 +783,10 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
     if (kp.pair_count) {  // profiling only: each pair found here is an in-cutoff pair of both cells
         const int wsum = __reduce_add_sync(0xffffffffu, count);
         if (lane == 0 && wsum) atomicAdd(kp.pair_count, 2ull * (unsigned long long)wsum);
+    }
+    if (kp.test_count) {  // profiling only: candidates tested
+        const uint32_t tsum = __reduce_add_sync(0xffffffffu, tests);
+        if (lane == 0 && tsum) atomicAdd(kp.test_count, (unsigned long long)tsum);
     }
     if (valid && (F.x | F.y | F.z)) {
         unsigned long long *pf = reinterpret_cast<unsigned long long *>(kp.Fh) + (size_t)j * FS;

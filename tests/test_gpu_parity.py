@@ -462,3 +462,21 @@ def test_half_window_many_steps_fixed_gradient_bitwise():
             chemo.chemo_step_n(sim, 3)
             outs.append(chemo.read_state_host(sim)[0])
     np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_profile_counts_pairs_and_candidate_tests():
+    """The profiling pass counts every in-cutoff pair for both of its cells
+    (the same total for the half and the full window) and, for the half
+    window, the candidates it tested (at least one per pair found)."""
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=20011, grid=[64, 64, 1], chem_mode=1,
+                                  fixed_grad=[1.0, 0.0, 0.0])
+    prof = {}
+    for mode in (3, 4):
+        with make_sim(dict(p, search_mode=mode), pos, sp) as sim:
+            prof[mode] = chemo.chemo_profile_steps(sim, 1)
+    assert prof[3]["pairs_per_step"] == prof[4]["pairs_per_step"] > 0
+    assert prof[3]["tests_per_step"] == 0.0
+    assert prof[4]["tests_per_step"] >= 0.5 * prof[4]["pairs_per_step"]
+    # the half window visits each unordered pair of cells at most once
+    n = pos.shape[0]
+    assert prof[4]["tests_per_step"] <= n * (n - 1) / 2
