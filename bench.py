@@ -103,7 +103,7 @@ FP32_LANES = 152 * 128
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
 # traffic field ("k_step": the particle kernels of one step together); None
 # where a kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": 136.11e6, "k_pde": 93.55e6, "k_scan": 32.79e6, "k_scatter": 53.50e6}
+NCU_TRAFFIC_BYTES = {"k_step": 137.46e6, "k_pde": 93.31e6, "k_scan": 32.75e6, "k_scatter": 53.34e6}
 
 
 # ---------------------------------------------------------------------------
