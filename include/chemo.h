@@ -142,6 +142,11 @@ typedef struct chemo_info {
     int32_t launches_per_step;   /* kernels one chemo_step launches */
     int32_t layers;              /* replicates stacked in the simulation (1 unless
                                     created by chemo_create_batch) */
+    float step_ratio;            /* the time-step rule of thumb (Sect. 3.2): the largest
+                                    sqrt(2 (D_i + D_j) dt) / eps_ij over species pairs
+                                    with eps_ij > 0 (0 if none). Above 1 a step moves
+                                    cells farther than the interaction range; this is
+                                    a warning, not an error */
 } chemo_info;
 
 typedef struct chemo_sim chemo_sim;

@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import warnings
 
 import numpy as np
 
@@ -87,6 +88,7 @@ class chemo_info(ctypes.Structure):
         ("device_bytes", ctypes.c_int64),
         ("launches_per_step", ctypes.c_int32),
         ("layers", ctypes.c_int32),
+        ("step_ratio", ctypes.c_float),
     ]
 
 
@@ -299,7 +301,18 @@ def chemo_create(params: dict, pos, species, stream=None) -> Sim:
     prm = make_params(params)
     _check(lib().chemo_create(ctypes.byref(prm), n, pp, sp, _kind(kp_, ks), _stream(stream), ctypes.byref(out)),
            "chemo_create")
-    return Sim(out, params, n)
+    sim = Sim(out, params, n)
+    _warn_step(sim)
+    return sim
+
+
+def _warn_step(sim):
+    """The paper's time-step rule (Sect. 3.2): a step should move a cell less
+    than the interaction range."""
+    ratio = chemo_get_info(sim)["step_ratio"]
+    if ratio > 1.0:
+        warnings.warn("dt is large for the interaction range: sqrt(2 (D_i + D_j) dt) / eps_ij = %.3g > 1" % ratio,
+                      stacklevel=3)
 
 
 def chemo_create_batch(params: dict, n_per_replicate, pos, species, stream=None) -> Sim:
@@ -313,7 +326,9 @@ def chemo_create_batch(params: dict, n_per_replicate, pos, species, stream=None)
     prm = make_params(params)
     _check(lib().chemo_create_batch(ctypes.byref(prm), int(sizes.size), sizes.ctypes.data, pp, sp, _kind(kp_, ks),
                                     _stream(stream), ctypes.byref(out)), "chemo_create_batch")
-    return Sim(out, params, int(sizes.sum()), sizes.tolist())
+    sim = Sim(out, params, int(sizes.sum()), sizes.tolist())
+    _warn_step(sim)
+    return sim
 
 
 def chemo_autotune(params: dict, n_per_replicate, pos, species, trial_steps: int = 20, stream=None):

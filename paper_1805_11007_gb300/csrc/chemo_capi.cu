@@ -1075,6 +1075,15 @@ int chemo_get_info(const chemo_sim *s, chemo_info *info)
     info->device_bytes = s->bytes;
     info->launches_per_step = s->launches_per_step;
     info->layers = kp.layers;
+    // the paper's rule of thumb for the time step against the interaction range
+    const chemo_params &p = s->prm;
+    double ratio = 0.0;
+    for (int a = 0; a < p.n_species; ++a)
+        for (int b = 0; b < p.n_species; ++b) {
+            const double eps = 0.5 * ((double)p.diameter[a] + (double)p.diameter[b]);
+            if (eps > 0.0) ratio = std::max(ratio, std::sqrt(2.0 * ((double)p.D[a] + (double)p.D[b]) * p.dt) / eps);
+        }
+    info->step_ratio = (float)ratio;
     return CHEMO_OK;
 }
 

@@ -480,3 +480,19 @@ def test_profile_counts_pairs_and_candidate_tests():
     # the half window visits each unordered pair of cells at most once
     n = pos.shape[0]
     assert prof[4]["tests_per_step"] <= n * (n - 1) / 2
+
+
+def test_time_step_rule_is_reported():
+    """The paper's rule of thumb (a step moves a cell less than the
+    interaction range): chemo_info.step_ratio is the largest
+    sqrt(2 (D_i + D_j) dt) / eps_ij, and the binding warns above 1."""
+    p, pos, sp = wl.initial_state("walls_grid_2d", n=2000, grid=[32, 32, 1])
+    want = max(np.sqrt(2.0 * (p["D"][a] + p["D"][b]) * p["dt"]) / (0.5 * (p["diameter"][a] + p["diameter"][b]))
+               for a in range(2) for b in range(2))
+    with pytest.warns(UserWarning, match="dt is large"):
+        sim = make_sim(p, pos, sp)
+    with sim:
+        assert chemo.chemo_get_info(sim)["step_ratio"] == pytest.approx(want, rel=1e-6)
+    q = dict(p, dt=p["dt"] / 100.0)
+    with make_sim(q, pos, sp) as sim:
+        assert chemo.chemo_get_info(sim)["step_ratio"] == pytest.approx(want / 10.0, rel=1e-6)
