@@ -291,6 +291,24 @@ int chemo_get_info(const chemo_sim *sim, chemo_info *info);
 #define CHEMO_PROF_SLOTS 7
 int chemo_profile_steps(chemo_sim *sim, int64_t nsteps, float *kernel_ms, void *stream);
 
+/* Observables of the current state, reduced on the device (the statistics
+ * of Sect. 4). out (mem_kind memory) receives, per replicate (1 unless the
+ * simulation is a batch), 8 x 5 + 1 doubles: for each species slot s < 8 the
+ * number of cells, their mean unwrapped displacement (x, y, z; 0 unless
+ * track_displacement) and mean squared displacement, then the chemical mass
+ * h^d sum_k tau_k c_k (trapezoid weights tau: 1/2 per wall axis at boundary
+ * nodes, 1 on a periodic grid; 0 without a grid). Synchronises `stream` when
+ * mem_kind is HOST. */
+int chemo_observables(chemo_sim *sim, double *out, int mem_kind, void *stream);
+
+/* Occupancy histogram of the cells: the box cut into shape[0] x shape[1]
+ * (x shape[2] in 3D) equal parts (1..4096 per axis); hist_out (mem_kind
+ * memory, float32) receives per replicate and species the count of cells in
+ * each part, C-order [replicate][species][z][y][x] (exact up to 2^24 per
+ * part). Cells on the upper wall count in the last part. Synchronises
+ * `stream` when mem_kind is HOST. EINVAL for a bad shape. */
+int chemo_histogram(chemo_sim *sim, const int32_t *shape, float *hist_out, int mem_kind, void *stream);
+
 /* Releases every resource of sim (NULL is ignored). Synchronises the device
  * work of the simulation first. */
 void chemo_destroy(chemo_sim *sim);

@@ -175,6 +175,8 @@ def _declare(L):
         "chemo_read_field": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_record": ([vp, i64, i32, vp], ctypes.c_int),
         "chemo_record_stored": ([vp, i64, i32, i64, vp], ctypes.c_int),
+        "chemo_observables": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_histogram": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_gradient": ([vp, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_set_params": ([vp, PP], ctypes.c_int),
         "chemo_step_index": ([vp], i64),
@@ -437,6 +439,40 @@ def chemo_profile_steps(sim: Sim, nsteps: int, stream=None) -> dict:
     out = (ctypes.c_float * PROF_SLOTS)()
     _check(lib().chemo_profile_steps(_h(sim), int(nsteps), out, _stream(stream)), "chemo_profile_steps")
     return {PROF_NAMES[i]: float(out[i]) for i in range(PROF_SLOTS)}
+
+
+OBS_PER_LAYER = 8 * 5 + 1
+
+
+def chemo_observables(sim: Sim, stream=None) -> list:
+    """Observables of the current state reduced on the device, one dict per
+    replicate: cells per species, mean displacement (n_species, 3) and mean
+    squared displacement per species (0 unless track_displacement), and the
+    chemical mass (trapezoid rule over the grid)."""
+    layers = sim.replicates
+    out = np.zeros(layers * OBS_PER_LAYER, np.float64)
+    _check(lib().chemo_observables(_h(sim), out.ctypes.data, MEM_HOST, _stream(stream)), "chemo_observables")
+    ns = int(sim.params["n_species"])
+    res = []
+    for layer in range(layers):
+        v = out[layer * OBS_PER_LAYER:(layer + 1) * OBS_PER_LAYER]
+        per = v[:40].reshape(8, 5)[:ns]
+        res.append({"count": per[:, 0].copy(), "mean_disp": per[:, 1:4].copy(), "msd": per[:, 4].copy(),
+                    "c_mass": float(v[40])})
+    return res
+
+
+def chemo_histogram(sim: Sim, shape, stream=None) -> np.ndarray:
+    """Cells per part of the box cut into shape (per axis), per replicate and
+    species: float32 array [replicate][species][z][y][x] (no z in 2D)."""
+    dim = int(sim.dim)
+    sh = [int(x) for x in shape][:dim] + [1] * (3 - dim)
+    layers = sim.replicates
+    ns = int(sim.params["n_species"])
+    out = np.zeros([layers, ns] + list(reversed(sh[:dim])), np.float32)
+    s3 = (ctypes.c_int32 * 3)(*sh)
+    _check(lib().chemo_histogram(_h(sim), s3, out.ctypes.data, MEM_HOST, _stream(stream)), "chemo_histogram")
+    return out
 
 
 def chemo_destroy(sim: Sim):

@@ -587,6 +587,7 @@ int eng_fail(int status, const char *fmt, ...)
     return status;
 }
 int eng_dalloc(chemo_sim *s, void **p, size_t bytes) { return dalloc(s, p, bytes); }
+int eng_scratch(chemo_sim *s, size_t bytes, void **p) { return scratch(s, bytes, p); }
 KP eng_view(const chemo_sim *s) { return view(s); }
 int eng_enqueue_step(chemo_sim *s, cudaStream_t st, int *launches) { return enqueue_step(s, st, launches); }
 int eng_ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp, int mem_kind, cudaStream_t st)

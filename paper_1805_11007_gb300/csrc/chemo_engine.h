@@ -37,6 +37,8 @@ struct chemo_sim {
 // Engine services used by adjoint.cu (implemented in chemo_capi.cu).
 int eng_fail(int status, const char *fmt, ...);
 int eng_dalloc(chemo_sim *s, void **p, size_t bytes);
+// Device scratch of at least `bytes` owned by the simulation (reused by every call).
+int eng_scratch(chemo_sim *s, size_t bytes, void **p);
 KP eng_view(const chemo_sim *s);
 int eng_enqueue_step(chemo_sim *s, cudaStream_t st, int *launches);
 int eng_ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp, int mem_kind, cudaStream_t st);
