@@ -556,6 +556,7 @@ extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *s
 
 extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, int64_t store_bytes, void *stream)
 {
+    ChemoRange nvtx_range("chemo_record_stored");
     if (!s || nsteps < 0 || every < 1) return eng_fail(CHEMO_EINVAL, "chemo_record: bad arguments");
     if (int r = check_adjoint_model(s)) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -640,6 +641,7 @@ extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, 
 extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
                               float *dL_dpos0, int mem_kind, void *stream)
 {
+    ChemoRange nvtx_range("chemo_gradient");
     if (!s) return eng_fail(CHEMO_EINVAL, "sim is NULL");
     chemo_tape *t = s->tape;
     if (!t) return eng_fail(CHEMO_EINVAL, "chemo_gradient: no recorded run (call chemo_record first)");

@@ -656,12 +656,14 @@ void chemo_destroy(chemo_sim *s)
 int chemo_create(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species, int mem_kind,
                  void *stream, chemo_sim **out)
 {
+    ChemoRange nvtx_range("chemo_create");
     return chemo_create_batch(params, 1, &n, pos, species, mem_kind, stream, out);
 }
 
 int chemo_create_batch(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
                        const float *pos, const uint8_t *species, int mem_kind, void *stream, chemo_sim **out)
 {
+    ChemoRange nvtx_range("chemo_create_batch");
     g_last_error[0] = 0;
     if (!params || !out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and out are required");
     *out = nullptr;
@@ -817,6 +819,7 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
                    const float *pos, const uint8_t *species, int mem_kind, int32_t trial_steps, void *stream,
                    chemo_params *best_out, float *best_ms_out)
 {
+    ChemoRange nvtx_range("chemo_autotune");
     g_last_error[0] = 0;
     if (!params || !best_out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and best_out are required");
     if (trial_steps < 1) return fail(CHEMO_EINVAL, "trial_steps must be >= 1");
@@ -896,6 +899,7 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
 int chemo_write_state(chemo_sim *s, const float *pos, const uint8_t *species, const float *disp, int mem_kind,
                       void *stream)
 {
+    ChemoRange nvtx_range("chemo_write_state");
     g_last_error[0] = 0;
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
@@ -918,6 +922,7 @@ int chemo_write_field(chemo_sim *s, const float *c, int mem_kind, void *stream)
 
 int chemo_step(chemo_sim *s, void *stream)
 {
+    ChemoRange nvtx_range("chemo_step");
     g_last_error[0] = 0;
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     return enqueue_step(s, (cudaStream_t)stream, nullptr);
@@ -925,6 +930,7 @@ int chemo_step(chemo_sim *s, void *stream)
 
 int chemo_step_n(chemo_sim *s, int64_t nsteps, void *stream)
 {
+    ChemoRange nvtx_range("chemo_step_n");
     g_last_error[0] = 0;
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (nsteps < 0) return fail(CHEMO_EINVAL, "nsteps < 0");
@@ -966,6 +972,7 @@ int chemo_step_n(chemo_sim *s, int64_t nsteps, void *stream)
 
 int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *disp_out, int mem_kind, void *stream)
 {
+    ChemoRange nvtx_range("chemo_read_state");
     g_last_error[0] = 0;
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
@@ -1090,6 +1097,7 @@ int chemo_get_info(const chemo_sim *s, chemo_info *info)
 
 int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *stream)
 {
+    ChemoRange nvtx_range("chemo_profile_steps");
     g_last_error[0] = 0;
     if (!s || !kernel_ms || nsteps <= 0) return fail(CHEMO_EINVAL, "bad arguments");
     cudaStream_t st = (cudaStream_t)stream;

@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <vector>
 
@@ -13,6 +14,15 @@
 using chemo::KP;
 
 struct chemo_tape;  // recorded run (adjoint.cu)
+
+// Named range of a library call for timeline profilers (NVTX; a no-op unless
+// a profiler is attached).
+struct ChemoRange {
+    explicit ChemoRange(const char *name) { nvtxRangePushA(name); }
+    ~ChemoRange() { nvtxRangePop(); }
+    ChemoRange(const ChemoRange &) = delete;
+    ChemoRange &operator=(const ChemoRange &) = delete;
+};
 
 struct chemo_sim {
     chemo_params prm{};

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(OTPB) k_histogram(KP kp, int hx, int hy, int h
 
 extern "C" int chemo_observables(chemo_sim *s, double *out, int mem_kind, void *stream)
 {
+    ChemoRange nvtx_range("chemo_observables");
     if (!s || !out) return eng_fail(CHEMO_EINVAL, "sim and out are required");
     if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE) return eng_fail(CHEMO_EINVAL, "bad mem_kind");
     cudaStream_t st = (cudaStream_t)stream;
@@ -179,6 +180,7 @@ extern "C" int chemo_observables(chemo_sim *s, double *out, int mem_kind, void *
 
 extern "C" int chemo_histogram(chemo_sim *s, const int32_t *shape, float *hist_out, int mem_kind, void *stream)
 {
+    ChemoRange nvtx_range("chemo_histogram");
     if (!s || !shape || !hist_out) return eng_fail(CHEMO_EINVAL, "sim, shape and hist_out are required");
     if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE) return eng_fail(CHEMO_EINVAL, "bad mem_kind");
     const KP kp = eng_view(s);
