@@ -348,15 +348,31 @@ def test_host_buffers_round_trip():
         sim.close()
 
 
-def test_bad_device_input_is_latched():
+@pytest.mark.parametrize("fault", ["nan", "outside", "species"])
+def test_bad_device_input_is_latched(fault):
+    """Device-side checks of the input (the host cannot see device buffers):
+    a non-finite position, a position outside the box and a species value
+    out of range are latched, reported once by chemo_check, and the state
+    stays usable (clamped to the box, species 0)."""
     p = wl.params("walls_grid_2d", grid=[33, 33, 1])
     pos = np.full((10, 2), 0.5, np.float32)
-    pos[3, 0] = np.nan
-    with make_sim(p, pos, np.zeros(10, np.uint8)) as sim:
+    sp = np.zeros(10, np.uint8)
+    want = {"nan": chemo.ENONFINITE, "outside": chemo.EDOMAIN, "species": chemo.EINVAL}[fault]
+    if fault == "nan":
+        pos[3, 0] = np.nan
+    elif fault == "outside":
+        pos[3, 1] = 1.5
+    else:
+        sp[4] = 7
+    with make_sim(p, pos, sp) as sim:
         with pytest.raises(chemo.ChemoError) as ei:
             chemo.chemo_check(sim)
-        assert ei.value.status == chemo.ENONFINITE
+        assert ei.value.status == want
         chemo.chemo_check(sim)  # cleared
+        x, s, _ = chemo.read_state_host(sim)
+        assert np.isfinite(x).all() and (x >= 0).all() and (x <= 1).all() and (s < 2).all()
+        chemo.chemo_step_n(sim, 3)
+        chemo.chemo_check(sim)
 
 
 def test_set_params_changes_model_constants():
