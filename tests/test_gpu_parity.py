@@ -512,3 +512,20 @@ def test_time_step_rule_is_reported():
     q = dict(p, dt=p["dt"] / 100.0)
     with make_sim(q, pos, sp) as sim:
         assert chemo.chemo_get_info(sim)["step_ratio"] == pytest.approx(want / 10.0, rel=1e-6)
+
+
+def test_time_step_rule_of_the_paper_figure():
+    """Fig. 1 of the paper picks dt = (0.23 epsilon)^2 / (4 D_beta)
+    (tests/golden/paper_parameters.txt): its step moves a beta cell 0.23 of
+    the interaction range, the largest ratio over the species pairs."""
+    gold = {}
+    for line in open(__file__.replace("test_gpu_parity.py", "golden/paper_parameters.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()[:2]
+            gold[k] = float(v)
+    eps, dt = gold["fig1_epsilon"], gold["fig1_dt"]
+    p = wl.params("walls_grid_2d", grid=[32, 32, 1], diameter=[eps, eps], D=[gold["fig1_D_alpha"], gold["fig1_D_beta"]],
+                  dt=dt)
+    pos = np.random.default_rng(3).uniform(0.1, 0.9, (500, 2)).astype(np.float32)
+    with make_sim(p, pos, wl.half_species(500, 2)) as sim:
+        assert chemo.chemo_get_info(sim)["step_ratio"] == pytest.approx(0.23, rel=2e-3)
