@@ -257,9 +257,11 @@ int chemo_record_stored(chemo_sim *sim, int64_t nsteps, int32_t every, int64_t s
  * cutoff jump and the reflection kinks are not differentiated (measure-zero
  * events). dL/dinter is 0 when inter = 0 (no pair force, no cell list for
  * its cutoff). Memory: two segments' states, fields, sorted states, cell
- * lists and pair forces of `every` steps each. The simulation is left at the
- * final state of the recorded run. Synchronises `stream` when mem_kind is
- * HOST. EINVAL if no run is recorded. */
+ * lists and pair forces of `every` steps each (segments kept by
+ * chemo_record_stored are not re-run). The simulation is left at the final
+ * state and step index of the recorded run, whatever was stepped after the
+ * record. Synchronises `stream` when mem_kind is HOST. EINVAL if no run is
+ * recorded. */
 int chemo_gradient(chemo_sim *sim, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
                    float *dL_dpos0, int mem_kind, void *stream);
 

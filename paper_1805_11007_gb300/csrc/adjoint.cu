@@ -717,7 +717,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
     // the pair force is linear in inter: dF/dinter = F / inter (the cell list
     // is not built for the cutoff when inter = 0, and dL/dinter is then 0)
     const float f_unit = s->prm.inter != 0.f ? 1.f / s->prm.inter : 0.f;
-    const int64_t end_step = s->step;
+    const int64_t end_step = t->step0 + t->nsteps;  // the recorded run's final step index
     // restores segment seg's checkpoint and re-runs it on sf, storing its states in B
     // (the particle kernel writes the states into buffer seg mod 2 through
     // the periodic tape, so chemo_step_n replays its graphs for every re-run)

@@ -108,6 +108,15 @@ def test_record_leaves_final_state_and_gradient_restores_it():
         np.testing.assert_array_equal(pa2, pa)
         assert chemo.chemo_step_index(a) == 10
         assert torch.isfinite(dth).all()
+        # steps taken after the record do not change what the gradient
+        # restores: the recorded run's final state and step index
+        chemo.chemo_step_n(a, 4)
+        dth2 = torch.zeros(4, dtype=torch.float32, device="cuda")
+        chemo.chemo_gradient(a, g, dth2)
+        pa3, _, _ = chemo.read_state_host(a)
+        np.testing.assert_array_equal(pa3, pa)
+        assert chemo.chemo_step_index(a) == 10
+        torch.testing.assert_close(dth2, dth, rtol=1e-4, atol=1e-6 * float(dth.abs().max()))
 
 
 @pytest.mark.parametrize("over", [dict(), dict(boundary=1, pde_bc=2), dict(pde_substeps=3, Dc=5.0)])
