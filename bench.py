@@ -390,6 +390,12 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
         if dist is not None:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
+        # the ensemble's statistics at the end of the run, reduced on the
+        # device per replicate and gathered from every rank (the one exchange
+        # of a sharded ensemble; outside the timed region)
+        obs = chemo.chemo_observables(sim, stream=stream)
+        rows = np.array([np.concatenate([o["count"], o["msd"], [o["c_mass"]]]) for o in obs], np.float64)
+        allrows = en.gather_replicates(rows, sizes, world, rank, dist.all_gather_object if dist is not None else None)
         reset()
         prof = chemo.chemo_profile_steps(sim, 50, stream=stream)
         info = chemo.chemo_get_info(sim)
@@ -402,7 +408,10 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
            "launches_per_step": info["launches_per_step"],
            "autotuned": {"search_mode": p["search_mode"], "bin_side": p["bin_side"], "warp_runs": p["warp_runs"],
                          "pde_overlap": p["pde_overlap"], "trial_ms_per_step": tuned_ms, "tuning_s": tune_s},
-           "kernel_ms": {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")}}
+           "kernel_ms": {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")},
+           "observables": {"how": "chemo_observables per replicate after the timed run, gathered from every rank",
+                           "cells": float(allrows[:, :2].sum()), "replicates": int(allrows.shape[0]),
+                           "mean_c_mass": float(allrows[:, -1].mean())}}
     if rank == 0:
         # the same replicates one simulation at a time (each with its own
         # CUDA graphs), for the batching gain

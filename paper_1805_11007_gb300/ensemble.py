@@ -6,7 +6,9 @@ Replicates are independent, so an ensemble shards across ranks with no data
 exchange: each rank creates one batched simulation (``chemo_create_batch``)
 of its own replicates. ``shard_replicates`` balances the particle count per
 rank (largest replicate first onto the least-loaded rank; ties by rank), the
-same on every rank, so no communication is needed to agree on it.
+same on every rank, so no communication is needed to agree on it. The one
+exchange is at the end: ``gather_replicates`` all-gathers each rank's
+per-replicate rows (observables) into the global replicate order.
 """
 from __future__ import annotations
 
@@ -48,3 +50,30 @@ def take(pos, sp, sizes, reps):
     sizes = np.asarray(sizes, dtype=np.int64)
     idx = np.concatenate([np.arange(off[r], off[r + 1]) for r in reps]) if len(reps) else np.zeros(0, np.int64)
     return sizes[list(reps)], np.ascontiguousarray(pos[idx]), np.ascontiguousarray(sp[idx])
+
+
+def gather_replicates(local_rows, sizes, world: int, rank: int, all_gather_object=None) -> np.ndarray:
+    """Rows of every replicate in global replicate order, on every rank:
+    `local_rows` holds one row per replicate of this rank's shard (in the
+    shard's order, shard_replicates(sizes, world)[rank]); the shards' rows
+    are exchanged with one all-gather (``all_gather_object`` of a process
+    group, e.g. torch.distributed's; None with world == 1)."""
+    shards = shard_replicates(sizes, world)
+    local_rows = np.asarray(local_rows)
+    if local_rows.shape[0] != len(shards[rank]):
+        raise ValueError("one row per replicate of this rank's shard is required")
+    if world == 1:
+        parts = [local_rows]
+    else:
+        if all_gather_object is None:
+            raise ValueError("a process group's all_gather_object is required for world > 1")
+        parts = [None] * world
+        all_gather_object(parts, local_rows)
+    out = None
+    for reps, rows in zip(shards, parts):
+        rows = np.asarray(rows)
+        if out is None:
+            out = np.zeros((len(np.asarray(sizes).reshape(-1)),) + rows.shape[1:], rows.dtype)
+        if len(reps):
+            out[np.asarray(reps)] = rows
+    return out

@@ -75,3 +75,46 @@ def test_split_and_take_roundtrip():
     s2, p2, sp2 = en.take(pos, sp, sizes, [2, 0])
     assert s2.tolist() == [5, 3]
     np.testing.assert_array_equal(p2, np.concatenate([parts[2], parts[0]]))
+
+
+def _gather_worker(rank, world, port, sizes, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = en.shard_replicates(sizes, world)[rank]
+        # stand-in observables of this rank's replicates: (replicate, size, rank)
+        rows = np.array([[r, sizes[r], rank] for r in mine], dtype=np.float64).reshape(-1, 3)
+        allr = en.gather_replicates(rows, sizes, world, rank, dist.all_gather_object)
+        q.put((rank, allr))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_gather_replicates_in_global_order():
+    """The final exchange of a sharded ensemble: every rank ends with every
+    replicate's row, in global replicate order, from the rank that ran it."""
+    _, sizes, _, _ = wl.ensemble_state(replicates=37)
+    sizes = sizes.tolist()
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_gather_worker, args=(r, world, port, sizes, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    shards = en.shard_replicates(sizes, world)
+    owner = {r: k for k, s in enumerate(shards) for r in s}
+    for rank in range(world):
+        rows = got[rank]
+        assert rows.shape == (len(sizes), 3)
+        np.testing.assert_array_equal(rows[:, 0], np.arange(len(sizes)))
+        np.testing.assert_array_equal(rows[:, 1], np.asarray(sizes, np.float64))
+        np.testing.assert_array_equal(rows[:, 2], [owner[r] for r in range(len(sizes))])
+    # one rank: no process group needed
+    one = en.gather_replicates(np.arange(len(sizes))[:, None], sizes, 1, 0)
+    np.testing.assert_array_equal(one[:, 0], np.arange(len(sizes)))
