@@ -332,6 +332,19 @@ const char *chemo_last_error(void);
 int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, int mem_kind,
                  void *stream);
 
+/* Initial state of the paper's experiments (Sect. 3), drawn on the device:
+ * cells i < n_alpha are species 0 (alpha), normal around the box centre with
+ * standard deviation sigma_frac x the box width per axis (0.1 in the paper),
+ * put inside by the box's boundary rule (reflection, or wrap when periodic);
+ * cells i >= n_alpha are species 1 (beta), uniform in the box. Cell i uses the
+ * Philox4x32-10 words of counter (i, 0, 3, 0) under the key params->seed:
+ * Box-Muller on (w0, w1) and (w2, w3) for alpha, u = (w_a + 1/2) 2^-32 per
+ * axis for beta. Writes pos_out (n x dim float32) and species_out (n uint8)
+ * in memory of mem_kind (HOST: synchronises `stream`). EINVAL for bad sizes,
+ * sigma_frac <= 0, or beta cells with n_species < 2. */
+int chemo_init_positions(const chemo_params *params, int64_t n, int64_t n_alpha, float sigma_frac, float *pos_out,
+                         uint8_t *species_out, int mem_kind, void *stream);
+
 /* Row a1: the bin cell of every particle, n x dim int32 (cell coordinates
  * per axis, not the Morton key). */
 int chemo_stage_bins(chemo_sim *sim, int32_t *cells_out, int mem_kind, void *stream);

@@ -27,6 +27,7 @@ _lib = None
 MAXS = 8
 TAG_MOVE = 0
 TAG_REACT = 2
+TAG_INIT = 3
 
 
 def build(force: bool = False) -> str:
@@ -193,6 +194,42 @@ def philox(ctr, seed: int) -> np.ndarray:
     out = np.zeros_like(ctr)
     lib().orc_philox_batch(ctr.shape[0], _ptr(ctr), int(seed) & (2**64 - 1), _ptr(out))
     return out
+
+
+def init_positions(params: dict, n: int, n_alpha: int, sigma_frac: float = 0.1):
+    """The paper's initial state (Sect. 3: alpha cells start normal around the
+    centre of the domain with sigma = 0.1 of its width, beta cells uniform),
+    in FP64 from the same Philox words as the device: cell i takes the words
+    of counter (i, 0, TAG_INIT, 0) under the key seed, u = (w + 1/2) 2^-32.
+    Alpha (i < n_alpha, species 0): Box-Muller on (u0, u1) and (u2, u3) gives
+    g, x = centre + sigma_frac L g, put inside by reflection at the walls or
+    by wrapping on a periodic box. Beta (species 1): x = lo + u_a L per axis.
+    Returns (pos (n, dim) float64, species (n,) uint8)."""
+    dim = int(params["dim"])
+    lo = np.asarray(params["lo"], np.float64)[:dim]
+    hi = np.asarray(params["hi"], np.float64)[:dim]
+    L = hi - lo
+    periodic = int(params.get("boundary", 0)) == 1
+    ctr = np.zeros((int(n), 4), np.uint32)
+    ctr[:, 0] = np.arange(int(n), dtype=np.uint32)
+    ctr[:, 2] = TAG_INIT
+    w = philox(ctr, int(params["seed"])).astype(np.float64)
+    u = (w + 0.5) / 2.0 ** 32
+    r01 = np.sqrt(-2.0 * np.log(u[:, 0]))
+    r23 = np.sqrt(-2.0 * np.log(u[:, 2]))
+    g = np.stack([r01 * np.cos(2.0 * np.pi * u[:, 1]), r01 * np.sin(2.0 * np.pi * u[:, 1]),
+                  r23 * np.cos(2.0 * np.pi * u[:, 3])], axis=1)[:, :dim]
+    alpha = np.arange(int(n)) < int(n_alpha)
+    pos = np.where(alpha[:, None], 0.5 * (lo + hi) + sigma_frac * L * g, lo + u[:, :dim] * L)
+    for a in range(dim):
+        x = pos[:, a]
+        if periodic:
+            x = lo[a] + np.mod(x - lo[a], L[a])
+        else:
+            for _ in range(16):  # reflect until inside (a triangle wave)
+                x = np.where(x < lo[a], 2.0 * lo[a] - x, np.where(x > hi[a], 2.0 * hi[a] - x, x))
+        pos[:, a] = x
+    return pos, np.where(alpha, 0, 1).astype(np.uint8)
 
 
 def normals(seed: int, ids, step: int, tag: int = TAG_MOVE) -> np.ndarray:

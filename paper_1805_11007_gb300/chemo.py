@@ -176,6 +176,7 @@ def _declare(L):
         "chemo_record": ([vp, i64, i32, vp], ctypes.c_int),
         "chemo_record_stored": ([vp, i64, i32, i64, vp], ctypes.c_int),
         "chemo_observables": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_init_positions": ([vp, i64, i64, ctypes.c_float, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_histogram": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_gradient": ([vp, vp, vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_set_params": ([vp, PP], ctypes.c_int),
@@ -439,6 +440,24 @@ def chemo_profile_steps(sim: Sim, nsteps: int, stream=None) -> dict:
     out = (ctypes.c_float * PROF_SLOTS)()
     _check(lib().chemo_profile_steps(_h(sim), int(nsteps), out, _stream(stream)), "chemo_profile_steps")
     return {PROF_NAMES[i]: float(out[i]) for i in range(PROF_SLOTS)}
+
+
+def chemo_init_positions(params: dict, n: int, n_alpha: int, sigma_frac: float = 0.1, pos_out=None,
+                         species_out=None, stream=None):
+    """The paper's initial state drawn on the device (alpha normal around the
+    centre, beta uniform). Fills pos_out (n, dim) float32 and species_out (n,)
+    uint8 (host or device); allocates host arrays when they are None."""
+    dim = int(params["dim"])
+    if pos_out is None:
+        pos_out = np.zeros((int(n), dim), np.float32)
+    if species_out is None:
+        species_out = np.zeros(int(n), np.uint8)
+    pp, k1, _a = _buf(pos_out, np.float32)
+    sp, k2, _b = _buf(species_out, np.uint8)
+    prm = make_params(params)
+    _check(lib().chemo_init_positions(ctypes.byref(prm), int(n), int(n_alpha), float(sigma_frac), pp, sp,
+                                      _kind(k1, k2), _stream(stream)), "chemo_init_positions")
+    return pos_out, species_out
 
 
 OBS_PER_LAYER = 8 * 5 + 1

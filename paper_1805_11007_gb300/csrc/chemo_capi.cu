@@ -1212,6 +1212,40 @@ int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, i
     return CHEMO_OK;
 }
 
+int chemo_init_positions(const chemo_params *params, int64_t n, int64_t n_alpha, float sigma_frac, float *pos_out,
+                         uint8_t *species_out, int mem_kind, void *stream)
+{
+    g_last_error[0] = 0;
+    ChemoRange nvtx_range("chemo_init_positions");
+    if (!params) return fail(CHEMO_EINVAL, "params is required");
+    if (int r = check_params(*params)) return r;
+    if (n < 0 || n > (int64_t)ID_MASK + 1 || n_alpha < 0 || n_alpha > n)
+        return fail(CHEMO_EINVAL, "need 0 <= n_alpha <= n <= 2^29");
+    if (params->n_species < 2 && n_alpha < n) return fail(CHEMO_EINVAL, "beta cells need n_species >= 2");
+    if (!(sigma_frac > 0.f) || !std::isfinite(sigma_frac)) return fail(CHEMO_EINVAL, "sigma_frac must be > 0");
+    if (n > 0 && (!pos_out || !species_out)) return fail(CHEMO_EINVAL, "pos_out and species_out are required");
+    if (int r = check_mem_kind(mem_kind)) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mem_kind == CHEMO_MEM_DEVICE) {
+        CUDA_TRY(launch_init_positions(params->dim, params->boundary == 1, params->lo, params->hi, params->seed, n,
+                                       n_alpha, sigma_frac, pos_out, species_out, st));
+        return CHEMO_OK;
+    }
+    const size_t pb = (size_t)n * params->dim * sizeof(float);
+    void *d = nullptr;
+    CUDA_TRY(cudaMalloc(&d, pb + (size_t)n + 64));
+    float *dp = (float *)d;
+    uint8_t *ds = (uint8_t *)d + ((pb + 15) & ~(size_t)15);
+    cudaError_t e = launch_init_positions(params->dim, params->boundary == 1, params->lo, params->hi, params->seed, n,
+                                          n_alpha, sigma_frac, dp, ds, st);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(pos_out, dp, pb, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && n) e = cudaMemcpyAsync(species_out, ds, (size_t)n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(CHEMO_ECUDA, "init_positions: %s", cudaGetErrorString(e));
+    return CHEMO_OK;
+}
+
 // Stage entry points: results land in device scratch, then go to the caller.
 static int stage_out(chemo_sim *s, void *dst, const void *src, size_t bytes, int mem_kind, cudaStream_t st)
 {

@@ -25,6 +25,7 @@ enum : uint32_t {
 // Philox stream tags (third counter word).
 constexpr uint32_t TAG_MOVE = 0u;
 constexpr uint32_t TAG_REACT = 2u;
+constexpr uint32_t TAG_INIT = 3u;   // initial positions (chemo_init_positions)
 
 // Kernel parameter block, passed by value to every kernel.
 struct KP {
@@ -347,6 +348,8 @@ cudaError_t launch_pde_multi(const KP &kp, const float *cin, float *cout, int ns
                              int avg_first, float avg_scale, int tau_mode, cudaStream_t st);
 cudaError_t launch_unsort(const KP &kp, float *pos, uint8_t *sp, float *disp, cudaStream_t st);
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, cudaStream_t st);
+cudaError_t launch_init_positions(int dim, int periodic, const double *lo, const double *hi, uint64_t seed, int64_t n,
+                                  int64_t n_alpha, float sigma_frac, float *pos, uint8_t *sp, cudaStream_t st);
 cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st);
 cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, uint32_t *bin_starts, cudaStream_t st);
 cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned long long *idsum,

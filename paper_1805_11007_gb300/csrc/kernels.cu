@@ -1886,6 +1886,44 @@ __global__ void k_philox(uint32_t seed_lo, uint32_t seed_hi, const uint4 *__rest
     if (i < n) out[i] = philox4x32_10(ctr[i], seed_lo, seed_hi);
 }
 
+// Initial state of the paper's experiments (Sect. 3): cell i < n_alpha is
+// species 0 (alpha), drawn from a normal distribution centred in the box with
+// standard deviation sigma_frac x the box width per axis and put inside by
+// the box's boundary rule (reflection or wrap); the other cells are species
+// 1 (beta), uniform in the box. Philox words of counter (i, 0, TAG_INIT, 0)
+// under the key (seed lo, seed hi); Box-Muller as for the move's noise.
+__global__ void k_init_positions(int dim, int periodic, float3 lo3, float3 hi3, int64_t n, int64_t n_alpha,
+                                 float sigma_frac, uint32_t k0, uint32_t k1, float *__restrict__ pos,
+                                 uint8_t *__restrict__ sp)
+{
+    const int64_t i = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    if (i >= n) return;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)i, 0u, TAG_INIT, 0u), k0, k1);
+    const float lo[3] = {lo3.x, lo3.y, lo3.z}, hi[3] = {hi3.x, hi3.y, hi3.z};
+    const bool alpha = i < n_alpha;
+    float g[3] = {0.f, 0.f, 0.f};
+    if (alpha) {
+        const float2 a = box_muller(w.x, w.y);
+        g[0] = a.x;
+        g[1] = a.y;
+        g[2] = box_muller(w.z, w.w).x;
+    }
+    const uint32_t ws[3] = {w.x, w.y, w.z};
+    for (int a = 0; a < dim; ++a) {
+        const float L = hi[a] - lo[a];
+        float x;
+        if (alpha) {
+            x = fmaf(sigma_frac * L, g[a], 0.5f * (lo[a] + hi[a]));
+            x = periodic ? wrap_axis(x, lo[a], hi[a], L) : reflect_axis(x, lo[a], hi[a]);
+        } else {
+            x = fmaf(word_uniform(ws[a]), L, lo[a]);
+            if (periodic && x >= hi[a]) x = lo[a];
+        }
+        pos[i * dim + a] = x;
+    }
+    sp[i] = alpha ? 0 : 1;
+}
+
 __global__ void k_stage_bins(KP kp, int32_t *__restrict__ cells)
 {
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
@@ -2213,6 +2251,17 @@ cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int
     if (n == 0) return cudaSuccess;
     k_philox<<<blocks_for(n), TPB, 0, st>>>((uint32_t)seed, (uint32_t)(seed >> 32),
                                             reinterpret_cast<const uint4 *>(ctr), reinterpret_cast<uint4 *>(out), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_positions(int dim, int periodic, const double *lo_d, const double *hi_d, uint64_t seed, int64_t n,
+                                  int64_t n_alpha, float sigma_frac, float *pos, uint8_t *sp, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const float3 lo = make_float3((float)lo_d[0], (float)lo_d[1], (float)lo_d[2]);
+    const float3 hi = make_float3((float)hi_d[0], (float)hi_d[1], (float)hi_d[2]);
+    k_init_positions<<<blocks_for(n), TPB, 0, st>>>(dim, periodic, lo, hi, n, n_alpha, sigma_frac, (uint32_t)seed,
+                                                    (uint32_t)(seed >> 32), pos, sp);
     return cudaGetLastError();
 }
 

@@ -529,3 +529,27 @@ def test_time_step_rule_of_the_paper_figure():
     pos = np.random.default_rng(3).uniform(0.1, 0.9, (500, 2)).astype(np.float32)
     with make_sim(p, pos, wl.half_species(500, 2)) as sim:
         assert chemo.chemo_get_info(sim)["step_ratio"] == pytest.approx(0.23, rel=2e-3)
+
+
+@pytest.mark.parametrize("dim,boundary", [(2, 0), (2, 1), (3, 0)])
+def test_init_positions_match_oracle(dim, boundary):
+    """The paper's initial state drawn on the device (chemo_init_positions)
+    against the oracle's FP64 draw from the same Philox words: species
+    exactly, positions within the single-precision Box-Muller error."""
+    p = wl.params("walls_grid_2d" if dim == 2 else "clumps_grid_3d", boundary=boundary,
+                  pde_bc=2 if boundary else 0, seed=21)
+    n, na = 30011, 12001
+    pos_h, sp_h = chemo.chemo_init_positions(p, n, na, 0.1)           # host buffers
+    pos_d = torch.zeros((n, dim), dtype=torch.float32, device="cuda")
+    sp_d = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    chemo.chemo_init_positions(p, n, na, 0.1, pos_d, sp_d)             # device buffers
+    np.testing.assert_array_equal(pos_d.cpu().numpy(), pos_h)
+    np.testing.assert_array_equal(sp_d.cpu().numpy(), sp_h)
+    ref, sref = orc.init_positions(p, n, na, 0.1)
+    np.testing.assert_array_equal(sp_h, sref)
+    L = max(p["hi"][a] - p["lo"][a] for a in range(dim))
+    assert np.abs(pos_h.astype(np.float64) - ref).max() <= 2e-6 * L
+    # and it is a valid state for a simulation
+    with make_sim(p, pos_h, sp_h) as sim:
+        chemo.chemo_step(sim)
+        chemo.chemo_check(sim)
