@@ -11,18 +11,23 @@ with Neumann walls, starting from c = 0; dt = 5e-5, 400 steps. The
 diameters are 4x the paper's so that dt can be 5x its value with the step
 still shorter than the interaction range (the paper's rule of Sect. 3).
 
-Observables of one run at the end (a vector of 2 x 7 + 3 numbers): for each
-species the fraction of its cells in the radial shells |x - centre| in
+Observables of one run (a vector of 2 x 7 + 2 x 4 + 1 = 23 numbers): for
+each species the fraction of its cells in the radial shells |x - centre| in
 [0, 0.1), [0.1, 0.15), [0.15, 0.2), [0.2, 0.3), [0.3, 0.4), [0.4, 0.5),
-[0.5, inf); the mean squared displacement of each species; c at the centre
-node.
+[0.5, inf) at the end; the mean squared displacement curve of each species
+(after 100, 200, 300 and 400 steps); c at the centre node at the end.
 
 Comparison of two sets of independent runs (different noise streams, the
 same initial state): for each observable z = (mean_B - mean_A) /
 (s_A sqrt(1/R_A + 1/R_B)), s_A the standard deviation over the R_A runs of
 set A (floored at one cell's share for the shell fractions). Two samples of
-the same law keep every |z| below Z_MAX = 6 (17 observables: a false alarm
-has a probability of about 1e-7 when the means are normal).
+the same law keep every |z| below Z_MAX = 6 (23 observables: a false alarm
+has a probability of about 5e-8 when the means are normal). A family-wise
+level of 0.01 (Bonferroni over the 23) would put the band at 3.5; every GPU
+run is a new sample (the float atomics of the deposit round in a different
+order each time), so the band is set where a run of the same law practically
+never leaves it, and the planted mistakes of the calibration land at
+|z| >= 2 Z_MAX.
 """
 from __future__ import annotations
 
@@ -34,6 +39,7 @@ from paper_1805_11007_gb300 import workloads as wl
 N_CELLS = 2000
 N_ALPHA = 1000
 STEPS = 400
+CHUNKS = 4  # points of the MSD curves, STEPS // CHUNKS steps apart
 EDGES = np.array([0.0, 0.1, 0.15, 0.2, 0.3, 0.4, 0.5, np.inf])
 Z_MAX = 6.0
 
@@ -48,20 +54,23 @@ def params(dim: int, **overrides) -> dict:
     return p
 
 
-def observables(pos0, pos, species, c) -> np.ndarray:
-    """Observable vector of one run: shell fractions per species, mean squared
-    displacement per species, c at the centre node."""
+def observables(pos0, traj, species, c) -> np.ndarray:
+    """Observable vector of one run from the initial positions, the positions
+    after each chunk of steps (the last is the end state), the species and
+    the final field: shell fractions per species at the end, the MSD curve
+    per species, c at the centre node."""
     pos0 = np.asarray(pos0, np.float64)
-    pos = np.asarray(pos, np.float64)
     species = np.asarray(species)
-    r = np.linalg.norm(pos - 0.5, axis=1)
+    end = np.asarray(traj[-1], np.float64)
+    r = np.linalg.norm(end - 0.5, axis=1)
     out = []
     for s in (0, 1):
         h, _ = np.histogram(r[species == s], EDGES)
         out += list(h / max(1, int((species == s).sum())))
     for s in (0, 1):
-        d = pos[species == s] - pos0[species == s]
-        out.append(float((d * d).sum(axis=1).mean()))
+        for x in traj:
+            d = np.asarray(x, np.float64)[species == s] - pos0[species == s]
+            out.append(float((d * d).sum(axis=1).mean()))
     c = np.asarray(c, np.float64)
     out.append(float(c[tuple(k // 2 for k in c.shape)]))
     return np.array(out)
@@ -73,17 +82,22 @@ def floors(n_species_cells) -> np.ndarray:
     f = []
     for m in n_species_cells:
         f += [1.0 / max(1, int(m))] * (len(EDGES) - 1)
-    return np.array(f + [0.0, 0.0, 0.0])
+    return np.array(f + [0.0] * (2 * CHUNKS + 1))
 
 
 def oracle_runs(p: dict, pos0, species, seeds, steps: int = STEPS) -> np.ndarray:
     """Observable vectors of FP64 oracle runs, one per noise seed."""
     shape = orc.grid_shape(p)
+    per = steps // CHUNKS
     rows = []
     for s in seeds:
         q = dict(p, seed=int(s))
-        pos, sp, c, _ = orc.run(q, pos0, species, c=np.zeros(shape), nsteps=steps)
-        rows.append(observables(pos0, pos, sp, c))
+        pos, sp, c = pos0, species, np.zeros(shape)
+        traj = []
+        for k in range(CHUNKS):
+            pos, sp, c, _ = orc.run(q, pos, sp, c=c, step0=k * per, nsteps=per)
+            traj.append(pos)
+        rows.append(observables(pos0, traj, sp, c))
     return np.array(rows)
 
 

@@ -2,7 +2,7 @@
 steps of the aggregation set-up of Sect. 3 (alpha cells secreting at the
 centre, beta cells climbing the gradient, soft repulsion, the chemical on a
 grid with walls), the radial profiles of both species, their mean squared
-displacements and c at the centre agree between 64 GPU runs and 8 oracle
+displacement curves and c at the centre agree between 64 GPU runs and 8 oracle
 runs with other noise seeds: every observable's oracle mean lies within
 Z_MAX = 6 standard errors of the GPU mean, the standard error taken from the
 spread of the GPU runs. The initial state is drawn on each side by its own
@@ -42,15 +42,17 @@ def test_ensemble_2d_long_run_matches_oracle_statistics():
     p = su.params(2, seed=1000)  # replicate r runs with key 1000 + r
     pos0, sp = chemo.chemo_init_positions(dict(p, seed=INIT_SEED), su.N_CELLS, su.N_ALPHA)
     sizes = [su.N_CELLS] * R_GPU
+    traj = []
     with chemo.chemo_create_batch(p, sizes, dev(np.tile(pos0, (R_GPU, 1))), dev(np.tile(sp, R_GPU))) as sim:
-        chemo.chemo_step_n(sim, su.STEPS)
-        x, s, _ = chemo.read_state_host(sim)
+        for _ in range(su.CHUNKS):
+            chemo.chemo_step_n(sim, su.STEPS // su.CHUNKS)
+            x, s, _ = chemo.read_state_host(sim)
+            assert np.all((x >= 0.0) & (x <= 1.0))
+            traj.append(x.reshape(R_GPU, su.N_CELLS, 2))
         c = chemo.read_field_host(sim)
-    assert np.all((x >= 0.0) & (x <= 1.0))
-    x = x.reshape(R_GPU, su.N_CELLS, 2)
     s = s.reshape(R_GPU, su.N_CELLS)
     assert np.all(s == sp[None, :])
-    A = np.array([su.observables(pos0, x[r], s[r], c[r]) for r in range(R_GPU)])
+    A = np.array([su.observables(pos0, [x[r] for x in traj], s[r], c[r]) for r in range(R_GPU)])
     _compare(2, A, sp)
 
 
@@ -59,10 +61,13 @@ def test_single_runs_3d_long_run_match_oracle_statistics():
     pos0, sp = chemo.chemo_init_positions(dict(p, seed=INIT_SEED), su.N_CELLS, su.N_ALPHA)
     rows = []
     for r in range(R_GPU):
+        traj = []
         with chemo.chemo_create(dict(p, seed=1000 + r), dev(pos0), dev(sp)) as sim:
-            chemo.chemo_step_n(sim, su.STEPS)
-            x, s, _ = chemo.read_state_host(sim)
+            for _ in range(su.CHUNKS):
+                chemo.chemo_step_n(sim, su.STEPS // su.CHUNKS)
+                x, s, _ = chemo.read_state_host(sim)
+                assert np.all((x >= 0.0) & (x <= 1.0))
+                traj.append(x)
             c = chemo.read_field_host(sim)
-        assert np.all((x >= 0.0) & (x <= 1.0))
-        rows.append(su.observables(pos0, x, s, c))
+        rows.append(su.observables(pos0, traj, s, c))
     _compare(3, np.array(rows), sp)
