@@ -35,6 +35,7 @@ def _compare(dim, A, sp):
     B = _oracle(dim)
     z = su.zscores(A, B, su.floors([(sp == 0).sum(), (sp == 1).sum()]))
     assert np.all(np.isfinite(z)), np.round(z, 2)
+    print(f"dim {dim}: largest |z| {np.abs(z).max():.2f} over {z.size} observables")
     assert np.abs(z).max() < su.Z_MAX, (dim, np.round(z, 2), np.round(A.mean(0), 4), np.round(B.mean(0), 4))
 
 
