@@ -40,6 +40,7 @@
 #ifndef CHEMO_H
 #define CHEMO_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -314,6 +315,26 @@ int chemo_histogram(chemo_sim *sim, const int32_t *shape, float *hist_out, int m
 /* Releases every resource of sim (NULL is ignored). Synchronises the device
  * work of the simulation first. */
 void chemo_destroy(chemo_sim *sim);
+
+/* Device memory source (plumbing; no counterpart in the paper). Every device
+ * buffer of the library (a simulation's state, cell list, grids and scratch,
+ * a recorded run's tape, the temporaries of chemo_philox and
+ * chemo_init_positions) is allocated once, outside the step, and comes from
+ * cudaMalloc unless an allocator is set here. alloc(ctx, bytes, &ptr) returns
+ * 0 and a device pointer of the current device aligned to 256 bytes, or
+ * non-zero on failure (the call that needed the memory then returns ENOMEM
+ * and releases what it had taken); release(ctx, ptr, bytes) takes back a
+ * pointer with the size it was allocated with. The library calls release only
+ * after the work that used the buffer has finished on the device. Both
+ * callbacks are called from the thread of the library call, never inside a
+ * stream capture or a kernel. The setting is process-wide and read when a
+ * simulation is created (or a temporary is needed): a simulation keeps the
+ * allocator it was created with until chemo_destroy. alloc and release are
+ * both set or both NULL (NULL, NULL restores cudaMalloc / cudaFree).
+ * Errors: EINVAL if exactly one of them is NULL. Touches no GPU. */
+typedef int (*chemo_alloc_fn)(void *ctx, size_t bytes, void **ptr);
+typedef void (*chemo_release_fn)(void *ctx, void *ptr, size_t bytes);
+int chemo_set_allocator(chemo_alloc_fn alloc, chemo_release_fn release, void *ctx);
 
 /* Static text of a status code. */
 const char *chemo_status_string(int status);

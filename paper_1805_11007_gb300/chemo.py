@@ -145,6 +145,11 @@ def make_params(d: dict) -> chemo_params:
 
 _lib = None
 
+# Callbacks of chemo_set_allocator: int alloc(ctx, bytes, void **ptr) and
+# void release(ctx, ptr, bytes).
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p))
+RELEASE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t)
+
 
 def lib():
     """The loaded library (raises if it was not built)."""
@@ -195,6 +200,7 @@ def _declare(L):
         "chemo_stage_drift": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_deposit": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_forces_noalloc": ([PP, i64, vp, vp, vp, vp], ctypes.c_int),
+        "chemo_set_allocator": ([vp, vp, vp], ctypes.c_int),  # callbacks as pointers (NULL allowed)
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -578,3 +584,58 @@ def read_field_host(sim: Sim):
     c = np.zeros(shape, np.float32)
     chemo_read_field(sim, c)
     return c
+
+
+_allocator = None  # the callbacks in force
+_retired = []      # earlier callbacks: simulations created under them release through them
+
+
+def chemo_set_allocator(alloc=None, release=None):
+    """Device buffers of simulations created from now on (and the temporaries
+    of chemo_philox / chemo_init_positions) come from alloc(nbytes) -> int
+    device pointer (0 or an exception: failure, the call raises ENOMEM) and go
+    back through release(ptr, nbytes) once the device is done with them. A
+    simulation keeps the allocator it was created with. None, None restores
+    cudaMalloc / cudaFree."""
+    global _allocator
+    if (alloc is None) != (release is None):
+        raise ValueError("alloc and release are both given or both None")
+    if alloc is None:
+        _check(lib().chemo_set_allocator(None, None, None), "chemo_set_allocator")
+        if _allocator is not None:
+            _retired.append(_allocator)
+        _allocator = None
+        return
+
+    def _alloc(ctx, nbytes, out):
+        try:
+            ptr = int(alloc(int(nbytes)) or 0)
+        except Exception:
+            return 1
+        if ptr == 0:
+            return 1
+        out[0] = ptr
+        return 0
+
+    def _release(ctx, ptr, nbytes):
+        if ptr:
+            try:
+                release(int(ptr), int(nbytes))
+            except Exception:
+                pass
+
+    cb = (ALLOC_FN(_alloc), RELEASE_FN(_release))
+    _check(lib().chemo_set_allocator(ctypes.cast(cb[0], ctypes.c_void_p), ctypes.cast(cb[1], ctypes.c_void_p), None),
+           "chemo_set_allocator")
+    if _allocator is not None:
+        _retired.append(_allocator)
+    _allocator = cb
+
+
+def use_torch_allocator():
+    """Backs the library's device buffers by PyTorch's caching allocator (on
+    the current device and stream at each allocation)."""
+    import torch
+
+    chemo_set_allocator(lambda nbytes: torch.cuda.caching_allocator_alloc(nbytes),
+                        lambda ptr, nbytes: torch.cuda.caching_allocator_delete(ptr))

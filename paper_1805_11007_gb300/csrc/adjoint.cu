@@ -55,7 +55,8 @@ struct SegBuf {
 struct Tape {
     int64_t n = 0, G = 0, nsteps = 0, every = 0, step0 = 0;
     int nseg = 0, dim = 0, ns = 0;
-    std::vector<void *> allocs;
+    DevMem mem;  // the simulation's allocator
+    std::vector<DevBuf> allocs;
     std::vector<float *> ck_pos, ck_c;  // checkpoints: positions by id (n x dim), field
     uint8_t *species = nullptr;         // species by id
     // two segment buffers: segment s - 1 is re-run into one while the
@@ -89,7 +90,7 @@ void chemo_tape_free(chemo_tape *t)
     if (t->s_fwd) cudaStreamSynchronize(t->s_fwd);
     if (t->s_rev) cudaStreamSynchronize(t->s_rev);
     if (t->s_pair) cudaStreamSynchronize(t->s_pair);
-    for (void *p : t->allocs) cudaFree(p);
+    for (const DevBuf &b : t->allocs) eng_mem_release(t->mem, b.ptr, b.bytes);
     for (cudaEvent_t e : {t->ev_ready[0], t->ev_ready[1], t->ev_done[0], t->ev_done[1], t->ev_start, t->ev_fwd_end,
                           t->ev_rev_end, t->ev_cells, t->ev_pairs})
         if (e) cudaEventDestroy(e);
@@ -103,14 +104,9 @@ namespace {
 
 int talloc(chemo_tape *t, void **p, size_t bytes)
 {
-    bytes = (bytes + 255) & ~(size_t)255;
-    if (bytes == 0) bytes = 256;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return eng_fail(CHEMO_ENOMEM, "adjoint: cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
-    t->allocs.push_back(*p);
+    size_t b = 0;
+    if (int r = eng_mem_alloc(t->mem, p, bytes, &b)) return r;
+    t->allocs.push_back({*p, b});
     return CHEMO_OK;
 }
 
@@ -564,6 +560,7 @@ extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, 
     s->tape = new (std::nothrow) chemo_tape();
     if (!s->tape) return eng_fail(CHEMO_ENOMEM, "host allocation failed");
     chemo_tape *t = s->tape;
+    t->mem = s->mem;
     const KP &kp = s->kp;
     t->n = kp.n;
     t->G = kp.has_grid ? kp.G : 0;

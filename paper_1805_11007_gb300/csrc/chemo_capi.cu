@@ -9,7 +9,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -47,18 +49,15 @@ __global__ void k_set_u64(unsigned long long *p, unsigned long long v) { *p = v;
 
 namespace {
 
+std::mutex g_alloc_mu;
+DevMem g_alloc;  // the setting of chemo_set_allocator, guarded by g_alloc_mu
+
 int dalloc(chemo_sim *s, void **p, size_t bytes)
 {
-    *p = nullptr;
-    if (bytes == 0) bytes = 16;
-    bytes = (bytes + 255) & ~(size_t)255;
-    cudaError_t e = cudaMalloc(p, bytes);
-    if (e != cudaSuccess) {
-        *p = nullptr;
-        return fail(CHEMO_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
-    }
-    s->allocs.push_back(*p);
-    s->bytes += (int64_t)bytes;
+    size_t b = 0;
+    if (int r = eng_mem_alloc(s->mem, p, bytes, &b)) return r;
+    s->allocs.push_back({*p, b});
+    s->bytes += (int64_t)b;
     return CHEMO_OK;
 }
 
@@ -68,17 +67,13 @@ int scratch(chemo_sim *s, size_t bytes, void **out)
         if (s->scratch) {
             cudaError_t e = cudaDeviceSynchronize();
             if (e != cudaSuccess) return fail(CHEMO_ECUDA, "sync: %s", cudaGetErrorString(e));
-            cudaFree(s->scratch);
+            eng_mem_release(s->mem, s->scratch, s->scratch_bytes);
             s->bytes -= (int64_t)s->scratch_bytes;
             s->scratch = nullptr;
             s->scratch_bytes = 0;
         }
-        size_t b = (bytes + 255) & ~(size_t)255;
-        cudaError_t e = cudaMalloc(&s->scratch, b);
-        if (e != cudaSuccess) {
-            s->scratch = nullptr;
-            return fail(CHEMO_ENOMEM, "cudaMalloc(%zu) failed: %s", b, cudaGetErrorString(e));
-        }
+        size_t b = 0;
+        if (int r = eng_mem_alloc(s->mem, &s->scratch, bytes, &b)) return r;
         s->scratch_bytes = b;
         s->bytes += (int64_t)b;
     }
@@ -587,6 +582,61 @@ int eng_fail(int status, const char *fmt, ...)
     return status;
 }
 int eng_dalloc(chemo_sim *s, void **p, size_t bytes) { return dalloc(s, p, bytes); }
+
+DevMem eng_allocator()
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    return g_alloc;
+}
+
+int eng_mem_alloc(const DevMem &m, void **p, size_t bytes, size_t *rounded)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (rounded) *rounded = bytes;
+    if (m.alloc) {
+        void *q = nullptr;
+        const int rc = m.alloc(m.ctx, bytes, &q);
+        if (rc != 0 || !q)
+            return fail(CHEMO_ENOMEM, "the allocator given to chemo_set_allocator failed for %zu bytes (status %d)",
+                        bytes, rc);
+        if (reinterpret_cast<uintptr_t>(q) & 255u) {
+            m.release(m.ctx, q, bytes);
+            return fail(CHEMO_ENOMEM, "the allocator given to chemo_set_allocator returned a pointer not aligned "
+                                      "to 256 bytes");
+        }
+        *p = q;
+        return CHEMO_OK;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(CHEMO_ENOMEM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return CHEMO_OK;
+}
+
+void eng_mem_release(const DevMem &m, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (m.release)
+        m.release(m.ctx, p, bytes);
+    else
+        cudaFree(p);
+}
+
+int chemo_set_allocator(chemo_alloc_fn alloc, chemo_release_fn release, void *ctx)
+{
+    g_last_error[0] = 0;
+    if ((alloc == nullptr) != (release == nullptr))
+        return fail(CHEMO_EINVAL, "alloc and release are both set or both NULL");
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    g_alloc.alloc = alloc;
+    g_alloc.release = release;
+    g_alloc.ctx = alloc ? ctx : nullptr;
+    return CHEMO_OK;
+}
 int eng_scratch(chemo_sim *s, size_t bytes, void **p) { return scratch(s, bytes, p); }
 KP eng_view(const chemo_sim *s) { return view(s); }
 int eng_enqueue_step(chemo_sim *s, cudaStream_t st, int *launches) { return enqueue_step(s, st, launches); }
@@ -644,8 +694,8 @@ void chemo_destroy(chemo_sim *s)
     cudaDeviceSynchronize();
     drop_graphs(s);
     chemo_tape_free(s->tape);
-    for (void *p : s->allocs) cudaFree(p);
-    if (s->scratch) cudaFree(s->scratch);
+    for (const DevBuf &b : s->allocs) eng_mem_release(s->mem, b.ptr, b.bytes);
+    eng_mem_release(s->mem, s->scratch, s->scratch_bytes);
     if (s->aux) cudaStreamDestroy(s->aux);
     if (s->cap) cudaStreamDestroy(s->cap);
     if (s->ev_fork) cudaEventDestroy(s->ev_fork);
@@ -683,6 +733,7 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
         return fail(CHEMO_EINVAL, "mem_kind is DEVICE but pos/species are not device pointers");
     chemo_sim *s = new (std::nothrow) chemo_sim();
     if (!s) return fail(CHEMO_ENOMEM, "host allocation failed");
+    s->mem = eng_allocator();
     s->prm = *params;
     KP &kp = s->kp;
     kp.n = n;
@@ -1200,14 +1251,17 @@ int chemo_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, i
         return CHEMO_OK;
     }
     const size_t bytes = (size_t)n * 16;
+    const DevMem mem = eng_allocator();
     void *d = nullptr;
-    CUDA_TRY(cudaMalloc(&d, 2 * bytes + 32));
+    size_t db = 0;
+    if (int r = eng_mem_alloc(mem, &d, 2 * bytes + 32, &db)) return r;
     uint32_t *dc = (uint32_t *)d, *dout = (uint32_t *)((char *)d + bytes);
     cudaError_t e = cudaMemcpyAsync(dc, ctr, bytes, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_philox(seed, dc, dout, n, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, bytes, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d);
+    const cudaError_t es = cudaStreamSynchronize(st);  // the buffer is idle before it goes back
+    if (e == cudaSuccess) e = es;
+    eng_mem_release(mem, d, db);
     if (e != cudaSuccess) return fail(CHEMO_ECUDA, "philox: %s", cudaGetErrorString(e));
     return CHEMO_OK;
 }
@@ -1232,16 +1286,19 @@ int chemo_init_positions(const chemo_params *params, int64_t n, int64_t n_alpha,
         return CHEMO_OK;
     }
     const size_t pb = (size_t)n * params->dim * sizeof(float);
+    const DevMem mem = eng_allocator();
     void *d = nullptr;
-    CUDA_TRY(cudaMalloc(&d, pb + (size_t)n + 64));
+    size_t db = 0;
+    if (int r = eng_mem_alloc(mem, &d, pb + (size_t)n + 64, &db)) return r;
     float *dp = (float *)d;
     uint8_t *ds = (uint8_t *)d + ((pb + 15) & ~(size_t)15);
     cudaError_t e = launch_init_positions(params->dim, params->boundary == 1, params->lo, params->hi, params->seed, n,
                                           n_alpha, sigma_frac, dp, ds, st);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(pos_out, dp, pb, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && n) e = cudaMemcpyAsync(species_out, ds, (size_t)n, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d);
+    const cudaError_t es = cudaStreamSynchronize(st);  // the buffer is idle before it goes back
+    if (e == cudaSuccess) e = es;
+    eng_mem_release(mem, d, db);
     if (e != cudaSuccess) return fail(CHEMO_ECUDA, "init_positions: %s", cudaGetErrorString(e));
     return CHEMO_OK;
 }

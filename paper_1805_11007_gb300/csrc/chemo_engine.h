@@ -24,6 +24,20 @@ struct ChemoRange {
     ChemoRange &operator=(const ChemoRange &) = delete;
 };
 
+// Source of device buffers: the allocator given to chemo_set_allocator, or
+// cudaMalloc / cudaFree when both callbacks are NULL.
+struct DevMem {
+    chemo_alloc_fn alloc = nullptr;
+    chemo_release_fn release = nullptr;
+    void *ctx = nullptr;
+};
+
+// A device buffer with the size it was allocated with.
+struct DevBuf {
+    void *ptr;
+    size_t bytes;
+};
+
 struct chemo_sim {
     chemo_params prm{};
     KP kp{};
@@ -36,7 +50,8 @@ struct chemo_sim {
     cudaStream_t cap = nullptr;  // capture stream for graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph[2][2][2] = {};  // [2-step, 16-step][grid parity][count parity]
-    std::vector<void *> allocs;
+    DevMem mem;                  // the allocator in force at creation
+    std::vector<DevBuf> allocs;
     int64_t bytes = 0;
     void *scratch = nullptr;     // staging for host transfers and stage outputs
     size_t scratch_bytes = 0;
@@ -46,6 +61,14 @@ struct chemo_sim {
 
 // Engine services used by adjoint.cu (implemented in chemo_capi.cu).
 int eng_fail(int status, const char *fmt, ...);
+// The process-wide allocator setting now.
+DevMem eng_allocator();
+// bytes (rounded up to 256) of device memory from m; CHEMO_OK or CHEMO_ENOMEM
+// with the last error set. *p is NULL on failure; *rounded gets the size
+// release must be given.
+int eng_mem_alloc(const DevMem &m, void **p, size_t bytes, size_t *rounded);
+// Gives back a buffer of eng_mem_alloc (p may be NULL).
+void eng_mem_release(const DevMem &m, void *p, size_t bytes);
 int eng_dalloc(chemo_sim *s, void **p, size_t bytes);
 // Device scratch of at least `bytes` owned by the simulation (reused by every call).
 int eng_scratch(chemo_sim *s, size_t bytes, void **p);

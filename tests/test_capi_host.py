@@ -66,6 +66,23 @@ def test_struct_layouts_match_ctypes(chemo, tmp_path):
         assert getattr(cls, name).offset == int(off), name
 
 
+def test_allocator_setting_checks_its_arguments(chemo):
+    """chemo_set_allocator takes both callbacks or neither, and touches no
+    GPU (the setting is read at the next allocation)."""
+    L = chemo.lib()
+    fa = chemo.ALLOC_FN(lambda ctx, nbytes, out: 1)
+    fr = chemo.RELEASE_FN(lambda ctx, ptr, nbytes: None)
+    only_alloc, only_release = ctypes.cast(fa, ctypes.c_void_p), ctypes.cast(fr, ctypes.c_void_p)
+    assert L.chemo_set_allocator(only_alloc, None, None) == chemo.EINVAL
+    assert "both" in L.chemo_last_error().decode()
+    assert L.chemo_set_allocator(None, only_release, None) == chemo.EINVAL
+    with pytest.raises(ValueError):
+        chemo.chemo_set_allocator(lambda nbytes: 0, None)
+    chemo.chemo_set_allocator(lambda nbytes: 0, lambda ptr, nbytes: None)
+    chemo.chemo_set_allocator(None, None)
+    assert L.chemo_set_allocator(None, None, None) == chemo.OK
+
+
 def test_status_strings(chemo):
     assert chemo.chemo_status_string(0) == "ok"
     assert "invalid" in chemo.chemo_status_string(chemo.EINVAL)
