@@ -194,6 +194,38 @@ def test_pde_periodic_fourier_mode_decay():
     np.testing.assert_allclose(out - 2.0, fac * (c - 2.0), atol=1e-12)
 
 
+@pytest.mark.parametrize("dim,bc", [(2, 0), (3, 0), (2, 2), (3, 2)])
+def test_pde_separable_mode_on_every_axis(dim, bc):
+    """A product of one eigenmode per axis on a grid whose spacing differs by
+    axis decays by 1 - dt_s (gamma + sum_a 4 D_c / h_a^2 sin^2(theta_a / 2)),
+    theta_a = pi m_a h_a / L_a (Neumann cosine) or 2 pi m_a / N_a (periodic):
+    every axis's stencil and spacing enter, so a wrong h, a dropped axis or a
+    transposed index shows."""
+    grid = [13, 9, 7][:dim] + [1] * (3 - dim)
+    over = dict(dim=dim, grid=grid, Dc=0.7, gamma=0.15, dt=2e-5)
+    if bc == 2:
+        over.update(pde_bc=2, boundary=1)
+    p = wl.params("walls_grid_2d", **over)
+    X = _nodes(p)
+    m = [2, 1, 3][:dim]
+    c = np.ones(orc.grid_shape(p))
+    lam = 0.0
+    for a in range(dim):
+        h = orc.grid_h(p, a)
+        L = p["hi"][a] - p["lo"][a]
+        if bc == 2:
+            c = c * np.cos(2 * np.pi * m[a] * (X[a] - p["lo"][a]) / L)
+            theta = 2 * np.pi * m[a] / grid[a]
+        else:
+            c = c * np.cos(np.pi * m[a] * (X[a] - p["lo"][a]) / L)
+            theta = np.pi * m[a] * h / L
+        lam += 4 * float(np.float32(0.7)) / h ** 2 * np.sin(theta / 2) ** 2
+    s = 3
+    fac = 1 - p["dt"] / s * (float(np.float32(0.15)) + lam)
+    out = orc.pde_substep(p, c, None, None, s)
+    np.testing.assert_allclose(out, fac * c, rtol=0, atol=1e-12)
+
+
 def test_pde_uniform_decay():
     p = wl.params("clumps_grid_3d", grid=[9, 9, 9], gamma=0.1)
     c = np.full(orc.grid_shape(p), 3.0)
