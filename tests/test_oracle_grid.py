@@ -93,6 +93,44 @@ def test_multilinear_field_gradient_and_value_exact(dim):
     np.testing.assert_allclose(v, field(*[pos[:, a] for a in range(dim)]), rtol=1e-10, atol=1e-10)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_periodic_grid_gradient_wraps(dim):
+    """Periodic grid (nodes k h, h = L/N): the central difference of a
+    Fourier mode at every node, the wrapped ones included, is the derivative
+    of the mode times sin(k h)/(k h) (for sin(k x): cos(k x_j) sin(k h)/h),
+    and a cell in the last interval [L - h, L) interpolates between node N-1
+    and node 0. Checked at random positions and in the last interval of
+    every axis."""
+    grid = [16, 12, 8][:dim] + [1] * (3 - dim)
+    p = wl.params("walls_grid_2d", dim=dim, grid=grid, boundary=1, pde_bc=2, chi=1.3, chemotactic=[0.0, 1.0])
+    X = _nodes(p)
+    m = [1, 2, 1][:dim]
+    kappa = [2 * np.pi * m[a] for a in range(dim)]
+    # c = sin(k0 x) + cos(k1 y) (+ sin(k2 z))
+    c = np.sin(kappa[0] * X[0]) + np.cos(kappa[1] * X[1]) + (np.sin(kappa[2] * X[2]) if dim == 3 else 0.0)
+    h = [orc.grid_h(p, a) for a in range(dim)]
+
+    def node_grad(a, j):  # central difference at node j of axis a, in closed form
+        x = j * h[a]
+        s = np.sin(kappa[a] * h[a]) / h[a]
+        return -np.sin(kappa[a] * x) * s if a == 1 else np.cos(kappa[a] * x) * s
+
+    rng = np.random.default_rng(3)
+    pos = rng.random((300, dim))
+    for a in range(dim):  # cells in the last interval of axis a
+        pos[a * 20:(a + 1) * 20, a] = 1.0 - h[a] * rng.random(20)
+    pos = pos.astype(np.float32).astype(np.float64)
+    d = orc.drift(p, pos, np.ones(len(pos), np.uint8), c)
+    chi = float(np.float32(1.3))
+    for i in range(len(pos)):
+        for a in range(dim):
+            u = pos[i, a] / h[a]
+            k = int(np.floor(u))
+            f = u - k
+            expect = (1 - f) * node_grad(a, k % grid[a]) + f * node_grad(a, (k + 1) % grid[a])
+            assert abs(d[i, a] - chi * expect) <= 1e-9 * max(1.0, abs(chi * expect)), (i, a, d[i, a], chi * expect)
+
+
 def test_wall_node_gradient_is_zero_normal_component():
     p = wl.params("walls_grid_2d", grid=[11, 11, 1])
     X = _nodes(p)
