@@ -11,6 +11,8 @@ Eq. (1d) (Sect. 3.5).
   Fourier modes, uniform decay, and exact discrete steady states with
   Dirichlet ends (linear profile; A r1^k + B r2^k with decay).
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -302,7 +304,8 @@ def test_pde_dirichlet_decay_steady_state():
 
 
 def test_substeps_match_stability_rule():
-    rows = [l.split() for l in open("tests/golden/substeps.txt") if l.strip() and not l.startswith("#")]
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "substeps.txt")
+    rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
     for name, dim, N, Dc, dt, _lam, s in rows:
         p = wl.params(name)
         assert p["dim"] == int(dim) and p["grid"][0] == int(N)
