@@ -12,9 +12,11 @@ The library must have been built (``paper_1805_11007_gb300.build.build()`` or
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
 import warnings
+import weakref
 
 import numpy as np
 
@@ -265,10 +267,13 @@ def _kind(*kinds):
 
 
 class Sim:
-    """Owned handle of a simulation (chemo_destroy on close / garbage)."""
+    """Owned handle of a simulation (chemo_destroy on close / garbage; the
+    ones still open at interpreter exit are closed while Python callbacks
+    of chemo_set_allocator can still run)."""
 
     def __init__(self, handle, params: dict, n: int, sizes=None):
         self.handle = handle
+        _open_sims.add(self)
         self.params = dict(params)
         self.n = int(n)
         self.dim = int(params["dim"])
@@ -292,6 +297,18 @@ class Sim:
 
     def __exit__(self, *a):
         self.close()
+
+
+_open_sims = weakref.WeakSet()
+
+
+@atexit.register
+def _close_open_sims():
+    for sim in list(_open_sims):
+        try:
+            sim.close()
+        except Exception:
+            pass
 
 
 def _h(sim):
