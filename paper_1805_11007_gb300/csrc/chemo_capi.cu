@@ -550,11 +550,11 @@ int ingest(chemo_sim *s, const float *pos, const uint8_t *sp, const float *disp,
     const size_t pbytes = (size_t)n * d * sizeof(float);
     const size_t sbytes = ((size_t)n + 255) & ~(size_t)255;
     if (mem_kind == CHEMO_MEM_HOST) {
-        void *tmp;
+        void *tmp = nullptr;
         int r = scratch(s, 2 * pbytes + sbytes + 512, &tmp);
         if (r) return r;
     }
-    void *dpos, *dsp, *ddisp = nullptr;
+    void *dpos = nullptr, *dsp = nullptr, *ddisp = nullptr;
     int r = copy_in(s, pos, pbytes, mem_kind, st, 0, &dpos);
     if (r) return r;
     r = copy_in(s, sp, (size_t)n, mem_kind, st, (pbytes + 255) & ~(size_t)255, &dsp);
@@ -1035,7 +1035,7 @@ int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *
     if (mem_kind == CHEMO_MEM_DEVICE) {
         CUDA_TRY(launch_unsort(view(s), pos_out, species_out, disp_out, st));
     } else {
-        void *tmp;
+        void *tmp = nullptr;
         if (int r = scratch(s, 2 * pb + (size_t)n + 256, &tmp)) return r;
         char *b = (char *)tmp;
         float *dp = pos_out ? (float *)b : nullptr;
@@ -1329,7 +1329,7 @@ int chemo_stage_bins(chemo_sim *s, int32_t *cells_out, int mem_kind, void *strea
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(int32_t);
-    void *tmp;
+    void *tmp = nullptr;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
     CUDA_TRY(launch_stage_bins(view(s), (int32_t *)tmp, st));
     if (int r = stage_out(s, cells_out, tmp, bytes, mem_kind, st)) return r;
@@ -1343,7 +1343,7 @@ int chemo_stage_sort(chemo_sim *s, uint32_t *ids_out, uint32_t *bin_start_out, i
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)s->kp.n * sizeof(uint32_t);
-    void *tmp;
+    void *tmp = nullptr;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
     if (ids_out) {
         CUDA_TRY(launch_stage_sort(view(s), (uint32_t *)tmp, nullptr, st));
@@ -1370,7 +1370,7 @@ int chemo_stage_forces(chemo_sim *s, float *F_out, int32_t *count_out, uint64_t 
     const size_t fb = ((size_t)n * s->kp.dim * sizeof(float) + 255) & ~(size_t)255;
     const size_t cb = ((size_t)n * sizeof(int32_t) + 255) & ~(size_t)255;
     const size_t ib = (size_t)n * sizeof(uint64_t);
-    void *tmp;
+    void *tmp = nullptr;
     if (int r = scratch(s, fb + cb + ib + 256, &tmp)) return r;
     char *b = (char *)tmp;
     CUDA_TRY(launch_stage_forces(view(s), (float *)b, (int32_t *)(b + fb), (unsigned long long *)(b + fb + cb), st));
@@ -1387,7 +1387,7 @@ int chemo_stage_drift(chemo_sim *s, float *drift_out, int mem_kind, void *stream
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = (size_t)s->kp.n * s->kp.dim * sizeof(float);
-    void *tmp;
+    void *tmp = nullptr;
     if (int r = scratch(s, bytes + 256, &tmp)) return r;
     CUDA_TRY(launch_stage_drift(view(s), s->cur, (float *)tmp, st));
     if (int r = stage_out(s, drift_out, tmp, bytes, mem_kind, st)) return r;
@@ -1402,7 +1402,7 @@ int chemo_stage_deposit(chemo_sim *s, float *S_out, float *R_out, int mem_kind, 
     if (!s->kp.has_grid) return fail(CHEMO_EINVAL, "this simulation has no grid (chem_mode 1)");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t gb = ((size_t)s->kp.G * sizeof(float) + 255) & ~(size_t)255;
-    void *tmp;
+    void *tmp = nullptr;
     if (int r = scratch(s, 2 * gb, &tmp)) return r;
     float *dS = (float *)tmp, *dR = (float *)((char *)tmp + gb);
     CUDA_TRY(cudaMemsetAsync(tmp, 0, 2 * gb, st));
