@@ -116,6 +116,47 @@ def test_struct_size_mismatch_rejected(chemo):
     assert "struct_size" in chemo.chemo_last_error()
 
 
+def test_plain_c_program_uses_the_library(chemo, tmp_path):
+    """The ABI needs no Python: a C program built against include/chemo.h
+    and linked to the library gets status strings, sets and resets an
+    allocator, and sees a bad parameter set rejected before any GPU work."""
+    prog = tmp_path / "use.c"
+    prog.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "chemo.h"
+static int my_alloc(void *ctx, size_t bytes, void **ptr) { (void)ctx; (void)bytes; *ptr = 0; return 1; }
+static void my_release(void *ctx, void *ptr, size_t bytes) { (void)ctx; (void)ptr; (void)bytes; }
+int main(void) {
+    chemo_params p;
+    chemo_sim *sim = 0;
+    int st;
+    memset(&p, 0, sizeof p);
+    p.struct_size = sizeof p;
+    p.dim = 4; /* invalid */
+    p.n_species = 1;
+    p.hi[0] = p.hi[1] = p.hi[2] = 1.0;
+    p.dt = 1e-5;
+    st = chemo_create(&p, 0, 0, 0, CHEMO_MEM_HOST, 0, &sim);
+    printf("%d %s|%s|%d\n", st, chemo_status_string(st), chemo_last_error(), sim == 0);
+    printf("%d %d %d\n", chemo_set_allocator(my_alloc, 0, 0), chemo_set_allocator(my_alloc, my_release, 0),
+           chemo_set_allocator(0, 0, 0));
+    chemo_destroy(0);
+    return 0;
+}
+""")
+    exe = tmp_path / "use"
+    libdir = os.path.dirname(gb.LIB)
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(prog), "-o",
+                    str(exe), "-L", libdir, "-lchemo_gb300", "-Wl,-rpath," + libdir], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    st, rest = out[0].split(" ", 1)
+    assert int(st) == chemo.EINVAL
+    text, msg, null_out = rest.split("|")
+    assert "invalid" in text and "dim" in msg and null_out == "1"
+    assert out[1].split() == [str(chemo.EINVAL), "0", "0"]
+
+
 def test_gradient_needs_a_simulation(chemo):
     st = chemo.lib().chemo_gradient(None, None, None, None, None, 0, None)
     assert st == chemo.EINVAL
