@@ -56,3 +56,42 @@ def test_resume_with_field():
     np.testing.assert_array_equal(whole[1], resumed[1])
     assert np.abs(whole[0] - resumed[0]).max() <= 1e-5
     assert np.abs(cw - cr).max() <= 1e-5 * np.abs(cw).max()
+
+
+def test_checkpoint_file_resumes_bitwise(tmp_path):
+    """save_sim / load_sim: the same continuation through an .npz file."""
+    from paper_1805_11007_gb300 import checkpoint as ck
+    p, pos, sp = wl.initial_state("periodic_fixed_gradient_2d", n=5003)
+    with make_sim(p, pos, sp) as a:
+        chemo.chemo_step_n(a, 30)
+        whole = chemo.read_state_host(a)
+    with make_sim(p, pos, sp) as b:
+        chemo.chemo_step_n(b, 17)
+        ck.save_sim(b, tmp_path / "run.npz")
+    with ck.load_sim(tmp_path / "run.npz") as r:
+        assert chemo.chemo_step_index(r) == 17
+        chemo.chemo_step_n(r, 13)
+        resumed = chemo.read_state_host(r)
+    for x, y in zip(whole, resumed):
+        np.testing.assert_array_equal(x, y)
+
+
+def test_checkpoint_file_of_an_ensemble(tmp_path):
+    """An ensemble's checkpoint keeps its replicate sizes and every
+    replicate's grid."""
+    from paper_1805_11007_gb300 import checkpoint as ck
+    p, s, pos, sp = wl.ensemble_state(sizes=[300, 0, 1200, 77], grid=[32, 32, 1], cutoff_mode=1)
+    with chemo.chemo_create_batch(p, s, dev(pos), dev(sp)) as a:
+        chemo.chemo_step_n(a, 5)
+        ck.save_sim(a, tmp_path / "ens.npz")
+        chemo.chemo_step_n(a, 6)
+        whole = chemo.read_state_host(a)
+        cw = chemo.read_field_host(a)
+    with ck.load_sim(tmp_path / "ens.npz") as r:
+        assert r.sizes == [300, 0, 1200, 77] and chemo.chemo_step_index(r) == 5
+        chemo.chemo_step_n(r, 6)
+        resumed = chemo.read_state_host(r)
+        cr = chemo.read_field_host(r)
+    np.testing.assert_array_equal(whole[1], resumed[1])
+    assert np.abs(whole[0] - resumed[0]).max() <= 1e-5
+    assert np.abs(cw - cr).max() <= 1e-5 * max(np.abs(cw).max(), 1e-30)
