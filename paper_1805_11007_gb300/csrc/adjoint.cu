@@ -90,6 +90,9 @@ void chemo_tape_free(chemo_tape *t)
     if (t->s_fwd) cudaStreamSynchronize(t->s_fwd);
     if (t->s_rev) cudaStreamSynchronize(t->s_rev);
     if (t->s_pair) cudaStreamSynchronize(t->s_pair);
+    // cudaFree waits for the device by itself; a caller's release does not,
+    // and the record may have run on the caller's stream
+    if (t->mem.release && !t->allocs.empty()) cudaDeviceSynchronize();
     for (const DevBuf &b : t->allocs) eng_mem_release(t->mem, b.ptr, b.bytes);
     for (cudaEvent_t e : {t->ev_ready[0], t->ev_ready[1], t->ev_done[0], t->ev_done[1], t->ev_start, t->ev_fwd_end,
                           t->ev_rev_end, t->ev_cells, t->ev_pairs})
