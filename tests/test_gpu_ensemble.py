@@ -3,7 +3,6 @@ in one simulation, against the FP64 oracle run replicate by replicate (seed +
 r) and against single GPU simulations of each replicate."""
 import numpy as np
 import pytest
-import torch
 
 from oracle import chemo_oracle as orc
 from paper_1805_11007_gb300 import chemo

@@ -13,7 +13,7 @@ import torch
 from oracle import chemo_oracle as orc
 from paper_1805_11007_gb300 import chemo
 from paper_1805_11007_gb300 import workloads as wl
-from parity_util import (assert_forces_match, assert_step_matches, dev, gpu_forces, make_sim)
+from parity_util import (assert_forces_match, assert_step_matches, gpu_forces, make_sim)
 
 pytestmark = pytest.mark.gpu
 

@@ -5,7 +5,6 @@ generator (a library routine run on the CPU; key = (seed lo, seed hi)). The
 normals are checked against the standard normal law.
 """
 import ctypes
-import os
 
 import numpy as np
 import pytest
