@@ -40,6 +40,14 @@ def test_every_declared_function_is_exported(chemo):
         assert hasattr(L, n)
 
 
+def test_binding_declares_every_function_of_the_header(chemo):
+    """The Python binding sets argument and result types for exactly the
+    functions the header declares (no call goes through ctypes' defaults)."""
+    import inspect
+    bound = set(re.findall(r'"(chemo_[a-z_0-9]+)"', inspect.getsource(chemo._declare)))
+    assert bound == set(_declared())
+
+
 def test_struct_layouts_match_ctypes(chemo, tmp_path):
     prog = tmp_path / "layout.c"
     fields_p = [f for f, _ in chemo.chemo_params._fields_]
