@@ -266,6 +266,23 @@ def test_pde_separable_mode_on_every_axis(dim, bc):
     np.testing.assert_allclose(out, fac * c, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("s", [1, 4])
+def test_pde_reaction_terms_per_node(s):
+    """With no diffusion a substep acts node by node: c' = c (1 - dt_s
+    (gamma + R)) + S / s, R the consumption density (kappa rho) and S the
+    step's source split over the s substeps (Eq. (1d), Sect. 3.5)."""
+    p = wl.params("walls_grid_2d", grid=[9, 7, 1], Dc=0.0, gamma=0.3, dt=1e-2)
+    rng = np.random.default_rng(8)
+    shape = orc.grid_shape(p)
+    c = rng.random(shape) + 0.5
+    R = 2.0 * rng.random(shape)
+    S = 0.01 * rng.random(shape)
+    dts = p["dt"] / s
+    g = float(np.float32(0.3))
+    out = orc.pde_substep(p, c, S, R, s)
+    np.testing.assert_allclose(out, c * (1 - dts * (g + R)) + S / s, rtol=0, atol=1e-14)
+
+
 def test_pde_uniform_decay():
     p = wl.params("clumps_grid_3d", grid=[9, 9, 9], gamma=0.1)
     c = np.full(orc.grid_shape(p), 3.0)
