@@ -280,6 +280,20 @@ int chemo_set_step_index(chemo_sim *sim, int64_t step, void *stream);
  * clears it. */
 int chemo_check(chemo_sim *sim, void *stream);
 
+/* Failure-detection test of the one device-side wait (the look-back of the
+ * cell-list scan, a decoupled look-back after Merrill & Garland; no
+ * counterpart in the paper). Runs one scan of the simulation's idle count
+ * buffer with its tile counter started at 1 instead of 0, so no block
+ * claims tile 0 and the tiles after it wait on a predecessor that never
+ * publishes; each wait gives up after spin_limit polls (the library's own
+ * scans use 2^22, about 0.1 s) and latches CHEMO_ETIMEOUT, which the next
+ * chemo_check returns and clears. The offsets go to scratch memory and the
+ * scan's counters are reset afterwards, so the simulation's state and cell
+ * list are untouched and the next step is a normal one. Asynchronous on
+ * `stream`. EINVAL for spin_limit 0 or a cell list of a single scan tile
+ * (4096 groups of 8 bins or fewer), where no tile waits on another. */
+int chemo_stall_scan(chemo_sim *sim, uint32_t spin_limit, void *stream);
+
 /* Fills *info. */
 int chemo_get_info(const chemo_sim *sim, chemo_info *info);
 
@@ -406,14 +420,20 @@ int chemo_stage_deposit(chemo_sim *sim, float *S_out, float *R_out, int mem_kind
  * params as for chemo_create (only the geometry, species and force fields
  * matter). The cell list is built in one static device array owned by the
  * library (about 3.4 MB, held on every GPU that loads the library until the
- * process exits), so: n <= 65536 and the cell list may use at most 262144
- * bins, else CHEMO_EINVAL with a message naming the limit. All calls share
- * the array and it keeps the last call's contents; calls whose kernels
- * overlap on the GPU (different streams without ordering) race on it. The
- * first call on a device looks up the array's device address, with that
- * device current; make that first call before any stream capture. The call
- * is asynchronous on `stream`; device-side input errors (non-finite
- * positions, species out of range) are not reported. */
+ * process exits), so: n <= 65535 (the largest 16-bit bin count, so that no
+ * bin can overflow even with every particle in it) and the cell list may use
+ * at most 262144 bins, else CHEMO_EINVAL with a message naming the limit.
+ * All calls share the array and it keeps the last call's contents; calls
+ * whose kernels overlap on the GPU (different streams without ordering) race
+ * on it. The first call on a device looks up the array's device address,
+ * with that device current; make that first call before any stream capture.
+ * The call is asynchronous on `stream` and returns before the kernels run,
+ * so conditions found on the device are not reported: a non-finite
+ * coordinate (taken as the box's lower bound on that axis), a species out of
+ * range (taken as species 0), a position outside the box (clamped to the
+ * box) and a bounded wait of the cell-list scan that ran out (possible only
+ * when other work starves the kernel; the forces are then unspecified).
+ * Validate inputs on the host where these can occur. */
 int chemo_forces_noalloc(const chemo_params *params, int64_t n, const float *pos, const uint8_t *species,
                          float *F_out, void *stream);
 

@@ -190,6 +190,7 @@ def _declare(L):
         "chemo_step_index": ([vp], i64),
         "chemo_set_step_index": ([vp, i64, vp], ctypes.c_int),
         "chemo_check": ([vp, vp], ctypes.c_int),
+        "chemo_stall_scan": ([vp, ctypes.c_uint32, vp], ctypes.c_int),
         "chemo_get_info": ([vp, ctypes.POINTER(chemo_info)], ctypes.c_int),
         "chemo_destroy": ([vp], None),
         "chemo_status_string": ([ctypes.c_int], ctypes.c_char_p),
@@ -444,6 +445,13 @@ def chemo_set_step_index(sim: Sim, step: int, stream=None):
 
 def chemo_check(sim: Sim, stream=None):
     _check(lib().chemo_check(_h(sim), _stream(stream)), "chemo_check")
+
+
+def chemo_stall_scan(sim: Sim, spin_limit: int, stream=None):
+    """Failure-detection test: one scan whose look-back waits on a tile that
+    no block publishes and gives up after spin_limit polls (the next
+    chemo_check raises ETIMEOUT); the simulation is left untouched."""
+    _check(lib().chemo_stall_scan(_h(sim), int(spin_limit), _stream(stream)), "chemo_stall_scan")
 
 
 def chemo_get_info(sim: Sim) -> dict:

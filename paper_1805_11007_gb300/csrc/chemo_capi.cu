@@ -269,6 +269,7 @@ void fill_model(const chemo_params &p, KP &kp)
 int fill_layout(const chemo_params &p, int64_t n, KP &kp)
 {
     kp.dim = p.dim;
+    kp.scan_spins = 1u << 22;  // look-back polls (~0.1 s) before the scan gives up
     kp.periodic = p.boundary == 1;
     for (int a = 0; a < 3; ++a) {
         kp.lo[a] = a < p.dim ? (float)p.lo[a] : 0.f;
@@ -1319,6 +1320,25 @@ static int finish(chemo_sim *s, int mem_kind, void *stream)
         CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
         return chemo_check(s, stream);
     }
+    return CHEMO_OK;
+}
+
+int chemo_stall_scan(chemo_sim *s, uint32_t spin_limit, void *stream)
+{
+    g_last_error[0] = 0;
+    if (!s || spin_limit == 0) return fail(CHEMO_EINVAL, "sim and a positive spin_limit are required");
+    cudaStream_t st = (cudaStream_t)stream;
+    KP k = view(s);
+    if (scan_tiles(k) < 2) return fail(CHEMO_EINVAL, "the cell list has one scan tile: no tile waits on another");
+    // The scan reads and clears the idle count buffer (all zero between
+    // steps) and writes its offsets to scratch: the simulation's cell list
+    // is left as it was.
+    k.cnt_cur = k.cnt_nxt;
+    void *tmp = nullptr;
+    if (int r = scratch(s, ((size_t)k.ngroups + 1) * sizeof(uint32_t) + 256, &tmp)) return r;
+    k.gstart = (uint32_t *)tmp;
+    k.scan_spins = spin_limit;
+    CUDA_TRY(launch_scan_from_tile(k, 1u, st));
     return CHEMO_OK;
 }
 

@@ -111,6 +111,7 @@ struct KP {
     uint32_t *cnt_cur, *cnt_nxt;
     uint32_t *gstart;            // group offsets (ngroups + 1) of the state last scanned
     unsigned long long *tiles;   // scan tile status
+    uint32_t scan_spins;         // polls of the scan's look-back wait before it gives up (ERR_TIMEOUT)
     uint32_t *tile_ctr;          // dynamic tile counter of the scan
     uint32_t *scan_seq;          // scan epoch counter
     float *c[2];                 // chemical ping-pong buffers
@@ -178,12 +179,43 @@ __device__ __forceinline__ float word_uniform(uint32_t w)
     return fmaf((float)w, 2.3283064365386963e-10f, 1.1641532182693481e-10f);
 }
 
-// Box-Muller transform of the uniform pair (u(a), u(b)): two N(0,1) draws.
+// ln u(w) to single-precision relative accuracy over the whole range. For
+// u >= 1/2 the logarithm is taken of 1 + (-(1 - u)) with 1 - u formed from
+// the complement of the word (exact up to one rounding); u itself rounded to
+// single precision would leave 1 - u with an absolute error of 2^-25 and the
+// radius sqrt(-2 ln u) off by up to ~2 % where it is small.
+__device__ __forceinline__ float word_log_uniform(uint32_t w)
+{
+    if (w >= 0x80000000u) return log1pf(-fmaf((float)(~w), 2.3283064365386963e-10f, 1.1641532182693481e-10f));
+    return logf(word_uniform(w));
+}
+
+// (sin, cos) of 2 pi u(w). The top two bits of w give the quarter turn; the
+// angle inside it, pi (f + 1/2) 2^-31 with f the low 30 bits, is folded to at
+// most pi/4 with integer arithmetic (pi/2 minus it for f in the upper half),
+// so the small one of the two results keeps single-precision relative
+// accuracy instead of the 2^-24 absolute error of 2 u rounded near a multiple
+// of 1/2.
+__device__ __forceinline__ void word_sincos_2pi(uint32_t w, float &s, float &c)
+{
+    const uint32_t q = w >> 30, f = w & 0x3FFFFFFFu;
+    const bool low = f < 0x20000000u;
+    const uint32_t k = low ? f : 0x3FFFFFFFu - f;
+    float s0, c0;
+    sincospif(fmaf((float)k, 4.656612873077393e-10f, 2.3283064365386963e-10f), &s0, &c0);
+    const float sa = low ? s0 : c0, ca = low ? c0 : s0;  // sin, cos of the angle inside the quarter
+    // rotate by q quarter turns
+    s = q == 0 ? sa : (q == 1 ? ca : (q == 2 ? -sa : -ca));
+    c = q == 0 ? ca : (q == 1 ? -sa : (q == 2 ? -ca : sa));
+}
+
+// Box-Muller transform of the uniform pair (u(a), u(b)): two N(0,1) draws,
+// (r cos 2 pi u(b), r sin 2 pi u(b)) with r = sqrt(-2 ln u(a)).
 __device__ __forceinline__ float2 box_muller(uint32_t a, uint32_t b)
 {
-    const float r = sqrtf(-2.0f * logf(word_uniform(a)));
+    const float r = sqrtf(-2.0f * word_log_uniform(a));
     float s, c;
-    sincospif(2.0f * word_uniform(b), &s, &c);
+    word_sincos_2pi(b, s, c);
     return make_float2(r * c, r * s);
 }
 
@@ -222,14 +254,18 @@ __device__ __forceinline__ uint32_t bin_start(const uint32_t *__restrict__ cnt, 
     return s;
 }
 
+// Largest count of one bin: counts are 16-bit halves of a 32-bit word, so a
+// 65536th particle in one bin would carry into the neighbouring bin's count.
+constexpr uint32_t BIN_COUNT_MAX = 0xFFFFu;
+
 // Counts particle key k into the packed counts; returns its slot in the bin
-// (the count before it). A bin holds at most 65535 particles.
+// (the count before it). A bin holds at most BIN_COUNT_MAX particles.
 __device__ __forceinline__ uint32_t count_bin(uint32_t *cnt, uint32_t k, uint32_t *err)
 {
     const uint32_t sh = (k & 1u) * 16u;
     const uint32_t old = atomicAdd(&cnt[k >> 1], 1u << sh);
-    const uint32_t slot = (old >> sh) & 0xFFFFu;
-    if (slot == 0xFFFFu) atomicOr(err, 4u /* ERR_OVERFLOW */);
+    const uint32_t slot = (old >> sh) & BIN_COUNT_MAX;
+    if (slot == BIN_COUNT_MAX) atomicOr(err, 4u /* ERR_OVERFLOW */);
     return slot;
 }
 
@@ -331,6 +367,12 @@ cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *l
 cudaError_t launch_pack(const KP &kp, const float *pos, const uint8_t *sp, const float *disp,
                         cudaStream_t st, int *launches);
 cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches);
+// Runs the scan with its tile counter started at first_tile (then puts the
+// counter back to 0 and advances the scan epoch, as the scatter does), so
+// the tiles that look back at the unclaimed ones wait until their limit.
+cudaError_t launch_scan_from_tile(const KP &kp, uint32_t first_tile, cudaStream_t st);
+// Number of tiles (blocks) of the scan of kp's cell list.
+unsigned scan_tiles(const KP &kp);
 cudaError_t launch_scatter(const KP &kp, int cur, int advance_step, cudaStream_t st, int *launches);
 cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches);
 // Substeps per launch of the temporal-blocked 2D PDE kernel (its halo width).

@@ -1218,13 +1218,13 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
             unsigned long long stw = 0ull;
             unsigned long long flag = ST_INC, val = 0ull;
             if (p >= 0) {
-                int spins = 0;
+                uint32_t spins = 0;
                 for (;;) {
                     stw = *(volatile unsigned long long *)&kp.tiles[p];
                     const uint32_t e = (uint32_t)(stw >> 40);
                     flag = (stw >> ST_VAL_BITS) & 3ull;
                     if (e == epoch && flag != 0ull) break;
-                    if (++spins > (1 << 22)) {  // bounded wait
+                    if (++spins > kp.scan_spins) {  // bounded wait
                         timed_out = true;
                         flag = ST_INC;
                         stw = 0ull;
@@ -2132,11 +2132,31 @@ cudaError_t launch_pack(const KP &kp, const float *pos, const uint8_t *sp, const
     return cudaGetLastError();
 }
 
+unsigned scan_tiles(const KP &kp) { return (unsigned)((kp.ngroups + SCAN_TILE - 1) / SCAN_TILE); }
+
 cudaError_t launch_scan(const KP &kp, cudaStream_t st, int *launches)
 {
-    const unsigned tiles = (unsigned)((kp.ngroups + SCAN_TILE - 1) / SCAN_TILE);
+    const unsigned tiles = scan_tiles(kp);
     k_scan<<<tiles, TPB, 0, st>>>(kp);
     if (launches) ++*launches;
+    return cudaGetLastError();
+}
+
+__global__ void k_set_tile_ctr(uint32_t *ctr, uint32_t v) { *ctr = v; }
+
+__global__ void k_end_scan(uint32_t *ctr, uint32_t *seq)
+{
+    *ctr = 0u;
+    *seq += 1u;
+}
+
+cudaError_t launch_scan_from_tile(const KP &kp, uint32_t first_tile, cudaStream_t st)
+{
+    k_set_tile_ctr<<<1, 1, 0, st>>>(kp.tile_ctr, first_tile);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_scan(kp, st, nullptr);
+    if (e != cudaSuccess) return e;
+    k_end_scan<<<1, 1, 0, st>>>(kp.tile_ctr, kp.scan_seq);
     return cudaGetLastError();
 }
 

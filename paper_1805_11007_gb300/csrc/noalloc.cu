@@ -14,7 +14,8 @@
 // (NOALLOC_BYTES) until the process exits, the array is shared by all calls
 // (calls whose kernels overlap on the GPU race on it: keep them on one stream
 // or otherwise ordered), and the problem size is capped (NOALLOC_MAX_N
-// particles, NOALLOC_MAX_BINS cell-list bins).
+// particles, NOALLOC_MAX_BINS cell-list bins). The particle cap keeps every
+// 16-bit bin count below its wrap-around, even with all particles in one bin.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -26,14 +27,18 @@ using namespace chemo;
 
 namespace {
 
-constexpr int64_t NOALLOC_MAX_N = 65536;
+// A bin holds at most BIN_COUNT_MAX particles (16-bit packed counts), so at
+// most that many particles are accepted: one bin can then never overflow.
+constexpr int64_t NOALLOC_MAX_N = BIN_COUNT_MAX;
+static_assert(NOALLOC_MAX_N <= (int64_t)BIN_COUNT_MAX, "a single bin could overflow its 16-bit count");
+constexpr int64_t NOALLOC_CAP = NOALLOC_MAX_N + 1;  // particle slots (a multiple of 16)
 constexpr int64_t NOALLOC_MAX_BINS = (int64_t)1 << 18;  // a multiple of 8
 constexpr int64_t NOALLOC_MAX_GROUPS = NOALLOC_MAX_BINS / 8;
 constexpr int64_t NOALLOC_MAX_TILES = (NOALLOC_MAX_GROUPS + 2047) / 2048;
 
 // Sub-array sizes in bytes, each a multiple of 256.
-constexpr size_t SZ_STATE = (size_t)NOALLOC_MAX_N * sizeof(float4);            // S and U
-constexpr size_t SZ_SLOT = (size_t)NOALLOC_MAX_N * sizeof(uint32_t);
+constexpr size_t SZ_STATE = (size_t)NOALLOC_CAP * sizeof(float4);            // S and U
+constexpr size_t SZ_SLOT = (size_t)NOALLOC_CAP * sizeof(uint32_t);
 constexpr size_t SZ_CNT = (size_t)NOALLOC_MAX_BINS / 2 * sizeof(uint32_t);      // 16-bit counts
 constexpr size_t SZ_GSTART = ((size_t)NOALLOC_MAX_GROUPS + 256) * sizeof(uint32_t);
 constexpr size_t SZ_TILES = 256 * ((NOALLOC_MAX_TILES * 8 + 255) / 256);
@@ -41,6 +46,8 @@ constexpr size_t SZ_CTL = 256;
 constexpr size_t NOALLOC_BYTES = 2 * SZ_STATE + SZ_SLOT + 2 * SZ_CNT + SZ_GSTART + SZ_TILES + SZ_CTL;
 
 static_assert(SZ_TILES >= NOALLOC_MAX_TILES * sizeof(unsigned long long), "tile table too small");
+static_assert(SZ_STATE % 256 == 0 && SZ_SLOT % 256 == 0 && SZ_CNT % 256 == 0 && SZ_GSTART % 256 == 0,
+              "sub-arrays must keep 256-byte alignment");
 
 }  // namespace
 
@@ -84,7 +91,7 @@ extern "C" int chemo_forces_noalloc(const chemo_params *params, int64_t n, const
     KP kp{};
     if (int r = chemo_internal_build_kp(params, n, &kp)) return r;
     if (n > NOALLOC_MAX_N)
-        return chemo_internal_fail(CHEMO_EINVAL, "chemo_forces_noalloc: n exceeds the limit of 65536 particles");
+        return chemo_internal_fail(CHEMO_EINVAL, "chemo_forces_noalloc: n exceeds the limit of 65535 particles");
     if (kp.bin_slots > NOALLOC_MAX_BINS)
         return chemo_internal_fail(CHEMO_EINVAL, "chemo_forces_noalloc: the cell list needs more than 262144 bins "
                                                  "(box too large for the cutoff); use chemo_create instead");
