@@ -796,8 +796,10 @@ __global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
     }
 }
 
-template <int DIM>
-__device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restrict__ c, float4 p, float &cval)
+// Offsets from the base node are taken in IT (32-bit for grids of fewer than
+// 2^31 nodes: one address multiply-add per load instead of 64-bit adds).
+template <int DIM, typename IT>
+__device__ __forceinline__ float3 grad_interp_t(const KP &kp, const float *__restrict__ c, float4 p, float &cval)
 {
     int i0, i1, j0, j1, k0 = 0, k1 = 0;
     float fx, fy, fz = 0.f;
@@ -805,26 +807,27 @@ __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restr
     gcell(kp, 1, p.y, j0, j1, fy);
     if (DIM == 3) gcell(kp, 2, p.z, k0, k1, fz);
     else k0 = layer_of(kp, p);  // the particle's own layer of the grid
-    const int64_t gx = kp.g[0], plane = (int64_t)kp.g[0] * kp.g[1];
+    const IT gx = kp.g[0], plane = (IT)kp.g[0] * (IT)kp.g[1];
     // base node (i0, j0, k0) and offsets to the other nodes used
-    const int64_t b = (int64_t)i0 + gx * ((int64_t)j0 + (int64_t)kp.g[1] * k0);
-    const int64_t ox[4] = {gnbr(kp, 0, i0 - 1) - i0, 0, i1 - i0, gnbr(kp, 0, i1 + 1) - i0};
-    const int64_t oy[4] = {(gnbr(kp, 1, j0 - 1) - j0) * gx, 0, (j1 - j0) * gx, (gnbr(kp, 1, j1 + 1) - j0) * gx};
-    int64_t oz[4] = {0, 0, 0, 0};
+    c += (int64_t)i0 + (int64_t)kp.g[0] * ((int64_t)j0 + (int64_t)kp.g[1] * k0);
+    const IT b = 0;
+    const IT ox[4] = {(IT)(gnbr(kp, 0, i0 - 1) - i0), 0, (IT)(i1 - i0), (IT)(gnbr(kp, 0, i1 + 1) - i0)};
+    const IT oy[4] = {(IT)(gnbr(kp, 1, j0 - 1) - j0) * gx, 0, (IT)(j1 - j0) * gx, (IT)(gnbr(kp, 1, j1 + 1) - j0) * gx};
+    IT oz[4] = {0, 0, 0, 0};
     if (DIM == 3) {
-        oz[0] = (gnbr(kp, 2, k0 - 1) - k0) * plane;
-        oz[2] = (k1 - k0) * plane;
-        oz[3] = (gnbr(kp, 2, k1 + 1) - k0) * plane;
+        oz[0] = (IT)(gnbr(kp, 2, k0 - 1) - k0) * plane;
+        oz[2] = (IT)(k1 - k0) * plane;
+        oz[3] = (IT)(gnbr(kp, 2, k1 + 1) - k0) * plane;
     }
     constexpr int NZ = DIM == 3 ? 2 : 1;
     // corners C[bz][by][bx] and the nodes one beyond them along each axis
     float C[NZ][2][2], XM[NZ][2], XP[NZ][2], YM[NZ][2], YP[NZ][2], ZM[2][2], ZP[2][2];
 #pragma unroll
     for (int bz = 0; bz < NZ; ++bz) {
-        const int64_t z = oz[1 + bz];  // plane k0 (offset 0) or k1
+        const IT z = oz[1 + bz];  // plane k0 (offset 0) or k1
 #pragma unroll
         for (int bb = 0; bb < 2; ++bb) {
-            const int64_t yb = oy[1 + bb], xb = ox[1 + bb];
+            const IT yb = oy[1 + bb], xb = ox[1 + bb];
             C[bz][bb][0] = __ldg(&c[b + z + yb]);
             C[bz][bb][1] = __ldg(&c[b + z + yb + ox[2]]);
             XM[bz][bb] = __ldg(&c[b + z + yb + ox[0]]);
@@ -869,6 +872,13 @@ __device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restr
     return g;
 }
 
+template <int DIM>
+__device__ __forceinline__ float3 grad_interp(const KP &kp, const float *__restrict__ c, float4 p, float &cval)
+{
+    return kp.G < ((int64_t)1 << 31) ? grad_interp_t<DIM, int>(kp, c, p, cval)
+                                     : grad_interp_t<DIM, int64_t>(kp, c, p, cval);
+}
+
 // ---------------------------------------------------------------------------
 // Boundary handling (FP32): reflect until inside (walls) or wrap (periodic).
 // ---------------------------------------------------------------------------
@@ -903,7 +913,7 @@ __global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
-    load_tables(kp, t);
+    if (!HALF) load_tables(kp, t);  // the half-window instance evaluates no pair terms
     const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
     if (kp.zero_src) {  // source grids of the last step, read by its PDE: cleared for this step's deposit
         for (int64_t g = j; g < kp.G; g += (int64_t)gridDim.x * TPB) {
@@ -922,7 +932,7 @@ __global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
         if (kp.has_grid)
             for (int64_t i = j; i < kp.G; i += stride) kp.tape.c[(int64_t)tk * kp.G + i] = kp.c[cur][i];
     }
-    __syncthreads();
+    if (!HALF) __syncthreads();
     const bool valid = j < kp.n;
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const uint32_t w = __float_as_uint(me.w);
