@@ -1282,6 +1282,28 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
 }
 
 // ---------------------------------------------------------------------------
+// Adds a0 to t[g0] and a1 to t[g1]. Adjacent nodes (g1 = g0 + 1) inside one
+// aligned 8- or 16-byte block go in one vector reduction (zeros added to the
+// other two floats of a 16-byte block), which halves the atomic operations
+// of the deposit at the L2.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_nodes(float *t, int64_t g0, int64_t g1, float a0, float a1)
+{
+    float *p = t + g0;
+    const unsigned off = (unsigned)((reinterpret_cast<uintptr_t>(p) >> 2) & 3u);  // float slot in its 16 bytes
+    if (g1 == g0 + 1 && (off & 1u) == 0u) {
+        asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a0), "f"(a1) : "memory");
+    } else if (g1 == g0 + 1 && off == 1u) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p - 1), "f"(0.f), "f"(a0), "f"(a1),
+                     "f"(0.f)
+                     : "memory");
+    } else {
+        atomicAdd(p, a0);
+        atomicAdd(t + g1, a1);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Cloud-in-cell deposit of one cell (Sect. 2.3): weights w_k of the 2^d nodes
 // around x, mass over the node's control volume tau_k h^d (tau = 1/2 per wall
 // axis). fused: add S - dt R c^n straight into c^{n+1}; else add to S and R.
@@ -1299,25 +1321,33 @@ __device__ __forceinline__ void deposit_cic(const KP &kp, float4 u, int sp, floa
     if (DIM == 3) gcell(kp, 2, u.z, k0, k1, fz);
     else k0 = layer_of(kp, u);
     const bool walls = kp.pde_bc != 2;
+    // the two nodes of each (y, z) row of the cell, x = i0 and i1
 #pragma unroll
-    for (int m = 0; m < (1 << DIM); ++m) {
-        const int bx = m & 1, by = (m >> 1) & 1, bz = (m >> 2) & 1;
-        const int x = bx ? i1 : i0, y = by ? j1 : j0, z = bz ? k1 : k0;
-        float wgt = (bx ? fx : 1.f - fx) * (by ? fy : 1.f - fy);
-        if (DIM == 3) wgt *= bz ? fz : 1.f - fz;
+    for (int m = 0; m < (1 << (DIM - 1)); ++m) {
+        const int by = m & 1, bz = (m >> 1) & 1;
+        const int y = by ? j1 : j0, z = bz ? k1 : k0;
+        float wr = by ? fy : 1.f - fy;
+        if (DIM == 3) wr *= bz ? fz : 1.f - fz;
         if (walls) {
-            if (x == 0 || x == kp.g[0] - 1) wgt *= 2.f;
-            if (y == 0 || y == kp.g[1] - 1) wgt *= 2.f;
-            if (DIM == 3 && (z == 0 || z == kp.g[2] - 1)) wgt *= 2.f;
+            if (y == 0 || y == kp.g[1] - 1) wr *= 2.f;
+            if (DIM == 3 && (z == 0 || z == kp.g[2] - 1)) wr *= 2.f;
         }
-        const int64_t g = gidx(kp, x, y, z);
+        float w0 = (1.f - fx) * wr, w1 = fx * wr;
+        if (walls) {
+            if (i0 == 0) w0 *= 2.f;
+            if (i1 == kp.g[0] - 1) w1 *= 2.f;
+        }
+        const int64_t g0 = gidx(kp, i0, y, z), g1 = gidx(kp, i1, y, z);
         if (fused) {
-            float a = ks * wgt;
-            if (kc != 0.f) a -= kp.dt * kc * wgt * __ldg(&cin[g]);
-            atomicAdd(&tS[g], a);
+            float a0 = ks * w0, a1 = ks * w1;
+            if (kc != 0.f) {
+                a0 -= kp.dt * kc * w0 * __ldg(&cin[g0]);
+                a1 -= kp.dt * kc * w1 * __ldg(&cin[g1]);
+            }
+            red_nodes(tS, g0, g1, a0, a1);
         } else {
-            if (ks != 0.f) atomicAdd(&tS[g], ks * wgt);
-            if (kc != 0.f) atomicAdd(&tR[g], kc * wgt);
+            if (ks != 0.f) red_nodes(tS, g0, g1, ks * w0, ks * w1);
+            if (kc != 0.f) red_nodes(tR, g0, g1, kc * w0, kc * w1);
         }
     }
 }
