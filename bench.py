@@ -410,6 +410,7 @@ def ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier, steps=500,
            "value": float(sizes.sum()) * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "launches_per_step": info["launches_per_step"],
            "autotuned": {"search_mode": p["search_mode"], "bin_side": p["bin_side"], "warp_runs": p["warp_runs"],
+                         "block_threads": p.get("block_threads", 0),
                          "pde_overlap": p["pde_overlap"], "trial_ms_per_step": tuned_ms, "tuning_s": tune_s},
            "kernel_ms": {k: prof[k] for k in ("k_step", "k_pde", "k_scan", "k_scatter", "step")},
            "observables": {"how": "chemo_observables per replicate after the timed run, gathered from every rank",

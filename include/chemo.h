@@ -125,6 +125,10 @@ typedef struct chemo_params {
                                     estimate with bandwidth sigma_s gathered at every node
                                     (Sect. 2.3), truncated at kde_range bandwidths */
     float kde_range;             /* KDE truncation radius in bandwidths (0 = 3) */
+    int32_t block_threads;       /* threads per block of the half-window pair kernel and the
+                                    move kernel after it: 0 = automatic (256), 128, 256 or 512
+                                    (the same registers per thread; chemo_autotune tries them).
+                                    Results are identical; only the speed differs */
 } chemo_params;
 
 /* Layout facts of a simulation (read-only). */

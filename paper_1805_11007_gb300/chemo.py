@@ -73,6 +73,7 @@ class chemo_params(ctypes.Structure):
         ("hard_sphere", ctypes.c_int32),
         ("deposit_kernel", ctypes.c_int32),
         ("kde_range", ctypes.c_float),
+        ("block_threads", ctypes.c_int32),
     ]
 
 
@@ -138,6 +139,7 @@ def make_params(d: dict) -> chemo_params:
     p.bin_order = int(d.get("bin_order", 0))
     p.pde_overlap = int(d.get("pde_overlap", 0))
     p.warp_runs = int(d.get("warp_runs", 0))
+    p.block_threads = int(d.get("block_threads", 0))
     p.move_scheme = int(d.get("move_scheme", 0))
     p.hard_sphere = int(d.get("hard_sphere", 0))
     p.deposit_kernel = int(d.get("deposit_kernel", 0))
@@ -359,8 +361,9 @@ def chemo_create_batch(params: dict, n_per_replicate, pos, species, stream=None)
 
 
 def chemo_autotune(params: dict, n_per_replicate, pos, species, trial_steps: int = 20, stream=None):
-    """Fastest (bin_side, search_mode, pde_overlap) for this particle set:
-    returns (params dict with those fields set, device ms per step)."""
+    """Fastest (bin_side, search_mode, warp_runs, block_threads, pde_overlap)
+    for this particle set: returns (params dict with those fields set,
+    device ms per step)."""
     sizes = np.ascontiguousarray(np.asarray(n_per_replicate, dtype=np.int64).reshape(-1))
     pp, kp_, _a = _buf(pos, np.float32)
     sp, ks, _b = _buf(species, np.uint8)
@@ -375,6 +378,7 @@ def chemo_autotune(params: dict, n_per_replicate, pos, species, trial_steps: int
     q["search_mode"] = int(best.search_mode)
     q["pde_overlap"] = int(best.pde_overlap)
     q["warp_runs"] = int(best.warp_runs)
+    q["block_threads"] = int(best.block_threads)
     return q, float(ms.value)
 
 

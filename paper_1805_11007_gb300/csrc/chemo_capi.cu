@@ -130,6 +130,8 @@ int check_params(const chemo_params &p)
     if (p.chem_mode != 0 && p.chem_mode != 1) return fail(CHEMO_EINVAL, "chem_mode must be 0 or 1");
     if (p.search_mode < 0 || p.search_mode > 4) return fail(CHEMO_EINVAL, "search_mode must be 0, 1, 2, 3 or 4");
     if (p.warp_runs < 0 || p.warp_runs > 32) return fail(CHEMO_EINVAL, "warp_runs must be 0..32");
+    if (p.block_threads != 0 && p.block_threads != 128 && p.block_threads != 256 && p.block_threads != 512)
+        return fail(CHEMO_EINVAL, "block_threads must be 0, 128, 256 or 512");
     if (p.move_scheme != 0 && p.move_scheme != 1) return fail(CHEMO_EINVAL, "move_scheme must be 0 or 1");
     if (p.hard_sphere != 0 && p.hard_sphere != 1) return fail(CHEMO_EINVAL, "hard_sphere must be 0 or 1");
     if (p.deposit_kernel != 0 && p.deposit_kernel != 1) return fail(CHEMO_EINVAL, "deposit_kernel must be 0 or 1");
@@ -359,6 +361,7 @@ int fill_layout(const chemo_params &p, int64_t n, KP &kp)
     kp.ngroups = slots / 8;
     kp.search = search;
     kp.warp_runs = p.warp_runs > 0 ? p.warp_runs : 12;
+    kp.bt = p.block_threads > 0 ? p.block_threads : 256;
     return CHEMO_OK;
 }
 
@@ -920,6 +923,21 @@ int chemo_autotune(const chemo_params *params, int32_t replicates, const int64_t
         for (int v : runs) {
             chemo_params c = q;
             c.warp_runs = v;
+            float ms = 0.f;
+            const int r = trial_time(c, replicates, n_per_replicate, pos, species, mem_kind, trial_steps, st, &ms);
+            if (r) return r;
+            if (ms < best_ms) {
+                best_ms = ms;
+                q = c;
+            }
+        }
+    }
+    if ((q.search_mode == 0 || q.search_mode == 4) && rc > 0.0 && params->inter != 0.f) {
+        // threads per block of the half-window pair and move kernels
+        const int bts[2] = {128, 512};
+        for (int b : bts) {
+            chemo_params c = q;
+            c.block_threads = b;
             float ms = 0.f;
             const int r = trial_time(c, replicates, n_per_replicate, pos, species, mem_kind, trial_steps, st, &ms);
             if (r) return r;

@@ -34,6 +34,8 @@ struct KP {
     int dim, periodic, search;  // search 1: 3^d bins >= r_c (warp), 2: 2^d bins >= 2 r_c, 3: 3^d (per lane),
                                 // 4: upper half of the 3^d window (per lane, each pair once)
     int warp_runs;              // search 1: warps with at most this many bins search together
+    int bt;                     // threads per block of the half-window pair kernel and its move kernel
+                                // (128, 256 or 512; the same register budget per thread)
     int pairs;                  // 0: no pair interaction (inter = 0 or zero range)
     float lo[3], hi[3], L[3], halfL[3];
     int nb[3];                  // bins per axis

@@ -583,10 +583,10 @@ constexpr size_t warp_region()
 
 // Dynamic shared memory of the kernels that evaluate pair forces: species
 // tables and one region per warp.
-template <int DIM, bool PERIODIC, bool WARP>
+template <int DIM, bool PERIODIC, bool WARP, int BT = TPB>
 constexpr size_t pair_smem()
 {
-    return sizeof(SmemTables) + (size_t)(TPB / 32) * warp_region<DIM, PERIODIC, WARP>();
+    return sizeof(SmemTables) + (size_t)(BT / 32) * warp_region<DIM, PERIODIC, WARP>();
 }
 
 // ---------------------------------------------------------------------------
@@ -704,15 +704,17 @@ __device__ __forceinline__ void stage_half(const KP &kp, float4 me, int sp, uint
     }
 }
 
-template <int DIM, bool PERIODIC>
-__global__ void __launch_bounds__(TPB, CHEMO_PAIR_BLOCKS) k_pairs_half(KP kp)
+// BT threads per block; resident blocks per SM scale so that every block
+// size keeps the same register budget per thread.
+template <int DIM, bool PERIODIC, int BT = TPB>
+__global__ void __launch_bounds__(BT, CHEMO_PAIR_BLOCKS *TPB / BT) k_pairs_half(KP kp)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
     load_tables(kp, t);
     __syncthreads();
     constexpr int FS = FhStride<DIM>::value;
-    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.x * BT + threadIdx.x;
     const bool valid = j < kp.n;
     const float4 me = valid ? kp.S[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     const int sp = (int)(__float_as_uint(me.w) >> SP_SHIFT);
@@ -908,15 +910,15 @@ __device__ __forceinline__ float wrap_axis(float x, float lo, float hi, float L)
 // HALF: the pair force was summed by the half-window kernel; this instance
 // holds no search code (fewer registers, small shared memory, more warps to
 // hide the latency of the gathers).
-template <int DIM, bool PERIODIC, bool WARP, bool HALF = false>
-__global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLOCKS) k_step(KP kp, int cur)
+template <int DIM, bool PERIODIC, bool WARP, bool HALF = false, int BT = TPB>
+__global__ void __launch_bounds__(BT, (HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLOCKS) * TPB / BT) k_step(KP kp, int cur)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemTables &t = *reinterpret_cast<SmemTables *>(smem);
     if (!HALF) load_tables(kp, t);  // the half-window instance evaluates no pair terms
-    const int64_t j = (int64_t)blockIdx.x * TPB + threadIdx.x;
+    const int64_t j = (int64_t)blockIdx.x * BT + threadIdx.x;
     if (kp.zero_src) {  // source grids of the last step, read by its PDE: cleared for this step's deposit
-        for (int64_t g = j; g < kp.G; g += (int64_t)gridDim.x * TPB) {
+        for (int64_t g = j; g < kp.G; g += (int64_t)gridDim.x * BT) {
             kp.srcg[g] = 0.f;
             kp.Rg[g] = 0.f;
         }
@@ -926,7 +928,7 @@ __global__ void __launch_bounds__(TPB, HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
     if (kp.tape.pos && kp.tape.period) tk %= kp.tape.period;
     const bool taping = tk < kp.tape.nk;
     if (taping) {
-        const int64_t stride = (int64_t)gridDim.x * TPB;
+        const int64_t stride = (int64_t)gridDim.x * BT;
         for (int64_t i = j; i < kp.tape.cwords; i += stride) kp.tape.cnt[(int64_t)tk * kp.tape.cwords + i] = kp.cnt_cur[i];
         for (int64_t i = j; i < kp.tape.gwords; i += stride) kp.tape.gst[(int64_t)tk * kp.tape.gwords + i] = kp.gstart[i];
         if (kp.has_grid)
@@ -2099,10 +2101,10 @@ static inline unsigned blocks_for(int64_t n) { return (unsigned)((n + TPB - 1) /
 // shared memory those blocks need and leave the rest of the SM's 256 KB to
 // L1, which caches the candidate positions.
 template <typename K>
-static void allow_smem(K kernel, size_t bytes)
+static void allow_smem(K kernel, size_t bytes, int blocks = CHEMO_PAIR_BLOCKS)
 {
     if (bytes > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    const double need = (double)CHEMO_PAIR_BLOCKS * (double)(bytes + 1024) / (228.0 * 1024.0);
+    const double need = (double)blocks * (double)(bytes + 1024) / (228.0 * 1024.0);
     const int pct = (int)std::ceil(100.0 * need);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, pct > 100 ? 100 : pct);
 }
@@ -2120,6 +2122,16 @@ static void pair_kernel_attributes_of()
     allow_smem(k_stage_forces<3, true, W>, pair_smem<3, true, W>());
 }
 
+template <int BT>
+static void half_block_attributes()
+{
+    constexpr int nb = CHEMO_PAIR_BLOCKS * TPB / BT;
+    allow_smem(k_pairs_half<2, false, BT>, pair_smem<2, false, false, BT>(), nb);
+    allow_smem(k_pairs_half<2, true, BT>, pair_smem<2, true, false, BT>(), nb);
+    allow_smem(k_pairs_half<3, false, BT>, pair_smem<3, false, false, BT>(), nb);
+    allow_smem(k_pairs_half<3, true, BT>, pair_smem<3, true, false, BT>(), nb);
+}
+
 static void pair_kernel_attributes()
 {
     static bool done = false;
@@ -2130,17 +2142,40 @@ static void pair_kernel_attributes()
     allow_smem(k_pairs_half<2, true>, pair_smem<2, true, false>());
     allow_smem(k_pairs_half<3, false>, pair_smem<3, false, false>());
     allow_smem(k_pairs_half<3, true>, pair_smem<3, true, false>());
+    half_block_attributes<128>();
+    half_block_attributes<512>();
     done = true;
 }
 
 // The 3^d window uses the warp search, the 2^d window the per-lane search.
+// The half-window pair kernel and the move kernel after it, BT threads per block.
+template <int DIM, bool PERIODIC, int BT>
+static void half_step_launch(const KP &kp, int cur, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((kp.n + BT - 1) / BT);
+    k_pairs_half<DIM, PERIODIC, BT><<<nb, BT, pair_smem<DIM, PERIODIC, false, BT>(), st>>>(kp);
+    k_step<DIM, PERIODIC, false, true, BT><<<nb, BT, sizeof(SmemTables), st>>>(kp, cur);
+}
+
+template <int DIM, bool PERIODIC>
+static void half_pairs_launch(const KP &kp, cudaStream_t st)
+{
+    if (kp.bt == 128)
+        k_pairs_half<DIM, PERIODIC, 128><<<(unsigned)((kp.n + 127) / 128), 128, pair_smem<DIM, PERIODIC, false, 128>(), st>>>(kp);
+    else if (kp.bt == 512)
+        k_pairs_half<DIM, PERIODIC, 512><<<(unsigned)((kp.n + 511) / 512), 512, pair_smem<DIM, PERIODIC, false, 512>(), st>>>(kp);
+    else
+        k_pairs_half<DIM, PERIODIC><<<(unsigned)((kp.n + TPB - 1) / TPB), TPB, pair_smem<DIM, PERIODIC, false>(), st>>>(kp);
+}
+
 template <int DIM, bool PERIODIC, bool W>
 static void step_launch(const KP &kp, int cur, cudaStream_t st)
 {
     const unsigned nb = (unsigned)((kp.n + TPB - 1) / TPB);
     if (kp.pairs && kp.Fh) {
-        k_pairs_half<DIM, PERIODIC><<<nb, TPB, pair_smem<DIM, PERIODIC, false>(), st>>>(kp);
-        k_step<DIM, PERIODIC, false, true><<<nb, TPB, sizeof(SmemTables), st>>>(kp, cur);
+        if (kp.bt == 128) half_step_launch<DIM, PERIODIC, 128>(kp, cur, st);
+        else if (kp.bt == 512) half_step_launch<DIM, PERIODIC, 512>(kp, cur, st);
+        else half_step_launch<DIM, PERIODIC, TPB>(kp, cur, st);
     } else {
         k_step<DIM, PERIODIC, W><<<nb, TPB, pair_smem<DIM, PERIODIC, W>(), st>>>(kp, cur);
     }
@@ -2357,10 +2392,8 @@ cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned
     if (kp.pairs && kp.Fh) {
         // the forces of the half-window kernel replace the full window's
         // (the counts and id sums stay the full window's)
-#define HALF_F(D, P) k_pairs_half<D, P><<<nb, TPB, pair_smem<D, P, false>(), st>>>(kp)
-        if (kp.dim == 2) kp.periodic ? HALF_F(2, true) : HALF_F(2, false);
-        else kp.periodic ? HALF_F(3, true) : HALF_F(3, false);
-#undef HALF_F
+        if (kp.dim == 2) kp.periodic ? half_pairs_launch<2, true>(kp, st) : half_pairs_launch<2, false>(kp, st);
+        else kp.periodic ? half_pairs_launch<3, true>(kp, st) : half_pairs_launch<3, false>(kp, st);
         if (kp.dim == 2) k_stage_take_half<2><<<nb, TPB, 0, st>>>(kp, F);
         else k_stage_take_half<3><<<nb, TPB, 0, st>>>(kp, F);
     }

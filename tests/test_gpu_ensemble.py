@@ -161,6 +161,7 @@ def test_autotune_choice_leaves_particles_unchanged():
     best, ms = chemo.chemo_autotune(p, s, pos, sp, trial_steps=3)
     assert ms > 0.0
     assert best["search_mode"] in (1, 2, 3, 4)
+    assert best["block_threads"] in (0, 128, 512)  # 0: the default 256 was fastest
     out = []
     for q in (p, best):
         with _batch(q, s, pos, sp, c0) as sim:

@@ -489,6 +489,31 @@ def test_half_window_step_bitwise(name, over):
     assert np.abs(outs[1] - outs[3]).max() <= 1e-6  # the deposit's float atomics round in any order
 
 
+@pytest.mark.parametrize("name,over", [
+    ("walls_grid_2d", dict(grid=[64, 64, 1])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32], diameter=[0.01, 0.02])),
+    ("clumps_grid_3d", dict(grid=[32, 32, 32], diameter=[0.01, 0.03], boundary=1, pde_bc=2)),
+])
+def test_block_shapes_give_identical_steps(name, over):
+    """128, 256 and 512 threads per block of the half-window pair and move
+    kernels (the autotuner's block-shape choice): forces and whole steps bit
+    for bit the same."""
+    p, pos, sp = wl.initial_state(name, n=30011, **over)
+    c0 = wl.random_field(p, seed=3, scale=0.3) if p["chem_mode"] == 0 else None
+    forces, states = [], []
+    for bt in (0, 128, 256, 512):
+        with make_sim(dict(p, search_mode=4, block_threads=bt), pos, sp, c0) as sim:
+            forces.append(gpu_forces(sim)[0])
+            chemo.chemo_step_n(sim, 3)
+            states.append(chemo.read_state_host(sim)[0])
+    for f, x in zip(forces[1:], states[1:]):
+        np.testing.assert_array_equal(f, forces[0])
+        if c0 is None:
+            np.testing.assert_array_equal(x, states[0])
+        else:  # the deposit's float atomics round in any order
+            assert np.abs(x - states[0]).max() <= 1e-6
+
+
 def test_half_window_many_steps_fixed_gradient_bitwise():
     """No chemical field (fixed gradient): every step is exact integer force
     sums and counter-based noise, so 37 graph-replayed steps of the half
