@@ -237,22 +237,14 @@ __device__ __forceinline__ uint32_t bin_key(const KP &kp, int cx, int cy, int cz
     return (uint32_t)cx + (uint32_t)kp.px * ((uint32_t)cy + (uint32_t)kp.nb[1] * (uint32_t)cz);
 }
 
-// Offset of bin k in the sorted arrays: its group's offset plus the counts of
-// the bins before it in the group (16-bit counts, 2 per word, 8 per group).
+// Offset of bin k in the sorted arrays: its group's offset plus its offset
+// within the group of 8 bins, which the scan writes over the bin's 16-bit
+// count (2 per word; the first bin of a group has offset 0).
 __device__ __forceinline__ uint32_t bin_start(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ gstart,
                                               uint32_t k)
 {
-    const uint32_t g = k >> 3, r = k & 7u;
-    uint32_t s = __ldg(&gstart[g]);
-    if (r) {
-        const uint4 w = __ldg(reinterpret_cast<const uint4 *>(cnt) + g);
-        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-        for (uint32_t i = 0; i < 4; ++i) {
-            if (2 * i < r) s += ws[i] & 0xFFFFu;
-            if (2 * i + 1 < r) s += ws[i] >> 16;
-        }
-    }
+    uint32_t s = __ldg(&gstart[k >> 3]);
+    if (k & 7u) s += __ldg(reinterpret_cast<const unsigned short *>(cnt) + k);
     return s;
 }
 
@@ -260,7 +252,9 @@ __device__ __forceinline__ uint32_t bin_start(const uint32_t *__restrict__ cnt, 
 // 65536th particle in one bin would carry into the neighbouring bin's count.
 constexpr uint32_t BIN_COUNT_MAX = 0xFFFFu;
 
-// Counts particle key k into the packed counts; returns its slot in the bin
+// Counts particle key k into the packed counts (zero before the count; the
+// scan turns them into offsets within the group afterwards); returns its
+// slot in the bin
 // (the count before it). A bin holds at most BIN_COUNT_MAX particles.
 __device__ __forceinline__ uint32_t count_bin(uint32_t *cnt, uint32_t k, uint32_t *err)
 {

@@ -1115,7 +1115,8 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
 // ---------------------------------------------------------------------------
 // k_scan: offsets of the groups of 8 bins of the state just counted
 // (cnt_nxt): gstart[g] = sum of the counts of all earlier groups,
-// gstart[ngroups] = n. Single pass with decoupled look-back (Merrill &
+// gstart[ngroups] = n; each nonempty group's counts are replaced by the
+// offsets of its bins within the group. Single pass with decoupled look-back (Merrill &
 // Garland, 2016): tiles are claimed in order from an atomic counter, each
 // publishes its aggregate, then its inclusive prefix once its predecessors'
 // are known. Waits are bounded; a wait that runs out latches ERR_TIMEOUT and
@@ -1189,7 +1190,7 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
     // shared memory as SCAN_ITEMS consecutive groups per thread (one padding
     // word per 32 keeps both passes free of bank conflicts)
     __shared__ uint32_t s_v[SCAN_TILE + SCAN_TILE / 32];
-    const uint4 *src = reinterpret_cast<const uint4 *>(kp.cnt_nxt);  // one uint4 per group
+    uint4 *src = reinterpret_cast<uint4 *>(kp.cnt_nxt);  // one uint4 per group
     uint4 *clr = reinterpret_cast<uint4 *>(kp.cnt_cur);
     const int64_t tbase = (int64_t)tile * SCAN_TILE;
 #pragma unroll
@@ -1201,6 +1202,16 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
             const uint4 q = __ldcs(src + g);
             s = halfsum(q.x) + halfsum(q.y) + halfsum(q.z) + halfsum(q.w);
             clr[g] = make_uint4(0u, 0u, 0u, 0u);
+            if (s) {
+                // the group's counts become the offsets of its bins within the
+                // group (exclusive prefix sums, 16 bits each): a bin's start is
+                // then its group's offset plus one 16-bit load (bin_start)
+                const uint32_t p1 = q.x & 0xFFFFu, p2 = p1 + (q.x >> 16), p3 = p2 + (q.y & 0xFFFFu);
+                const uint32_t p4 = p3 + (q.y >> 16), p5 = p4 + (q.z & 0xFFFFu), p6 = p5 + (q.z >> 16);
+                const uint32_t p7 = p6 + (q.w & 0xFFFFu);
+                if (p7 > 0xFFFFu) set_err(kp, ERR_OVERFLOW);
+                src[g] = make_uint4(p1 << 16, p2 | (p3 << 16), p4 | (p5 << 16), p6 | (p7 << 16));
+            }
         }
         s_v[k + (k >> 5)] = s;
     }
