@@ -104,9 +104,9 @@ FP32_LANES = 152 * 128
 PARTICLE_BYTES = 42.0
 
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
-# traffic field ("k_step": the particle kernels of one step together); None
-# where a kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": None, "k_pde": 93.31e6, "k_scan": 32.75e6, "k_scatter": 53.34e6}
+# traffic field ("k_step": the particle kernels of one step together, at
+# step 10 of the 3D workload); None where a kernel changed after the capture.
+NCU_TRAFFIC_BYTES = {"k_step": 138.28e6, "k_pde": 93.31e6, "k_scan": None, "k_scatter": None}
 
 
 # ---------------------------------------------------------------------------
