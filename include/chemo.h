@@ -409,6 +409,113 @@ int chemo_stage_drift(chemo_sim *sim, float *drift_out, int mem_kind, void *stre
 int chemo_stage_deposit(chemo_sim *sim, float *S_out, float *R_out, int mem_kind, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Slab decomposition of one system along z (sub-domains).                 */
+/* ---------------------------------------------------------------------- */
+
+/* One system (3D, reflecting walls, a grid) splits into slabs along z, one
+ * sub-domain simulation per slab (on one GPU or one per GPU). The paper runs
+ * one domain; these calls are the exchange points of its step (Sect. 3:
+ * interaction, move, deposit, PDE) across slab faces:
+ *
+ *   - a sub-domain holds the cells it owns (z in its slab) and ghosts:
+ *     copies of the neighbours' cells within the interaction range of a face
+ *     (Sect. 2.2), which add their pair force to owned cells and are neither
+ *     moved nor deposited (their owner does both);
+ *   - its box and grid are the slab widened by halo planes of the global
+ *     grid; an inner face (open) does not reflect, so an owned cell may step
+ *     into the halo and then migrates to the neighbour;
+ *   - deposits of owned cells onto halo planes are added to the neighbour's
+ *     source before its PDE (chemo_slab_planes, op ADD), and after the PDE the
+ *     halo planes of c are refreshed from the neighbours (op WRITE).
+ *
+ * Per step: chemo_step_particles on every sub-domain; fold the halo planes of
+ * the source and consumption grids into the neighbours; chemo_step_field;
+ * refresh the halo planes of c; chemo_slab_select into the cell sets of the
+ * sub-domain and its two neighbours; chemo_slab_ingest of each sub-domain's
+ * own set and the two it received. The noise is keyed by the cells' ids,
+ * which travel with them, so the decomposed run takes the steps of the
+ * single-domain run; results differ from it only by the order of the float
+ * additions of the deposit and the rounding of a sub-domain's grid origin. */
+
+#define CHEMO_OPEN_ZLO 1u           /* open_faces bit: the z = lo face is an inner face */
+#define CHEMO_OPEN_ZHI 2u           /* open_faces bit: the z = hi face is an inner face */
+#define CHEMO_GHOST_ID 0x1FFFFFFFu  /* id of a ghost cell in chemo_cell.tag */
+
+/* One cell in transit between sub-domains: 32 bytes, arrays of them 16-byte
+ * aligned. tag = id | species << 29 (id < CHEMO_GHOST_ID, or CHEMO_GHOST_ID
+ * for a ghost); (dx, dy, dz) is the displacement since the run began (zero
+ * unless the simulation tracks it). */
+typedef struct chemo_cell {
+    float x, y, z;
+    uint32_t tag;
+    float dx, dy, dz;
+    uint32_t reserved;
+} chemo_cell;
+
+/* Destination of chemo_slab_select: the cells with z0 <= z < z1 are
+ * appended to out (device memory, `capacity` records); those outside
+ * own0 <= z < own1 are written as ghosts. count points to two device
+ * counters that the call adds to: [0] cells selected, [1] of them owned
+ * (not ghosts). Cells past capacity are counted but not written, so
+ * count[0] > capacity reports an overflow. */
+typedef struct chemo_slab_target {
+    float z0, z1, own0, own1;
+    chemo_cell *out;
+    int64_t capacity;
+    unsigned long long *count;
+} chemo_slab_target;
+
+/* An empty sub-domain. params describes the slab with its halo: the box's z
+ * extent and grid[2] are those of the halo-widened slab, cut from the global
+ * grid at node planes (node spacing as in the global grid), every other
+ * field as for the whole system. Needs dim 3, boundary 0 (walls), chem_mode
+ * 0 and none of hard_sphere, deposit_kernel 1; pde_bc 0 or 1. capacity >= 1
+ * is the most cells (owned and ghosts) it will hold; open_faces is a mask of
+ * CHEMO_OPEN_ZLO / CHEMO_OPEN_ZHI. The deposit always goes to the source
+ * and consumption grids (read by chemo_slab_planes grids 1 and 2), the PDE
+ * runs after it on one stream. A move that leaves the box through an open
+ * face is clamped and latched as CHEMO_EDOMAIN (the halo was too thin).
+ * chemo_read_state, chemo_write_state, chemo_record*, chemo_observables,
+ * chemo_histogram and the stage calls return CHEMO_ENOTSUP for sub-domains
+ * (read cells with chemo_slab_select; the field with chemo_read_field or
+ * chemo_slab_planes). */
+int chemo_create_subdomain(const chemo_params *params, int64_t capacity, uint32_t open_faces, void *stream,
+                           chemo_sim **out);
+
+/* Replaces the cells of a sub-domain by n records (0 <= n <= capacity,
+ * host or device memory as mem_kind; device arrays 16-byte aligned) and
+ * bins them; the field, the step index and the source grids are kept.
+ * Positions outside the box are clamped and latched (CHEMO_EDOMAIN), species
+ * out of range taken as 0 and latched. */
+int chemo_slab_ingest(chemo_sim *sim, int64_t n, const chemo_cell *cells, int mem_kind, void *stream);
+
+/* Appends the sub-domain's own (non-ghost) cells to up to 4 targets (each
+ * cell to every target whose [z0, z1) holds it), asynchronously on stream;
+ * targets is host memory read during the call. */
+int chemo_slab_select(chemo_sim *sim, int32_t ntargets, const chemo_slab_target *targets, void *stream);
+
+/* Planes plane0 .. plane0 + nplanes - 1 (z index of the sub-domain's grid;
+ * g[0] x g[1] floats each, C-order) of grid 0 (c, the current field), 1 (the
+ * source S deposited since the last field step) or 2 (the consumption rate R
+ * deposited since then), against buf (device memory of at least
+ * nplanes x g[1] x g[0] floats; the call cannot check its size):
+ * op 0 reads the planes into buf, 1 writes buf into them, 2 adds buf to
+ * them. Asynchronous on stream. */
+#define CHEMO_PLANES_READ 0
+#define CHEMO_PLANES_WRITE 1
+#define CHEMO_PLANES_ADD 2
+int chemo_slab_planes(chemo_sim *sim, int32_t grid, int32_t op, int64_t plane0, int64_t nplanes, float *buf,
+                      void *stream);
+
+/* The two halves of chemo_step on a sub-domain: chemo_step_particles runs
+ * rows a1-a6 (pair force, drift, move, re-binning, deposit into the source
+ * grids) and advances the step index; chemo_step_field runs row a7 (the PDE
+ * substeps, consuming the source grids). chemo_step on a sub-domain runs
+ * both with no exchange between them. CHEMO_ENOTSUP for other simulations. */
+int chemo_step_particles(chemo_sim *sim, void *stream);
+int chemo_step_field(chemo_sim *sim, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Pair forces without device allocation.                                  */
 /* ---------------------------------------------------------------------- */
 

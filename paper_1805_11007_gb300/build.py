@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libchemo_gb300.so")
-SOURCES = ["kernels.cu", "chemo_capi.cu", "noalloc.cu", "adjoint.cu", "observe.cu"]
+SOURCES = ["kernels.cu", "chemo_capi.cu", "noalloc.cu", "adjoint.cu", "observe.cu", "slabs.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

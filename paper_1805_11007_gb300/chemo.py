@@ -95,6 +95,30 @@ class chemo_info(ctypes.Structure):
     ]
 
 
+# Sub-domains of a z-slab decomposition (include/chemo.h): a cell in transit
+# is one 32-byte record, tag = id | species << 29 (id GHOST_ID for a ghost).
+CELL_DTYPE = np.dtype([("x", "<f4"), ("y", "<f4"), ("z", "<f4"), ("tag", "<u4"),
+                       ("dx", "<f4"), ("dy", "<f4"), ("dz", "<f4"), ("reserved", "<u4")])
+CELL_FLOATS = 8
+GHOST_ID = 0x1FFFFFFF
+SPECIES_SHIFT = 29
+OPEN_ZLO, OPEN_ZHI = 1, 2
+PLANES_READ, PLANES_WRITE, PLANES_ADD = 0, 1, 2
+SLAB_TARGETS = 4
+
+
+class chemo_slab_target(ctypes.Structure):
+    _fields_ = [
+        ("z0", ctypes.c_float),
+        ("z1", ctypes.c_float),
+        ("own0", ctypes.c_float),
+        ("own1", ctypes.c_float),
+        ("out", ctypes.c_void_p),
+        ("capacity", ctypes.c_int64),
+        ("count", ctypes.c_void_p),
+    ]
+
+
 def make_params(d: dict) -> chemo_params:
     """chemo_params from a dict keyed by the field names (missing = 0 /
     library defaults; per-species lists may be shorter than 8)."""
@@ -205,6 +229,12 @@ def _declare(L):
         "chemo_stage_drift": ([vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_stage_deposit": ([vp, vp, vp, ctypes.c_int, vp], ctypes.c_int),
         "chemo_forces_noalloc": ([PP, i64, vp, vp, vp, vp], ctypes.c_int),
+        "chemo_create_subdomain": ([PP, i64, ctypes.c_uint32, vp, ctypes.POINTER(vp)], ctypes.c_int),
+        "chemo_slab_ingest": ([vp, i64, vp, ctypes.c_int, vp], ctypes.c_int),
+        "chemo_slab_select": ([vp, i32, ctypes.POINTER(chemo_slab_target), vp], ctypes.c_int),
+        "chemo_slab_planes": ([vp, i32, i32, i64, i64, vp, vp], ctypes.c_int),
+        "chemo_step_particles": ([vp, vp], ctypes.c_int),
+        "chemo_step_field": ([vp, vp], ctypes.c_int),
         "chemo_set_allocator": ([vp, vp, vp], ctypes.c_int),  # callbacks as pointers (NULL allowed)
     }
     for name, (args, res) in sigs.items():
@@ -589,6 +619,87 @@ def chemo_forces_noalloc(params: dict, pos, species, F_out, stream=None):
     prm = make_params(params)
     n = int(pos.shape[0])
     _check(lib().chemo_forces_noalloc(ctypes.byref(prm), n, pp, sp, fp, _stream(stream)), "chemo_forces_noalloc")
+
+
+def chemo_create_subdomain(params: dict, capacity: int, open_faces: int, stream=None) -> Sim:
+    """An empty sub-domain (a z-slab with its halo) holding up to `capacity`
+    cells; open_faces is a mask of OPEN_ZLO / OPEN_ZHI."""
+    out = ctypes.c_void_p()
+    prm = make_params(params)
+    _check(lib().chemo_create_subdomain(ctypes.byref(prm), int(capacity), int(open_faces), _stream(stream),
+                                        ctypes.byref(out)), "chemo_create_subdomain")
+    sim = Sim(out, params, 0)
+    sim.capacity = int(capacity)
+    return sim
+
+
+def _cells(cells):
+    """(pointer, mem_kind, count, keepalive) of a cell-record buffer: a CUDA or
+    CPU float32 tensor of shape (m, 8), or a numpy array of CELL_DTYPE."""
+    try:
+        import torch
+        if isinstance(cells, torch.Tensor):
+            if cells.dim() != 2 or cells.shape[1] != CELL_FLOATS or cells.dtype != torch.float32:
+                raise TypeError("cell records must be a float32 tensor of shape (m, 8)")
+            if not cells.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            return (ctypes.c_void_p(cells.data_ptr()), MEM_DEVICE if cells.is_cuda else MEM_HOST,
+                    int(cells.shape[0]), cells)
+    except ImportError:
+        pass
+    a = np.asarray(cells)
+    if a.dtype != CELL_DTYPE or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError("numpy cell records must be a C-contiguous CELL_DTYPE array")
+    return a.ctypes.data_as(ctypes.c_void_p), MEM_HOST, int(a.shape[0]), a
+
+
+def chemo_slab_ingest(sim: Sim, cells, n=None, stream=None):
+    """Replaces the sub-domain's cells by the first n records of `cells`."""
+    ptr, kind, m, _k = _cells(cells)
+    n = m if n is None else int(n)
+    if n > m:
+        raise ValueError("n = %d exceeds the %d records given" % (n, m))
+    _check(lib().chemo_slab_ingest(_h(sim), n, ptr, kind, _stream(stream)), "chemo_slab_ingest")
+    sim.n = n
+
+
+def chemo_slab_select(sim: Sim, targets, stream=None):
+    """targets: sequence of (z0, z1, own0, own1, out, count) with out a CUDA
+    float32 tensor (capacity, 8) and count a CUDA int64 tensor of 2 counters
+    that the call adds to."""
+    import torch
+    arr = (chemo_slab_target * max(len(targets), 1))()
+    keep = []
+    for k, (z0, z1, own0, own1, out, count) in enumerate(targets):
+        if not (out.is_cuda and count.is_cuda and count.dtype == torch.int64 and count.numel() >= 2):
+            raise TypeError("out and count must be CUDA tensors; count int64 with 2 entries")
+        if out.dim() != 2 or out.shape[1] != CELL_FLOATS or out.dtype != torch.float32 or not out.is_contiguous():
+            raise TypeError("out must be a contiguous float32 tensor of shape (capacity, 8)")
+        arr[k] = chemo_slab_target(float(z0), float(z1), float(own0), float(own1), out.data_ptr(),
+                                   int(out.shape[0]), count.data_ptr())
+        keep.append((out, count))
+    _check(lib().chemo_slab_select(_h(sim), len(targets), arr, _stream(stream)), "chemo_slab_select")
+
+
+def chemo_slab_planes(sim: Sim, grid: int, op: int, plane0: int, nplanes: int, buf, stream=None):
+    """Reads (op 0), writes (1) or adds (2) z-planes plane0.. of grid 0 (c),
+    1 (source) or 2 (consumption) against the CUDA float32 tensor buf."""
+    bp, kind, _k = _buf(buf, np.float32)
+    if kind != MEM_DEVICE:
+        raise ValueError("chemo_slab_planes takes a device buffer")
+    need = max(int(nplanes), 0) * int(sim.params["grid"][0]) * int(sim.params["grid"][1])
+    if buf.numel() < need:
+        raise ValueError("buf holds %d floats, %d planes need %d" % (buf.numel(), int(nplanes), need))
+    _check(lib().chemo_slab_planes(_h(sim), int(grid), int(op), int(plane0), int(nplanes), bp, _stream(stream)),
+           "chemo_slab_planes")
+
+
+def chemo_step_particles(sim: Sim, stream=None):
+    _check(lib().chemo_step_particles(_h(sim), _stream(stream)), "chemo_step_particles")
+
+
+def chemo_step_field(sim: Sim, stream=None):
+    _check(lib().chemo_step_field(_h(sim), _stream(stream)), "chemo_step_field")
 
 
 # ---------------------------------------------------------------------------

@@ -556,6 +556,7 @@ extern "C" int chemo_record(chemo_sim *s, int64_t nsteps, int32_t every, void *s
 extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, int64_t store_bytes, void *stream)
 {
     ChemoRange nvtx_range("chemo_record_stored");
+    if (s && s->kp.sub) return eng_fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_record_stored");
     if (!s || nsteps < 0 || every < 1) return eng_fail(CHEMO_EINVAL, "chemo_record: bad arguments");
     if (int r = check_adjoint_model(s)) return r;
     cudaStream_t st = (cudaStream_t)stream;

@@ -714,44 +714,55 @@ int chemo_create(const chemo_params *params, int64_t n, const float *pos, const 
     return chemo_create_batch(params, 1, &n, pos, species, mem_kind, stream, out);
 }
 
-int chemo_create_batch(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
-                       const float *pos, const uint8_t *species, int mem_kind, void *stream, chemo_sim **out)
+}  // extern "C"
+
+namespace {
+
+// A sub-domain keeps every deposit in the source grids and runs its PDE
+// after the particle part on one stream (the halo planes of the source are
+// exchanged in between).
+void apply_subdomain(KP &kp, uint32_t open_faces)
 {
-    ChemoRange nvtx_range("chemo_create_batch");
-    g_last_error[0] = 0;
-    if (!params || !out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and out are required");
-    *out = nullptr;
-    if (int r = check_mem_kind(mem_kind)) return r;
-    if (int r = check_params(*params)) return r;
-    if (replicates < 1 || replicates > 65535) return fail(CHEMO_EINVAL, "replicates = %d out of range [1, 65535]", replicates);
-    if (replicates > 1 && params->dim != 2) return fail(CHEMO_EINVAL, "replicates > 1 needs dim = 2");
-    std::vector<int64_t> off((size_t)replicates + 1, 0);
-    for (int r = 0; r < replicates; ++r) {
-        const int64_t m = n_per_replicate[r];
-        if (m < 0 || m > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "replicate %d: n = %lld out of range", r, (long long)m);
-        off[(size_t)r + 1] = off[(size_t)r] + m;
-        if (off[(size_t)r + 1] > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "more than 2^29 cells in total");
-    }
+    kp.sub = 1;
+    kp.open_z = (int)open_faces;
+    kp.fused_deposit = 0;
+    kp.overlap = 0;
+}
+
+int launches_per_step(const KP &kp)
+{
+    const int64_t n = kp.n;
+    return (n > 0 ? (kp.pairs && kp.search == 4 ? 2 : 1) : 0) + 2 + (kp.has_grid ? kp.pde_launches : 0) +
+           (kp.hard_sphere ? (n > 0 ? 3 : 2) : 0) + (kp.kde && kp.has_grid ? 1 : 0);
+}
+
+// Creates a simulation of `replicates` layers holding off[replicates] cells
+// (buffers for `capacity` >= that many); a sub-domain when sub.
+int create_sim(const chemo_params *params, int32_t replicates, const std::vector<int64_t> &off, int64_t capacity,
+               bool sub, uint32_t open_faces, const float *pos, const uint8_t *species, int mem_kind,
+               cudaStream_t st, chemo_sim **out)
+{
     const int64_t n = off[(size_t)replicates];
-    if (n > 0 && mem_kind == CHEMO_MEM_DEVICE && !(is_device_ptr(pos) && is_device_ptr(species)))
-        return fail(CHEMO_EINVAL, "mem_kind is DEVICE but pos/species are not device pointers");
     chemo_sim *s = new (std::nothrow) chemo_sim();
     if (!s) return fail(CHEMO_ENOMEM, "host allocation failed");
     s->mem = eng_allocator();
     s->prm = *params;
+    s->capacity = capacity;
     KP &kp = s->kp;
     kp.n = n;
     kp.layers = replicates;
     kp.layer_off = nullptr;
+    kp.sub = 0;
+    kp.open_z = 0;
     s->layer_off_host = off;
     int r;
-    if ((r = fill_layout(*params, n, kp)) || (r = fill_grid(*params, kp))) {
+    if ((r = fill_layout(*params, capacity, kp)) || (r = fill_grid(*params, kp))) {
         delete s;
         return r;
     }
+    if (sub) apply_subdomain(kp, open_faces);
     fill_model(*params, kp);
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t N = (size_t)std::max<int64_t>(n, 1);
+    const size_t N = (size_t)std::max<int64_t>(capacity, 1);
     void *p;
 #define ALLOC(field, bytes)                         \
     if ((r = dalloc(s, &p, (bytes)))) {             \
@@ -835,9 +846,171 @@ int chemo_create_batch(const chemo_params *params, int32_t replicates, const int
         return r;
     }
     // launches per step: particles, scan, scatter, and the PDE substeps
-    s->launches_per_step = (n > 0 ? (kp.pairs && kp.search == 4 ? 2 : 1) : 0) + 2 + (kp.has_grid ? kp.pde_launches : 0) +
-                           (kp.hard_sphere ? (n > 0 ? 3 : 2) : 0) + (kp.kde && kp.has_grid ? 1 : 0);
+    s->launches_per_step = launches_per_step(kp);
     *out = s;
+    return CHEMO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int chemo_create_batch(const chemo_params *params, int32_t replicates, const int64_t *n_per_replicate,
+                       const float *pos, const uint8_t *species, int mem_kind, void *stream, chemo_sim **out)
+{
+    ChemoRange nvtx_range("chemo_create_batch");
+    g_last_error[0] = 0;
+    if (!params || !out || !n_per_replicate) return fail(CHEMO_EINVAL, "params, n_per_replicate and out are required");
+    *out = nullptr;
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (int r = check_params(*params)) return r;
+    if (replicates < 1 || replicates > 65535) return fail(CHEMO_EINVAL, "replicates = %d out of range [1, 65535]", replicates);
+    if (replicates > 1 && params->dim != 2) return fail(CHEMO_EINVAL, "replicates > 1 needs dim = 2");
+    std::vector<int64_t> off((size_t)replicates + 1, 0);
+    for (int r = 0; r < replicates; ++r) {
+        const int64_t m = n_per_replicate[r];
+        if (m < 0 || m > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "replicate %d: n = %lld out of range", r, (long long)m);
+        off[(size_t)r + 1] = off[(size_t)r] + m;
+        if (off[(size_t)r + 1] > (int64_t)ID_MASK + 1) return fail(CHEMO_EINVAL, "more than 2^29 cells in total");
+    }
+    const int64_t n = off[(size_t)replicates];
+    if (n > 0 && mem_kind == CHEMO_MEM_DEVICE && !(is_device_ptr(pos) && is_device_ptr(species)))
+        return fail(CHEMO_EINVAL, "mem_kind is DEVICE but pos/species are not device pointers");
+    return create_sim(params, replicates, off, n, false, 0u, pos, species, mem_kind, (cudaStream_t)stream, out);
+}
+
+int chemo_create_subdomain(const chemo_params *params, int64_t capacity, uint32_t open_faces, void *stream,
+                           chemo_sim **out)
+{
+    ChemoRange nvtx_range("chemo_create_subdomain");
+    g_last_error[0] = 0;
+    if (!params || !out) return fail(CHEMO_EINVAL, "params and out are required");
+    *out = nullptr;
+    if (int r = check_params(*params)) return r;
+    const chemo_params &p = *params;
+    if (p.dim != 3) return fail(CHEMO_EINVAL, "sub-domains are z-slabs of a 3D system (dim = %d)", p.dim);
+    if (p.boundary != 0 || p.chem_mode != 0)
+        return fail(CHEMO_ENOTSUP, "sub-domains need reflecting walls (boundary 0) and the grid (chem_mode 0)");
+    if (p.hard_sphere || p.deposit_kernel != 0)
+        return fail(CHEMO_ENOTSUP, "sub-domains support neither hard_sphere nor deposit_kernel 1");
+    if (capacity < 1 || capacity > (int64_t)ID_MASK)
+        return fail(CHEMO_EINVAL, "capacity = %lld out of range [1, 2^29 - 1]", (long long)capacity);
+    if (open_faces > (CHEMO_OPEN_ZLO | CHEMO_OPEN_ZHI)) return fail(CHEMO_EINVAL, "open_faces = %u: bits 0 and 1 only", open_faces);
+    const std::vector<int64_t> off(2, 0);
+    return create_sim(params, 1, off, capacity, true, open_faces, nullptr, nullptr, CHEMO_MEM_DEVICE,
+                      (cudaStream_t)stream, out);
+}
+
+static int need_subdomain(const chemo_sim *s, const char *what)
+{
+    if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
+    if (!s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not a sub-domain (chemo_create_subdomain)", what);
+    return CHEMO_OK;
+}
+
+int chemo_slab_ingest(chemo_sim *s, int64_t n, const chemo_cell *cells, int mem_kind, void *stream)
+{
+    ChemoRange nvtx_range("chemo_slab_ingest");
+    g_last_error[0] = 0;
+    if (int r = need_subdomain(s, "chemo_slab_ingest")) return r;
+    if (int r = check_mem_kind(mem_kind)) return r;
+    if (n < 0 || n > s->capacity)
+        return fail(CHEMO_EINVAL, "n = %lld out of range [0, capacity = %lld]", (long long)n, (long long)s->capacity);
+    if (n > 0 && !cells) return fail(CHEMO_EINVAL, "cells is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)n * sizeof(chemo_cell);
+    const float4 *rec = reinterpret_cast<const float4 *>(cells);
+    if (n > 0 && mem_kind == CHEMO_MEM_DEVICE) {
+        if (((uintptr_t)cells & 15u) != 0) return fail(CHEMO_EINVAL, "cells must be 16-byte aligned");
+        if (!is_device_ptr(cells)) return fail(CHEMO_EINVAL, "mem_kind is DEVICE but cells is not a device pointer");
+    } else if (n > 0) {
+        void *tmp = nullptr;
+        if (int r = scratch(s, bytes, &tmp)) return r;
+        CUDA_TRY(cudaMemcpyAsync(tmp, cells, bytes, cudaMemcpyHostToDevice, st));
+        rec = static_cast<const float4 *>(tmp);
+    }
+    if (n != s->kp.n) {
+        drop_graphs(s);  // graphs hold the old count
+        s->kp.n = n;
+        s->launches_per_step = launches_per_step(s->kp);
+    }
+    const KP k = view(s);
+    CUDA_TRY(launch_pack_cells(k, rec, st));
+    if (int r = sort_from_u(s, k, st)) return r;
+    if (mem_kind == CHEMO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(st));
+    return CHEMO_OK;
+}
+
+int chemo_slab_select(chemo_sim *s, int32_t ntargets, const chemo_slab_target *targets, void *stream)
+{
+    g_last_error[0] = 0;
+    if (int r = need_subdomain(s, "chemo_slab_select")) return r;
+    if (ntargets < 0 || ntargets > SLAB_TARGETS) return fail(CHEMO_EINVAL, "ntargets = %d out of range [0, %d]", ntargets, SLAB_TARGETS);
+    if (ntargets > 0 && !targets) return fail(CHEMO_EINVAL, "targets is NULL");
+    SlabSelect t{};
+    t.nt = ntargets;
+    for (int k = 0; k < ntargets; ++k) {
+        const chemo_slab_target &g = targets[k];
+        if (g.capacity < 0) return fail(CHEMO_EINVAL, "target %d: negative capacity", k);
+        if (g.capacity > 0 && (!g.out || ((uintptr_t)g.out & 15u) != 0))
+            return fail(CHEMO_EINVAL, "target %d: out must be a 16-byte aligned device array", k);
+        if (!g.count || ((uintptr_t)g.count & 7u) != 0) return fail(CHEMO_EINVAL, "target %d: count must be an aligned device pointer", k);
+        t.z0[k] = g.z0;
+        t.z1[k] = g.z1;
+        t.own0[k] = g.own0;
+        t.own1[k] = g.own1;
+        t.out[k] = reinterpret_cast<float4 *>(g.out);
+        t.cap[k] = g.capacity;
+        t.count[k] = g.count;
+    }
+    CUDA_TRY(launch_slab_select(view(s), t, (cudaStream_t)stream));
+    return CHEMO_OK;
+}
+
+int chemo_slab_planes(chemo_sim *s, int32_t grid, int32_t op, int64_t plane0, int64_t nplanes, float *buf,
+                      void *stream)
+{
+    g_last_error[0] = 0;
+    if (int r = need_subdomain(s, "chemo_slab_planes")) return r;
+    const KP &kp = s->kp;
+    if (grid < 0 || grid > 2) return fail(CHEMO_EINVAL, "grid = %d: 0 (c), 1 (source) or 2 (consumption)", grid);
+    if (op < CHEMO_PLANES_READ || op > CHEMO_PLANES_ADD) return fail(CHEMO_EINVAL, "op = %d: 0 read, 1 write, 2 add", op);
+    if (plane0 < 0 || nplanes < 0 || plane0 + nplanes > kp.g[2])
+        return fail(CHEMO_EINVAL, "planes [%lld, %lld) outside [0, %d)", (long long)plane0, (long long)(plane0 + nplanes), kp.g[2]);
+    if (nplanes == 0) return CHEMO_OK;
+    if (!buf) return fail(CHEMO_EINVAL, "buf is NULL");
+    const int64_t P = (int64_t)kp.g[0] * kp.g[1];
+    float *base = grid == 0 ? kp.c[s->cur] : (grid == 1 ? kp.srcg : kp.Rg);
+    float *g = base + plane0 * P;
+    const int64_t m = nplanes * P;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (op == CHEMO_PLANES_READ) CUDA_TRY(cudaMemcpyAsync(buf, g, (size_t)m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else if (op == CHEMO_PLANES_WRITE) CUDA_TRY(cudaMemcpyAsync(g, buf, (size_t)m * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else CUDA_TRY(launch_add(g, buf, m, st));
+    return CHEMO_OK;
+}
+
+int chemo_step_particles(chemo_sim *s, void *stream)
+{
+    ChemoRange nvtx_range("chemo_step_particles");
+    g_last_error[0] = 0;
+    if (int r = need_subdomain(s, "chemo_step_particles")) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const KP kp = view(s);
+    CUDA_TRY(launch_step_particles(kp, s->cur, st, nullptr));
+    if (int r = enqueue_sort_and_density(s, kp, st, nullptr)) return r;
+    s->step += 1;
+    return CHEMO_OK;
+}
+
+int chemo_step_field(chemo_sim *s, void *stream)
+{
+    ChemoRange nvtx_range("chemo_step_field");
+    g_last_error[0] = 0;
+    if (int r = need_subdomain(s, "chemo_step_field")) return r;
+    const KP kp = view(s);
+    CUDA_TRY(launch_pde(kp, s->cur, (cudaStream_t)stream, nullptr));
+    s->cur ^= (kp.pde_launches & 1);
     return CHEMO_OK;
 }
 
@@ -971,6 +1144,7 @@ int chemo_write_state(chemo_sim *s, const float *pos, const uint8_t *species, co
 {
     ChemoRange nvtx_range("chemo_write_state");
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_write_state");
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
     return ingest(s, pos, species, disp, mem_kind, (cudaStream_t)stream);
@@ -1044,6 +1218,7 @@ int chemo_read_state(chemo_sim *s, float *pos_out, uint8_t *species_out, float *
 {
     ChemoRange nvtx_range("chemo_read_state");
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_read_state");
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
     if (disp_out && !s->kp.dS) return fail(CHEMO_EINVAL, "displacement is not tracked (track_displacement = 0)");
@@ -1098,7 +1273,8 @@ int chemo_set_params(chemo_sim *s, const chemo_params *p)
     if (!same) return fail(CHEMO_EINVAL, "chemo_set_params cannot change geometry, species count or modes");
     KP k2 = s->kp;
     int r;
-    if ((r = fill_layout(*p, s->kp.n, k2)) || (r = fill_grid(*p, k2))) return r;
+    if ((r = fill_layout(*p, s->capacity, k2)) || (r = fill_grid(*p, k2))) return r;
+    if (s->kp.sub) apply_subdomain(k2, (uint32_t)s->kp.open_z);
     if (k2.nb[0] != s->kp.nb[0] || k2.nb[1] != s->kp.nb[1] || k2.nb[2] != s->kp.nb[2] ||
         k2.search != s->kp.search || k2.px != s->kp.px || k2.substeps != s->kp.substeps ||
         k2.fused_deposit != s->kp.fused_deposit || k2.overlap != s->kp.overlap)
@@ -1363,6 +1539,7 @@ int chemo_stall_scan(chemo_sim *s, uint32_t spin_limit, void *stream)
 int chemo_stage_bins(chemo_sim *s, int32_t *cells_out, int mem_kind, void *stream)
 {
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_stage_bins");
     if (!s || !cells_out) return fail(CHEMO_EINVAL, "sim and cells_out are required");
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1377,6 +1554,7 @@ int chemo_stage_bins(chemo_sim *s, int32_t *cells_out, int mem_kind, void *strea
 int chemo_stage_sort(chemo_sim *s, uint32_t *ids_out, uint32_t *bin_start_out, int mem_kind, void *stream)
 {
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_stage_sort");
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1401,6 +1579,7 @@ int chemo_stage_sort(chemo_sim *s, uint32_t *ids_out, uint32_t *bin_start_out, i
 int chemo_stage_forces(chemo_sim *s, float *F_out, int32_t *count_out, uint64_t *idsum_out, int mem_kind, void *stream)
 {
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_stage_forces");
     if (!s || !F_out) return fail(CHEMO_EINVAL, "sim and F_out are required");
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1421,6 +1600,7 @@ int chemo_stage_forces(chemo_sim *s, float *F_out, int32_t *count_out, uint64_t 
 int chemo_stage_drift(chemo_sim *s, float *drift_out, int mem_kind, void *stream)
 {
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_stage_drift");
     if (!s || !drift_out) return fail(CHEMO_EINVAL, "sim and drift_out are required");
     if (int r = check_mem_kind(mem_kind)) return r;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1435,6 +1615,7 @@ int chemo_stage_drift(chemo_sim *s, float *drift_out, int mem_kind, void *stream
 int chemo_stage_deposit(chemo_sim *s, float *S_out, float *R_out, int mem_kind, void *stream)
 {
     g_last_error[0] = 0;
+    if (s && s->kp.sub) return fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_stage_deposit");
     if (!s) return fail(CHEMO_EINVAL, "sim is NULL");
     if (int r = check_mem_kind(mem_kind)) return r;
     if (!s->kp.has_grid) return fail(CHEMO_EINVAL, "this simulation has no grid (chem_mode 1)");

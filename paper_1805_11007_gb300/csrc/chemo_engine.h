@@ -57,6 +57,7 @@ struct chemo_sim {
     size_t scratch_bytes = 0;
     chemo_tape *tape = nullptr;  // recorded run for the adjoint (adjoint.cu)
     std::vector<int64_t> layer_off_host;  // replicate offsets (layers + 1), host copy
+    int64_t capacity = 0;        // cells the buffers hold (kp.n <= capacity; kp.n changes only in sub-domains)
 };
 
 // Engine services used by adjoint.cu (implemented in chemo_capi.cu).

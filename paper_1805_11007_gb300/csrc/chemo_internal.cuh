@@ -51,6 +51,11 @@ struct KP {
     // stored in .w as the id local to the layer; its Philox key is seed + l.
     int layers;
     const int64_t *layer_off;    // device, layers + 1 entries (NULL when layers == 1)
+    // Sub-domain of a z-slab decomposition (sub = 1): cells with id ID_MASK
+    // are ghosts (copies of a neighbour's cells: they exert pair forces but
+    // are neither moved nor deposited). open_z bit 0 / 1: the z = lo / hi
+    // face is an inner face (no reflection, no half control volume).
+    int sub, open_z;
     // species tables (index s * MAXS + t)
     int ns;
     float rc2[MAXS * MAXS];      // r_c,st^2
@@ -388,6 +393,21 @@ cudaError_t launch_unsort(const KP &kp, float *pos, uint8_t *sp, float *disp, cu
 cudaError_t launch_philox(uint64_t seed, const uint32_t *ctr, uint32_t *out, int64_t n, cudaStream_t st);
 cudaError_t launch_init_positions(int dim, int periodic, const double *lo, const double *hi, uint64_t seed, int64_t n,
                                   int64_t n_alpha, float sigma_frac, float *pos, uint8_t *sp, cudaStream_t st);
+// Sub-domains of a z-slab decomposition (slabs.cu). launch_pack_cells ingests
+// kp.n records (two float4 each: x, y, z, tag | dx, dy, dz, 0) into U and
+// counts their bins; launch_slab_select appends the sorted state's own cells
+// to up to SLAB_TARGETS targets; launch_add adds n floats of src to dst.
+constexpr int SLAB_TARGETS = 4;
+struct SlabSelect {
+    int nt;
+    float z0[SLAB_TARGETS], z1[SLAB_TARGETS], own0[SLAB_TARGETS], own1[SLAB_TARGETS];
+    float4 *out[SLAB_TARGETS];
+    int64_t cap[SLAB_TARGETS];
+    unsigned long long *count[SLAB_TARGETS];
+};
+cudaError_t launch_pack_cells(const KP &kp, const float4 *rec, cudaStream_t st);
+cudaError_t launch_slab_select(const KP &kp, const SlabSelect &t, cudaStream_t st);
+cudaError_t launch_add(float *dst, const float *src, int64_t n, cudaStream_t st);
 cudaError_t launch_stage_bins(const KP &kp, int32_t *cells, cudaStream_t st);
 cudaError_t launch_stage_sort(const KP &kp, uint32_t *ids, uint32_t *bin_starts, cudaStream_t st);
 cudaError_t launch_stage_forces(const KP &kp, float *F, int32_t *count, unsigned long long *idsum,

@@ -968,6 +968,12 @@ __global__ void __launch_bounds__(BT, (HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
         }
     }
     if (!valid) return;
+    if (kp.sub && id == ID_MASK) {  // a ghost stays put: its own sub-domain moves it
+        kp.U[j] = me;
+        if (kp.dS) kp.dU[j] = kp.dS[j];
+        kp.slot[j] = count_bin(kp.cnt_nxt, key_of(kp, me), kp.err);
+        return;
+    }
     if (taping) {  // recorded for the adjoint: the state before the move and the pair force
         const int64_t gi = gid_of(kp, me);
         const int64_t r = ((int64_t)tk * kp.n + gi) * DIM;
@@ -1030,7 +1036,10 @@ __global__ void __launch_bounds__(BT, (HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
     } else {
         xb = reflect_axis(x1, kp.lo[0], kp.hi[0]);
         yb = reflect_axis(y1, kp.lo[1], kp.hi[1]);
-        zb = DIM == 3 ? reflect_axis(z1, kp.lo[2], kp.hi[2]) : me.z;
+        if (DIM == 3 && kp.open_z)  // walls only where the face is the system's
+            zb = reflect_axis(z1, (kp.open_z & 1) ? -INFINITY : kp.lo[2], (kp.open_z & 2) ? INFINITY : kp.hi[2]);
+        else
+            zb = DIM == 3 ? reflect_axis(z1, kp.lo[2], kp.hi[2]) : me.z;
     }
     const bool finite = isfinite(x1) && isfinite(y1) && (DIM == 2 || isfinite(z1));
     if (!finite) {
@@ -1038,6 +1047,10 @@ __global__ void __launch_bounds__(BT, (HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
         xb = me.x;
         yb = me.y;
         zb = me.z;
+    }
+    if (DIM == 3 && kp.open_z && (zb < kp.lo[2] || zb > kp.hi[2])) {  // beyond the halo of an inner face
+        set_err(kp, ERR_DOMAIN);
+        zb = fminf(fmaxf(zb, kp.lo[2]), kp.hi[2]);
     }
     if (kp.dS) {
         float4 d = kp.dS[j];
@@ -1343,7 +1356,7 @@ __device__ __forceinline__ void deposit_cic(const KP &kp, float4 u, int sp, floa
         if (DIM == 3) wr *= bz ? fz : 1.f - fz;
         if (walls) {
             if (y == 0 || y == kp.g[1] - 1) wr *= 2.f;
-            if (DIM == 3 && (z == 0 || z == kp.g[2] - 1)) wr *= 2.f;
+            if (DIM == 3 && ((z == 0 && !(kp.open_z & 1)) || (z == kp.g[2] - 1 && !(kp.open_z & 2)))) wr *= 2.f;
         }
         float w0 = (1.f - fx) * wr, w1 = fx * wr;
         if (walls) {
@@ -1394,7 +1407,8 @@ __global__ void __launch_bounds__(TPB) k_scatter(KP kp, int cur, int advance)
     }
     kp.S[dst] = u;
     if (kp.dS) kp.dS[dst] = kp.dU[j];
-    if (advance && kp.has_grid && kp.chem_mode == 0 && !kp.kde) {
+    if (advance && kp.has_grid && kp.chem_mode == 0 && !kp.kde &&
+        !(kp.sub && (__float_as_uint(u.w) & ID_MASK) == ID_MASK)) {  // a ghost's owner deposits it
         const int sp = (int)(__float_as_uint(u.w) >> SP_SHIFT);
         if (kp.fused_deposit)
             deposit_cic<DIM>(kp, u, sp, kp.c[cur ^ 1], nullptr, kp.c[cur], true);

@@ -145,6 +145,7 @@ __global__ void __launch_bounds__(OTPB) k_histogram(KP kp, int hx, int hy, int h
 extern "C" int chemo_observables(chemo_sim *s, double *out, int mem_kind, void *stream)
 {
     ChemoRange nvtx_range("chemo_observables");
+    if (s && s->kp.sub) return eng_fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_observables");
     if (!s || !out) return eng_fail(CHEMO_EINVAL, "sim and out are required");
     if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE) return eng_fail(CHEMO_EINVAL, "bad mem_kind");
     cudaStream_t st = (cudaStream_t)stream;
@@ -181,6 +182,7 @@ extern "C" int chemo_observables(chemo_sim *s, double *out, int mem_kind, void *
 extern "C" int chemo_histogram(chemo_sim *s, const int32_t *shape, float *hist_out, int mem_kind, void *stream)
 {
     ChemoRange nvtx_range("chemo_histogram");
+    if (s && s->kp.sub) return eng_fail(CHEMO_ENOTSUP, "%s: not for sub-domains", "chemo_histogram");
     if (!s || !shape || !hist_out) return eng_fail(CHEMO_EINVAL, "sim, shape and hist_out are required");
     if (mem_kind != CHEMO_MEM_HOST && mem_kind != CHEMO_MEM_DEVICE) return eng_fail(CHEMO_EINVAL, "bad mem_kind");
     const KP kp = eng_view(s);

@@ -198,3 +198,69 @@ def test_autotune_needs_trial_steps(chemo):
     with pytest.raises(chemo.ChemoError) as ei:
         chemo.chemo_autotune(p, [0], np.zeros((0, 2), np.float32), np.zeros(0, np.uint8), trial_steps=0)
     assert ei.value.status == chemo.EINVAL
+
+
+def test_slab_structs_match_the_binding(chemo, tmp_path):
+    """chemo_cell is 32 bytes laid out as CELL_DTYPE; chemo_slab_target as
+    the ctypes structure."""
+    prog = tmp_path / "slab.c"
+    cell = list(chemo.CELL_DTYPE.names)
+    tgt = [f for f, _ in chemo.chemo_slab_target._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "chemo.h"', "int main(void){",
+             'printf("%zu %zu\\n", sizeof(chemo_cell), sizeof(chemo_slab_target));']
+    lines += ['printf("c %s %%zu\\n", offsetof(chemo_cell, %s));' % (f, f) for f in cell]
+    lines += ['printf("t %s %%zu\\n", offsetof(chemo_slab_target, %s));' % (f, f) for f in tgt]
+    lines += ['printf("g %u %u %u\\n", CHEMO_GHOST_ID, CHEMO_OPEN_ZLO, CHEMO_OPEN_ZHI);', "return 0;}"]
+    prog.write_text("\n".join(lines))
+    exe = tmp_path / "slab"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    sc, st = map(int, out[0].split())
+    assert sc == chemo.CELL_DTYPE.itemsize == 32
+    assert st == ctypes.sizeof(chemo.chemo_slab_target)
+    for line in out[1:]:
+        f = line.split()
+        if f[0] == "c":
+            assert chemo.CELL_DTYPE.fields[f[1]][1] == int(f[2]), f[1]
+        elif f[0] == "t":
+            assert getattr(chemo.chemo_slab_target, f[1]).offset == int(f[2]), f[1]
+        else:
+            assert [int(v) for v in f[1:]] == [chemo.GHOST_ID, chemo.OPEN_ZLO, chemo.OPEN_ZHI]
+
+
+@pytest.mark.parametrize("case,status", [("dim2", "EINVAL"), ("periodic", "ENOTSUP"), ("hard_sphere", "ENOTSUP"),
+                                         ("kde", "ENOTSUP"), ("fixed_gradient", "ENOTSUP"),
+                                         ("capacity", "EINVAL"), ("faces", "EINVAL")])
+def test_subdomain_arguments_rejected_on_host(chemo, case, status):
+    """chemo_create_subdomain checks its arguments before touching the
+    device: 3D walls with a grid, no hard spheres or kernel density, a
+    capacity of 1 .. 2^29 - 1, face bits 0 and 1 only."""
+    from paper_1805_11007_gb300 import workloads as wl
+    p = wl.params("clumps_grid_3d", grid=[8, 8, 8])
+    cap, faces = 100, chemo.OPEN_ZLO | chemo.OPEN_ZHI
+    if case == "dim2":
+        p = wl.params("walls_grid_2d")
+    elif case == "periodic":
+        p = dict(p, boundary=1, pde_bc=2)
+    elif case == "hard_sphere":
+        p = dict(p, hard_sphere=1)
+    elif case == "kde":
+        p = dict(p, deposit_kernel=1)
+    elif case == "fixed_gradient":
+        p = dict(p, chem_mode=1)
+    elif case == "capacity":
+        cap = 0
+    else:
+        faces = 4
+    with pytest.raises(chemo.ChemoError) as ei:
+        chemo.chemo_create_subdomain(p, cap, faces)
+    assert ei.value.status == getattr(chemo, status)
+
+
+def test_slab_calls_need_a_subdomain(chemo):
+    L = chemo.lib()
+    assert L.chemo_slab_ingest(None, 0, None, chemo.MEM_HOST, None) == chemo.EINVAL
+    assert L.chemo_slab_select(None, 0, None, None) == chemo.EINVAL
+    assert L.chemo_slab_planes(None, 0, 0, 0, 0, None, None) == chemo.EINVAL
+    assert L.chemo_step_particles(None, None) == chemo.EINVAL
+    assert L.chemo_step_field(None, None) == chemo.EINVAL
