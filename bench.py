@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-slabs", action="store_true")
     return ap.parse_args()
 
 
@@ -480,6 +481,39 @@ def variants_leg(chemo, wl, devc, stream, steps=200):
     return out
 
 
+def slabs_leg(chemo, wl, steps=20, counts=(1, 2, 3)):
+    """Wall-clock ms per step of the 1M-cell 3D clump workload decomposed into
+    K z-slabs (slabs.py), every sub-domain on this GPU on its own stream, the
+    exchanges included (the host reads the selection counters once per step
+    and synchronises), for each K in counts; K = 1 is the same driver with
+    one sub-domain (it still selects and re-ingests its cells every step)."""
+    import torch
+    from paper_1805_11007_gb300 import slabs
+    p, pos, sp = wl.initial_state("clumps_grid_3d")
+    out = {"workload": "clumps_grid_3d: 3D, N=%d, 256^3 grid, %d steps after 3 warm-up steps" % (pos.shape[0], steps),
+           "how": "slabs.create_local + SlabRun.step (particles, fold, field, halo, select, count read-back, "
+                  "ingest per step); wall clock between device synchronisations"}
+    for K in counts:
+        run = slabs.create_local(p, pos, sp, K)
+        try:
+            for _ in range(3):
+                run.step()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                run.step()
+            torch.cuda.synchronize()
+            ms = (time.perf_counter() - t0) * 1e3 / steps
+            for sub in run.subs.values():
+                sub.check()
+            out["K=%d" % K] = {"ms_per_step": ms, "particle_steps_per_s": pos.shape[0] / (ms * 1e-3),
+                               "halo_planes": run.layout.H, "cut_planes": run.layout.P,
+                               "cells_per_subdomain": [int(s.sim.n) for s in run.subs.values()]}
+        finally:
+            slabs.close_run(run)
+    return out
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -654,6 +688,10 @@ def main():
     if rank == 0 and not args.no_variants:
         variants = variants_leg(chemo, wl, devc, stream)
 
+    slab_runs = None
+    if rank == 0 and world == 1 and not args.no_slabs:
+        slab_runs = slabs_leg(chemo, wl)
+
     ensemble = None
     if not args.no_ensemble:
         ensemble = ensemble_leg(chemo, wl, devc, stream, rank, world, dist, barrier)
@@ -685,6 +723,7 @@ def main():
             "adjoint": adjoint,
             "ensemble": ensemble,
             "variants": variants,
+            "slabs": slab_runs,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
