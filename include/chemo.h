@@ -509,9 +509,10 @@ int chemo_slab_planes(chemo_sim *sim, int32_t grid, int32_t op, int64_t plane0, 
 
 /* The two halves of chemo_step on a sub-domain: chemo_step_particles runs
  * rows a1-a6 (pair force, drift, move, re-binning, deposit into the source
- * grids) and advances the step index; chemo_step_field runs row a7 (the PDE
- * substeps, consuming the source grids). chemo_step on a sub-domain runs
- * both with no exchange between them. CHEMO_ENOTSUP for other simulations. */
+ * grids, which it clears first) and advances the step index;
+ * chemo_step_field runs row a7 (the PDE substeps, reading the source grids).
+ * chemo_step on a sub-domain runs both with no exchange between them.
+ * CHEMO_ENOTSUP for other simulations. */
 int chemo_step_particles(chemo_sim *sim, void *stream);
 int chemo_step_field(chemo_sim *sim, void *stream);
 

@@ -407,10 +407,13 @@ int fill_grid(const chemo_params &p, KP &kp)
     // one launch (the halo of a tile grows by one node per substep)
     kp.pde_multi = (p.dim == 2 && kp.substeps > 1) ? 1 : 0;
     kp.pde_launches = kp.pde_multi ? (kp.substeps + PDE_MULTI_MAX - 1) / PDE_MULTI_MAX : kp.substeps;
-    kp.zero_src = (kp.pde_multi && p.deposit_kernel == 0) ? 1 : 0;
     // one substep: the CIC deposit goes straight into c^{n+1} (the density
     // kernel writes a source grid instead)
     kp.fused_deposit = (kp.substeps == 1 && p.pde_bc != 1 && p.deposit_kernel == 0) ? 1 : 0;
+    // a CIC deposit into the source grids needs them zero: the next step's
+    // particle kernel clears them (a PDE that stored zeros over the values it
+    // had just loaded ran at a tenth of the copy rate)
+    kp.zero_src = (!kp.fused_deposit && p.deposit_kernel == 0) ? 1 : 0;
     kp.overlap = kp.fused_deposit && p.pde_overlap != 1;
     return CHEMO_OK;
 }
@@ -727,6 +730,7 @@ void apply_subdomain(KP &kp, uint32_t open_faces)
     kp.open_z = (int)open_faces;
     kp.fused_deposit = 0;
     kp.overlap = 0;
+    kp.zero_src = 1;
 }
 
 int launches_per_step(const KP &kp)

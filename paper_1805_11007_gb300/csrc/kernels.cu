@@ -2208,7 +2208,14 @@ static void step_launch(const KP &kp, int cur, cudaStream_t st)
 
 cudaError_t launch_step_particles(const KP &kp, int cur, cudaStream_t st, int *launches)
 {
-    if (kp.n == 0) return cudaSuccess;
+    if (kp.n == 0) {  // no particle kernel: the source grids of the last step are cleared here
+        if (kp.zero_src && kp.has_grid) {
+            cudaError_t e = cudaMemsetAsync(kp.srcg, 0, (size_t)kp.G * sizeof(float), st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(kp.Rg, 0, (size_t)kp.G * sizeof(float), st);
+            return e;
+        }
+        return cudaSuccess;
+    }
     pair_kernel_attributes();
     if (launches && kp.pairs && kp.Fh) ++*launches;
     const bool w = kp.search == 1;
@@ -2344,7 +2351,7 @@ cudaError_t launch_pde(const KP &kp, int cur, cudaStream_t st, int *launches)
     const int use_src = kp.fused_deposit ? 0 : 1;
     int c = cur;
     for (int m = 0; m < s; ++m) {
-        const int last = m == s - 1;
+        const int last = m == s - 1 && !kp.zero_src;  // else the next particle kernel clears the sources
         if (stream) {
             if (kp.dim == 2) pde_stream_launch<2>(kp, kp.c[c], kp.c[c ^ 1], use_src, last, st);
             else pde_stream_launch<3>(kp, kp.c[c], kp.c[c ^ 1], use_src, last, st);

@@ -188,6 +188,36 @@ def test_an_empty_slab_takes_part():
         slabs.close_run(run)
 
 
+def test_an_empty_slab_receives_deposits():
+    # a grid coarser than the ghost width: cells 0.012 - 0.02 below the cut
+    # (more than 5.6 noise amplitudes beyond the 0.004 ghost band) are no
+    # ghosts of the upper slab, which holds no cell at all, yet they deposit
+    # on its first plane (within one node spacing, 0.0213, of the cut); its
+    # sources are folded in every step and must be cleared every step
+    # although it has no particle kernel to run
+    p, pos, sp = wl.initial_state("clumps_grid_3d", n=5000, grid=[48, 48, 48], dt=1e-6)
+    cut = 30
+    z_cut = np.float32(cut / 47.0)
+    rng = np.random.default_rng(4)
+    # spread in x and y so that the band is dilute (mean spacing 0.012, three
+    # times the cutoff): no pair force pushes a cell across the gap
+    pos[:, :2] = rng.random((pos.shape[0], 2)).astype(np.float32)
+    pos[:, 2] = (z_cut - rng.uniform(0.012, 0.02, pos.shape[0])).astype(np.float32)
+    c0 = wl.random_field(p, seed=5, scale=0.3)
+    run = slabs.create_local(p, pos, sp, 2, c0=c0, planes=[cut], balance=False)
+    try:
+        assert run.subs[1].sim.n == 0
+        x, s, c = pos, sp, c0
+        for n in range(4):
+            run.step()
+            assert run.subs[1].sim.n == 0
+            x1, s1, _, c1 = _gather(run)
+            assert_step_matches(p, x, s, c, x1, s1, c1, step_index=n)
+            x, s, c = x1, s1, c1
+    finally:
+        slabs.close_run(run)
+
+
 def test_a_halo_too_thin_for_a_move_is_latched():
     # noise of 0.05 per step against a box that reaches two planes of 1/47
     # beyond a face: some own cells step out of their sub-domain's box; they
@@ -275,10 +305,21 @@ def test_planes_read_write_add():
         want[5:8] += c[2:5]
         want[0:2] = -1
         assert torch.equal(out, want)
-        # the source grid: written, then consumed (cleared) by the field step
+        # the source grid: written, read by the field step (a constant field
+        # has no Laplacian, so one substep adds S and decays by dt gamma c),
+        # cleared by the next particle step before its deposit
+        chemo.chemo_write_field(sub.sim, torch.ones_like(c))
         src = torch.full((gz, 48 * 48), 0.25, device="cuda")
         chemo.chemo_slab_planes(sub.sim, 1, chemo.PLANES_WRITE, 0, gz, src)
         chemo.chemo_step_field(sub.sim)
+        after = torch.empty_like(c)
+        chemo.chemo_read_field(sub.sim, after)
+        torch.cuda.synchronize()
+        want_c = 1.0 + 0.25 - p["dt"] * p["gamma"]
+        assert torch.allclose(after, torch.full_like(after, want_c), rtol=0, atol=1e-5)
+        zero_cells = np.zeros(0, chemo.CELL_DTYPE)  # no cells: nothing is deposited again
+        chemo.chemo_slab_ingest(sub.sim, zero_cells)
+        chemo.chemo_step_particles(sub.sim)
         chemo.chemo_slab_planes(sub.sim, 1, chemo.PLANES_READ, 0, gz, src)
         torch.cuda.synchronize()
         assert torch.count_nonzero(src) == 0
