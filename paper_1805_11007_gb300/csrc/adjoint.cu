@@ -169,15 +169,25 @@ __global__ void k_adj_pde(KP kp, const float *__restrict__ mu_in, float *__restr
 
 __device__ __forceinline__ int64_t nidx(const KP &kp, const int *k) { return gidx(kp, k[0], k[1], k[2]); }
 
-// Corner m of the 2^d nodes around x: node indices, multilinear weight and
-// its gradient d(weight)/dx_b.
+// Grid cell of x per axis (lower and upper node, offset in the cell).
 template <int DIM>
-__device__ __forceinline__ void corner_of(const KP &kp, const float *x, int m, int node[3], float &w, float dw[3])
+__device__ __forceinline__ void cell_frac(const KP &kp, const float *x, int k0[3], int k1[3], float f[3])
 {
-    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
-    float f[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        k0[a] = k1[a] = 0;
+        f[a] = 0.f;
+    }
 #pragma unroll
     for (int a = 0; a < DIM; ++a) gcell(kp, a, x[a], k0[a], k1[a], f[a]);
+}
+
+// Corner m of the 2^d nodes of a grid cell: node indices, multilinear
+// weight and its gradient d(weight)/dx_b.
+template <int DIM>
+__device__ __forceinline__ void corner_w(const KP &kp, const int k0[3], const int k1[3], const float f[3], int m,
+                                         int node[3], float &w, float dw[3])
+{
     w = 1.f;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
@@ -198,28 +208,25 @@ __device__ __forceinline__ void corner_of(const KP &kp, const float *x, int m, i
     }
 }
 
-// Adds v over the block into the block's own slot dst[blockIdx.x] (no two
-// blocks share a slot; the kernels of successive steps run in order, so no
-// atomics are needed). Every thread of the block must call it.
-__device__ __forceinline__ void block_add_double(double v, double *dst, double *red)
+// Sum over the NC consecutive lanes of a cell's group (NC divides 32).
+template <int NC>
+__device__ __forceinline__ float group_sum(float v)
 {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    const int wid = threadIdx.x >> 5;
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) red[wid] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s = 0.0;
-        for (int k = 0; k < ATPB / 32; ++k) s += red[k];
-        dst[blockIdx.x] += s;
-    }
+#pragma unroll
+    for (int o = 1; o < NC; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
 }
 
-// Per-cell adjoint terms (by id), one thread per cell. Reads X^n, X^{n+1},
-// c^n, lambda_X^{n+1}, lambda_S and the step's pair force Fb (f_unit Fb =
-// dF/dinter); writes lambda_Y and the local part of lambda_X^n, scatters the
-// interpolation transpose into lambda_c and adds the parameter gradients to
-// the block's slots of dpar.
+// Per-cell adjoint terms (by id), 2^d threads per cell: thread m of a cell's
+// group takes grid corner m of the deposit transpose at X^{n+1}, of the
+// gradient interpolation at X^n with its Jacobian, and of the interpolation
+// transpose; the group adds the corners' parts with shuffles (one thread per
+// cell left the adjoint's per-cell kernel latency bound at a few warps per
+// SM). Reads X^n, X^{n+1}, c^n, lambda_X^{n+1}, lambda_S and the step's pair
+// force Fb (f_unit Fb = dF/dinter); writes lambda_Y and the local part of
+// lambda_X^n, scatters the interpolation transpose into lambda_c and adds
+// the parameter gradients to the block's slots of dpar (launched over
+// n 2^d threads).
 template <int DIM>
 __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restrict__ Xn, const float *__restrict__ Xn1,
                                                     const uint8_t *__restrict__ spec, const float *__restrict__ cn,
@@ -229,58 +236,73 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
                                                     unsigned long long step, double *dpar, int64_t pstride,
                                                     int has_grid, int lams_over_tau)
 {
-    __shared__ double red[ATPB / 32];
     constexpr int NC = 1 << DIM;
-    const int64_t i = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    static_assert(32 % NC == 0 && ATPB % 32 == 0, "a cell's threads lie in one warp");
+    __shared__ float red[ATPB / 32][2 + MAXS];
+    const int64_t t = (int64_t)blockIdx.x * ATPB + threadIdx.x;
+    const int64_t i = t / NC;
+    const int m = (int)(t % NC);
     const bool valid = i < kp.n;
-    double d_chi = 0.0, d_int = 0.0, d_Ds = 0.0;  // d_Ds: dL/dD of this cell's species
-    int sp = 0;
-    if (valid) {
-        sp = spec[i];
-        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
+    const int sp = valid ? (int)spec[i] : 0;
+    float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
+    if (valid)
         for (int a = 0; a < DIM; ++a) {
             x0[a] = Xn[i * DIM + a];
             x1[a] = Xn1[i * DIM + a];
             lx[a] = lamX1[i * DIM + a];
         }
-        // 2. deposit transpose at X^{n+1}
-        if (has_grid && kp.src[sp] != 0.f) {
+    // 2. deposit transpose at X^{n+1}: this corner's part
+    float dl[3] = {0.f, 0.f, 0.f};
+    if (valid && has_grid && kp.src[sp] != 0.f) {
+        int k0[3], k1[3], nd[3];
+        float f[3], wm, dwm[3];
+        cell_frac<DIM>(kp, x1, k0, k1, f);
+        corner_w<DIM>(kp, k0, k1, f, m, nd, wm, dwm);
+        float inv_tau = 1.f;
+        if (kp.pde_bc != 2 && !lams_over_tau)  // (already divided by tau when lams_over_tau)
+            for (int a = 0; a < DIM; ++a)
+                if (nd[a] == 0 || nd[a] == kp.g[a] - 1) inv_tau *= 2.f;
+        const float l = lamS[nidx(kp, nd)] * inv_tau * kp.src[sp];
+        for (int a = 0; a < DIM; ++a) dl[a] = l * dwm[a];
+    }
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                int nd[3];
-                float wm, dwm[3];
-                corner_of<DIM>(kp, x1, m, nd, wm, dwm);
-                float inv_tau = 1.f;
-                if (kp.pde_bc != 2 && !lams_over_tau)  // (already divided by tau when lams_over_tau)
-                    for (int a = 0; a < DIM; ++a)
-                        if (nd[a] == 0 || nd[a] == kp.g[a] - 1) inv_tau *= 2.f;
-                const float l = lamS[nidx(kp, nd)] * inv_tau * kp.src[sp];
-                for (int a = 0; a < DIM; ++a) lx[a] = fmaf(l, dwm[a], lx[a]);
+    for (int a = 0; a < DIM; ++a) lx[a] += group_sum<NC>(dl[a]);
+    // forward quantities at X^n: gradient interpolation and its Jacobian
+    const float chem = kp.chem[sp];
+    float G[3] = {0.f, 0.f, 0.f}, J[3][3] = {{0.f}};
+    const bool interp = has_grid && kp.chem_mode == 0;
+    int nd0[3] = {0, 0, 0};
+    float w0 = 0.f;
+    if (kp.chem_mode == 1) {
+        for (int a = 0; a < DIM; ++a) G[a] = kp.fixed_g[a];
+    } else if (interp) {
+        if (valid) {
+            int k0[3], k1[3];
+            float f[3], dw0[3];
+            cell_frac<DIM>(kp, x0, k0, k1, f);
+            corner_w<DIM>(kp, k0, k1, f, m, nd0, w0, dw0);
+#pragma unroll
+            for (int a = 0; a < DIM; ++a) {
+                int kp1[3] = {nd0[0], nd0[1], nd0[2]}, km1[3] = {nd0[0], nd0[1], nd0[2]};
+                kp1[a] = gnbr(kp, a, nd0[a] + 1);
+                km1[a] = gnbr(kp, a, nd0[a] - 1);
+                const float ga = (cn[nidx(kp, kp1)] - cn[nidx(kp, km1)]) * kp.inv_2h[a];
+                G[a] = w0 * ga;
+#pragma unroll
+                for (int b = 0; b < DIM; ++b) J[a][b] = dw0[b] * ga;
             }
         }
-        // forward quantities at X^n: gradient interpolation and its Jacobian
-        const float chem = kp.chem[sp];
-        float G[3] = {0.f, 0.f, 0.f}, J[3][3] = {{0.f}};
-        const bool interp = has_grid && kp.chem_mode == 0;
-        if (kp.chem_mode == 1) {
-            for (int a = 0; a < DIM; ++a) G[a] = kp.fixed_g[a];
-        } else if (interp) {
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                int nd[3];
-                float wm, dwm[3];
-                corner_of<DIM>(kp, x0, m, nd, wm, dwm);
-                for (int a = 0; a < DIM; ++a) {
-                    int kp1[3] = {nd[0], nd[1], nd[2]}, km1[3] = {nd[0], nd[1], nd[2]};
-                    kp1[a] = gnbr(kp, a, nd[a] + 1);
-                    km1[a] = gnbr(kp, a, nd[a] - 1);
-                    const float ga = (cn[nidx(kp, kp1)] - cn[nidx(kp, km1)]) * kp.inv_2h[a];
-                    G[a] = fmaf(wm, ga, G[a]);
-                    for (int b = 0; b < DIM; ++b) J[a][b] = fmaf(dwm[b], ga, J[a][b]);
-                }
-            }
+        for (int a = 0; a < DIM; ++a) {
+            G[a] = group_sum<NC>(G[a]);
+#pragma unroll
+            for (int b = 0; b < DIM; ++b) J[a][b] = group_sum<NC>(J[a][b]);
         }
-        // noise and the pre-boundary position Y (reflection signs)
+    }
+    float p_chi = 0.f, p_int = 0.f, p_Ds = 0.f;
+    if (valid) {
+        // noise and the pre-boundary position Y (reflection signs), in every
+        // thread of the group
         const uint4 rw = cell_words(kp, (uint32_t)i, step, TAG_MOVE);
         const float2 n01 = box_muller(rw.x, rw.y);
         const float xi[3] = {n01.x, n01.y, DIM == 3 ? box_muller(rw.z, rw.w).x : 0.f};
@@ -295,54 +317,65 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
                 }
             }
         }
-        // 3. boundary, 4. local terms
-        float ly[3] = {0.f, 0.f, 0.f};
-        for (int a = 0; a < DIM; ++a) {
-            ly[a] = sgn[a] * lx[a];
-            lamY[i * DIM + a] = ly[a];
-        }
+        // 3. boundary, 4. local terms (thread a of the group writes axis a)
+        float ly[3] = {0.f, 0.f, 0.f}, tx[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < DIM; ++a) ly[a] = sgn[a] * lx[a];
         for (int b = 0; b < DIM; ++b) {
-            float t = ly[b];
+            float tb = ly[b];
             if (interp && chem != 0.f) {
-                float s = 0.f;
-                for (int a = 0; a < DIM; ++a) s = fmaf(ly[a], J[a][b], s);
-                t = fmaf(kp.dt * chem, s, t);
+                float sj = 0.f;
+                for (int a = 0; a < DIM; ++a) sj = fmaf(ly[a], J[a][b], sj);
+                tb = fmaf(kp.dt * chem, sj, tb);
             }
-            lamXn[i * DIM + b] = t;
+            tx[b] = tb;
         }
-        // interpolation transpose onto the nodes
+        if (m < DIM) {
+            lamY[i * DIM + m] = m == 0 ? ly[0] : (m == 1 ? ly[1] : ly[2]);
+            lamXn[i * DIM + m] = m == 0 ? tx[0] : (m == 1 ? tx[1] : tx[2]);
+        }
+        // interpolation transpose onto the nodes: this corner
         if (interp && chem != 0.f) {
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                int nd[3];
-                float wm, dwm[3];
-                corner_of<DIM>(kp, x0, m, nd, wm, dwm);
-                for (int a = 0; a < DIM; ++a) {
-                    const float coef = kp.dt * chem * wm * ly[a] * kp.inv_2h[a];
-                    if (coef == 0.f) continue;
-                    int kp1[3] = {nd[0], nd[1], nd[2]}, km1[3] = {nd[0], nd[1], nd[2]};
-                    kp1[a] = gnbr(kp, a, nd[a] + 1);
-                    km1[a] = gnbr(kp, a, nd[a] - 1);
-                    atomicAdd(&lamC[nidx(kp, kp1)], coef);
-                    atomicAdd(&lamC[nidx(kp, km1)], -coef);
-                }
+            for (int a = 0; a < DIM; ++a) {
+                const float coef = kp.dt * chem * w0 * ly[a] * kp.inv_2h[a];
+                if (coef == 0.f) continue;
+                int kp1[3] = {nd0[0], nd0[1], nd0[2]}, km1[3] = {nd0[0], nd0[1], nd0[2]};
+                kp1[a] = gnbr(kp, a, nd0[a] + 1);
+                km1[a] = gnbr(kp, a, nd0[a] - 1);
+                atomicAdd(&lamC[nidx(kp, kp1)], coef);
+                atomicAdd(&lamC[nidx(kp, km1)], -coef);
             }
         }
-        // 5. parameters
-        double gl = 0.0, fl = 0.0, xl = 0.0;
-        for (int a = 0; a < DIM; ++a) {
-            gl += (double)G[a] * ly[a];
-            fl += (double)Fb[i * DIM + a] * (double)f_unit * ly[a];
-            xl += (double)xi[a] * ly[a];
+        // 5. parameters (the group's first thread)
+        if (m == 0) {
+            float gl = 0.f, fl = 0.f, xl = 0.f;
+            for (int a = 0; a < DIM; ++a) {
+                gl = fmaf(G[a], ly[a], gl);
+                fl = fmaf(Fb[i * DIM + a] * f_unit, ly[a], fl);
+                xl = fmaf(xi[a], ly[a], xl);
+            }
+            p_chi = kp.dt * kp.chemotactic_f[sp] * gl;
+            p_int = kp.dt * fl;
+            if (amp > 0.f) p_Ds = kp.dt / amp * xl;  // d sqrt(2 D dt)/dD = dt / sqrt(2 D dt)
         }
-        d_chi = (double)kp.dt * (double)kp.chemotactic_f[sp] * gl;
-        d_int = (double)kp.dt * fl;
-        if (amp > 0.f) d_Ds = (double)kp.dt / (double)amp * xl;  // d sqrt(2 D dt)/dD = dt / sqrt(2 D dt)
     }
-    // parameter partials: slot blockIdx.x of each parameter's row of dpar
-    block_add_double(d_chi, dpar, red);
-    block_add_double(d_int, dpar + pstride, red);
-    for (int s = 0; s < kp.ns; ++s) block_add_double(s == sp ? d_Ds : 0.0, dpar + (2 + s) * pstride, red);
+    // parameter partials: each warp sums its cells' parts, the block adds the
+    // warps' sums in double into its slot blockIdx.x of each parameter's row
+    // (no two blocks share a slot and successive kernels run in order)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int np = 2 + kp.ns;
+    for (int v = 0; v < np; ++v) {
+        float x = v == 0 ? p_chi : (v == 1 ? p_int : (sp == v - 2 ? p_Ds : 0.f));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[wid][v] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < np) {
+        double sum = 0.0;
+        for (int w = 0; w < ATPB / 32; ++w) sum += (double)red[w][threadIdx.x];
+        dpar[(int64_t)threadIdx.x * pstride + blockIdx.x] += sum;
+    }
 }
 
 // Pair term of the adjoint over the cell list of X^n (sorted S):
@@ -696,7 +729,7 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
         t->lamY = (float *)p;
         if ((r = talloc(t, &p, gb))) return r;
         t->lamS = (float *)p;
-        t->pstride = (int64_t)blocks(std::max<int64_t>(n, 1));
+        t->pstride = (int64_t)blocks(std::max<int64_t>(n, 1) * 8);  // k_adj_cells: up to 8 threads per cell
         if ((r = talloc(t, &p, sizeof(double) * (2 + MAXS) * (size_t)t->pstride))) return r;
         t->dpar = (double *)p;
         if ((r = talloc(t, &p, sizeof(float) * (2 + MAXS)))) return r;
@@ -826,11 +859,11 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                     pairs_pending = false;
                 }
                 if (dim == 2)
-                    k_adj_cells<2><<<blocks(n), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
+                    k_adj_cells<2><<<blocks(n * 4), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
                                                              t->pstride, G ? 1 : 0, kp.pde_multi);
                 else
-                    k_adj_cells<3><<<blocks(n), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
+                    k_adj_cells<3><<<blocks(n * 8), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
                                                              t->pstride, G ? 1 : 0, kp.pde_multi);
                 ATRY(cudaGetLastError());
