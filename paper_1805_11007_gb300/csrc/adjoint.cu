@@ -381,12 +381,20 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
 // Pair term of the adjoint over the cell list of X^n (sorted S):
 // lambda_X^n_i += dt sum_j H_ij (lambda_Y_i - lambda_Y_j). APC threads share
 // a cell (each takes every APC-th candidate of each row range) and sum their
-// parts with shuffles.
+// parts with shuffles. H_ij = f/r (I - d d^T) + f' d d^T is even in the
+// difference d = X_i - X_j, so the term of j is the negation of the term of
+// i: with HALF (walls), each pair is found once, by the cell whose upper
+// half window holds the other (the rows at (dz, dy) > (0, 0) with all their
+// bins, in its own row the next bin and the cells of its own bin after it),
+// which adds the term to itself and its negation to the partner (float
+// atomics, so the order of the additions is open); else every cell searches
+// its whole window and adds its own term.
 constexpr int APC = 8;
 
-template <int DIM, bool PERIODIC>
+template <int DIM, bool PERIODIC, bool HALF>
 __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restrict__ lamY, float *__restrict__ lamXn)
 {
+    static_assert(!(HALF && PERIODIC), "the half window is taken with walls only");
     const int64_t t = (int64_t)blockIdx.x * ATPB + threadIdx.x;
     const int64_t j = t / APC;
     const int sub = (int)(t % APC);
@@ -421,53 +429,77 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
             }
         }
         const uint32_t n = (uint32_t)kp.n;
-        for (int z = lo[2]; z <= hi[2]; ++z) {
-            int zz = z;
-            if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
-            for (int y = lo[1]; y <= hi[1]; ++y) {
-                int yy = y;
-                if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
-                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
-                // the row's bins as contiguous ranges of the sorted array (a
-                // periodic row that wraps is two ranges)
-                int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
-                if (PERIODIC && lo[0] < 0) {
-                    xa[0] = 0;
-                    xa[1] = xb[1] = kp.nb[0] + lo[0];
-                } else if (PERIODIC && hi[0] >= kp.nb[0]) {
-                    xb[0] = kp.nb[0] - 1;
-                    xa[1] = 0;
-                    xb[1] = hi[0] - kp.nb[0];
+        // one candidate: the pair term, added to this cell (and, with the
+        // half window, its negation to the partner)
+        auto term = [&](uint32_t q) {
+            const float4 o = __ldg(&kp.S[q]);
+            float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
+            if (PERIODIC)
+                for (int a = 0; a < DIM; ++a) {
+                    if (d[a] > kp.halfL[a]) d[a] -= kp.L[a];
+                    else if (d[a] < -kp.halfL[a]) d[a] += kp.L[a];
                 }
-                for (int piece = 0; piece < 2; ++piece) {
-                    if (xa[piece] > xb[piece]) continue;
-                    const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
-                    const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
-                    for (uint32_t q = q0 + (uint32_t)sub; q < q1; q += APC) {
-                        if (q == (uint32_t)j) continue;
-                        const float4 o = __ldg(&kp.S[q]);
-                        float d[3] = {me.x - o.x, me.y - o.y, DIM == 3 ? me.z - o.z : 0.f};
-                        if (PERIODIC)
-                            for (int a = 0; a < DIM; ++a) {
-                                if (d[a] > kp.halfL[a]) d[a] -= kp.L[a];
-                                else if (d[a] < -kp.halfL[a]) d[a] += kp.L[a];
-                            }
-                        const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-                        const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
-                        if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) continue;
-                        const int64_t jd = __float_as_uint(o.w) & ID_MASK;
-                        if (jd >= kp.n) continue;
-                        const float r = sqrtf(r2), rinv = 1.f / r;
-                        const float e = __expf(-r * kp.inv_eps[st]);
-                        const float f = kp.amp_f[st] * (e - kp.shift[st]);
-                        const float fp = -kp.amp_f[st] * kp.inv_eps[st] * e;
-                        float dl[3], dot = 0.f;
-                        for (int a = 0; a < DIM; ++a) {
-                            dl[a] = li[a] - lamY[jd * DIM + a];
-                            dot = fmaf(d[a] * rinv, dl[a], dot);
-                        }
-                        const float s1 = f * rinv, s2 = (fp - f * rinv) * dot;
-                        for (int a = 0; a < DIM; ++a) acc[a] += s1 * dl[a] + s2 * d[a] * rinv;
+            const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+            const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
+            if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) return;
+            const int64_t jd = __float_as_uint(o.w) & ID_MASK;
+            if (jd >= kp.n) return;
+            const float r = sqrtf(r2), rinv = 1.f / r;
+            const float e = __expf(-r * kp.inv_eps[st]);
+            const float f = kp.amp_f[st] * (e - kp.shift[st]);
+            const float fp = -kp.amp_f[st] * kp.inv_eps[st] * e;
+            float dl[3], dot = 0.f;
+            for (int a = 0; a < DIM; ++a) {
+                dl[a] = li[a] - lamY[jd * DIM + a];
+                dot = fmaf(d[a] * rinv, dl[a], dot);
+            }
+            const float s1 = f * rinv, s2 = (fp - f * rinv) * dot;
+            for (int a = 0; a < DIM; ++a) {
+                const float v = s1 * dl[a] + s2 * d[a] * rinv;
+                acc[a] += v;
+                if (HALF) atomicAdd(&lamXn[jd * DIM + a], -kp.dt * v);
+            }
+        };
+        if (HALF) {
+            // rows (oy, oz) of the upper half: the own row (0, 0), then (1, 0),
+            // then (-1..1, 1) in 3D
+            constexpr int NROWS = DIM == 3 ? 5 : 2;
+            for (int k = 0; k < NROWS; ++k) {
+                const int oy = k == 0 ? 0 : (k == 1 ? 1 : k - 3);
+                const int oz = k < 2 ? 0 : 1;
+                const int y = c[1] + oy, z = c[2] + oz;
+                if (y < 0 || y >= kp.nb[1] || (DIM == 3 && z >= kp.nb[2])) continue;
+                const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)y + (uint32_t)kp.nb[1] * (uint32_t)z);
+                const int x0 = max(k == 0 ? c[0] : c[0] - 1, 0), x1 = min(c[0] + 1, kp.nb[0] - 1);
+                const uint32_t q0 = k == 0 ? (uint32_t)j + 1u : min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)x0), n);
+                const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)x1 + 1u), n);
+                for (uint32_t q = q0 + (uint32_t)sub; q < q1; q += APC) term(q);
+            }
+        } else {
+            for (int z = lo[2]; z <= hi[2]; ++z) {
+                int zz = z;
+                if (PERIODIC && DIM == 3) zz = z < 0 ? z + kp.nb[2] : (z >= kp.nb[2] ? z - kp.nb[2] : z);
+                for (int y = lo[1]; y <= hi[1]; ++y) {
+                    int yy = y;
+                    if (PERIODIC) yy = y < 0 ? y + kp.nb[1] : (y >= kp.nb[1] ? y - kp.nb[1] : y);
+                    const uint32_t rowk = (uint32_t)kp.px * ((uint32_t)yy + (uint32_t)kp.nb[1] * (uint32_t)zz);
+                    // the row's bins as contiguous ranges of the sorted array (a
+                    // periodic row that wraps is two ranges)
+                    int xa[2] = {lo[0], 0}, xb[2] = {hi[0], -1};
+                    if (PERIODIC && lo[0] < 0) {
+                        xa[0] = 0;
+                        xa[1] = xb[1] = kp.nb[0] + lo[0];
+                    } else if (PERIODIC && hi[0] >= kp.nb[0]) {
+                        xb[0] = kp.nb[0] - 1;
+                        xa[1] = 0;
+                        xb[1] = hi[0] - kp.nb[0];
+                    }
+                    for (int piece = 0; piece < 2; ++piece) {
+                        if (xa[piece] > xb[piece]) continue;
+                        const uint32_t q0 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xa[piece]), n);
+                        const uint32_t q1 = min(bin_start(kp.cnt_cur, kp.gstart, rowk + (uint32_t)xb[piece] + 1u), n);
+                        for (uint32_t q = q0 + (uint32_t)sub; q < q1; q += APC)
+                            if (q != (uint32_t)j) term(q);
                     }
                 }
             }
@@ -477,7 +509,10 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
     for (int o = APC / 2; o > 0; o >>= 1)
         for (int a = 0; a < DIM; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
     if (id >= 0 && sub == 0)
-        for (int a = 0; a < DIM; ++a) lamXn[id * DIM + a] += kp.dt * acc[a];
+        for (int a = 0; a < DIM; ++a) {
+            if (HALF) atomicAdd(&lamXn[id * DIM + a], kp.dt * acc[a]);  // partners add here too
+            else lamXn[id * DIM + a] += kp.dt * acc[a];
+        }
 }
 
 // Sums each parameter's row of per-block partials (one warp per parameter).
@@ -871,12 +906,18 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                     cudaStream_t sp2 = t->s_pair;
                     ATRY(cudaEventRecord(t->ev_cells, sr));
                     ATRY(cudaStreamWaitEvent(sp2, t->ev_cells, 0));
+                    // walls: the half window (each pair once; the 3^d bins of
+                    // a search mode other than 2 are needed for it)
+                    const bool half = !kp.periodic && kp.search != 2;
+                    const unsigned nbk = blocks(n * APC);
                     if (dim == 2) {
-                        if (kp.periodic) k_adj_pairs<2, true><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<2, false><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<2, true, false><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else if (half) k_adj_pairs<2, false, true><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<2, false, false><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     } else {
-                        if (kp.periodic) k_adj_pairs<3, true><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
-                        else k_adj_pairs<3, false><<<blocks(n * APC), ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        if (kp.periodic) k_adj_pairs<3, true, false><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else if (half) k_adj_pairs<3, false, true><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
+                        else k_adj_pairs<3, false, false><<<nbk, ATPB, 0, sp2>>>(kp, t->lamY, t->lamX[lx ^ 1]);
                     }
                     ATRY(cudaGetLastError());
                     ATRY(cudaEventRecord(t->ev_pairs, sp2));
