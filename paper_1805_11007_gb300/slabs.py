@@ -427,23 +427,34 @@ class DistExchange:
     def mine(self):
         return [self.rank]
 
+    def _on_stream(self):
+        """Context running device work on this rank's sub-domain stream (NCCL
+        orders its transfers against the current stream, and the staged
+        copies must precede the sub-domain's own kernels)."""
+        st = self.subs[self.rank].stream
+        if st is None:
+            import contextlib
+            return contextlib.nullcontext()
+        return self.torch.cuda.stream(st)
+
     def _sendrecv(self, sends, recvs):
         """sends {peer: tensor}, recvs {peer: tensor to fill} in one batch."""
         torch, dist = self.torch, self.dist
-        ops, land = [], []
-        for peer, t in sorted(sends.items()):
-            src = t.cpu() if (self.stage and t.is_cuda) else t
-            ops.append(dist.P2POp(dist.isend, src.contiguous(), peer, self.group))
-        for peer, t in sorted(recvs.items()):
-            dst = torch.empty(t.shape, dtype=t.dtype) if (self.stage and t.is_cuda) else t
-            land.append((t, dst))
-            ops.append(dist.P2POp(dist.irecv, dst, peer, self.group))
-        if ops:
-            for req in dist.batch_isend_irecv(ops):
-                req.wait()
-        for t, dst in land:
-            if dst is not t:
-                t.copy_(dst)
+        with self._on_stream():
+            ops, land = [], []
+            for peer, t in sorted(sends.items()):
+                src = t.cpu() if (self.stage and t.is_cuda) else t
+                ops.append(dist.P2POp(dist.isend, src.contiguous(), peer, self.group))
+            for peer, t in sorted(recvs.items()):
+                dst = torch.empty(t.shape, dtype=t.dtype) if (self.stage and t.is_cuda) else t
+                land.append((t, dst))
+                ops.append(dist.P2POp(dist.irecv, dst, peer, self.group))
+            if ops:
+                for req in dist.batch_isend_irecv(ops):
+                    req.wait()
+            for t, dst in land:
+                if dst is not t:
+                    t.copy_(dst)
 
     @staticmethod
     def _recv_buffer(sub, peer, sent):
@@ -482,7 +493,8 @@ class DistExchange:
         if sub.stream is not None:
             sub.stream.synchronize()
         if recv_into[(me, me)].shape[0]:
-            recv_into[(me, me)].copy_(sends[(me, me)])
+            with self._on_stream():
+                recv_into[(me, me)].copy_(sends[(me, me)])
         s = {dst: t for (src, dst), t in sends.items() if src == me and dst != me and t.shape[0]}
         r = {src: t for (src, dst), t in recv_into.items() if dst == me and src != me and t.shape[0]}
         self._sendrecv(s, r)
