@@ -265,8 +265,10 @@ int chemo_record_stored(chemo_sim *sim, int64_t nsteps, int32_t every, int64_t s
  * lists and pair forces of `every` steps each (segments kept by
  * chemo_record_stored are not re-run). The simulation is left at the final
  * state and step index of the recorded run, whatever was stepped after the
- * record. Synchronises `stream` when mem_kind is HOST. EINVAL if no run is
- * recorded. */
+ * record. An ensemble (chemo_create_batch) is differentiated as a whole: its
+ * replicates share the parameters, so dL_dparams is the sum of every
+ * replicate's part, and positions are by the ids of the batch. Synchronises
+ * `stream` when mem_kind is HOST. EINVAL if no run is recorded. */
 int chemo_gradient(chemo_sim *sim, const float *dL_dpos_final, const float *dL_dc_final, float *dL_dparams,
                    float *dL_dpos0, int mem_kind, void *stream);
 

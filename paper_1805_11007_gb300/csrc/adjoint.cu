@@ -59,6 +59,7 @@ struct Tape {
     std::vector<DevBuf> allocs;
     std::vector<float *> ck_pos, ck_c;  // checkpoints: positions by id (n x dim), field
     uint8_t *species = nullptr;         // species by id
+    uint16_t *layer_id = nullptr;       // replicate of each id (NULL for a single simulation)
     // two segment buffers: segment s - 1 is re-run into one while the
     // reverse sweep of segment s reads the other (two streams)
     SegBuf sb[2];
@@ -124,7 +125,7 @@ __global__ void k_gather_state(KP kp, float *__restrict__ pos, uint8_t *__restri
     if (j >= kp.n) return;
     const float4 u = kp.S[j];
     const uint32_t w = __float_as_uint(u.w);
-    const int64_t id = w & ID_MASK;
+    const int64_t id = gid_of(kp, u);  // replicates: the layer's offset plus the id within it
     if (id >= kp.n) return;
     pos[id * kp.dim + 0] = u.x;
     pos[id * kp.dim + 1] = u.y;
@@ -192,7 +193,7 @@ __device__ __forceinline__ void corner_w(const KP &kp, const int k0[3], const in
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const int bit = (m >> a) & 1;
-        node[a] = a < DIM ? (bit ? k1[a] : k0[a]) : 0;
+        node[a] = a < DIM ? (bit ? k1[a] : k0[a]) : k0[a];  // beyond DIM: the replicate's layer
         if (a < DIM) w *= bit ? f[a] : 1.f - f[a];
     }
 #pragma unroll
@@ -234,7 +235,8 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
                                                     const float *__restrict__ Fb, float f_unit, float *__restrict__ lamY,
                                                     float *__restrict__ lamXn, float *__restrict__ lamC,
                                                     unsigned long long step, double *dpar, int64_t pstride,
-                                                    int has_grid, int lams_over_tau)
+                                                    int has_grid, int lams_over_tau,
+                                                    const uint16_t *__restrict__ layer_id)
 {
     constexpr int NC = 1 << DIM;
     static_assert(32 % NC == 0 && ATPB % 32 == 0, "a cell's threads lie in one warp");
@@ -244,6 +246,10 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
     const int m = (int)(t % NC);
     const bool valid = i < kp.n;
     const int sp = valid ? (int)spec[i] : 0;
+    // replicates (2D layers): the cell's layer is the third grid index and
+    // keys its noise with its id within the layer
+    const int layer = (valid && layer_id) ? (int)layer_id[i] : 0;
+    const uint32_t lid = (uint32_t)(layer_id && valid ? i - kp.layer_off[layer] : i);
     float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f}, lx[3] = {0.f, 0.f, 0.f};
     if (valid)
         for (int a = 0; a < DIM; ++a) {
@@ -257,6 +263,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
         int k0[3], k1[3], nd[3];
         float f[3], wm, dwm[3];
         cell_frac<DIM>(kp, x1, k0, k1, f);
+        if (DIM == 2) k0[2] = k1[2] = layer;
         corner_w<DIM>(kp, k0, k1, f, m, nd, wm, dwm);
         float inv_tau = 1.f;
         if (kp.pde_bc != 2 && !lams_over_tau)  // (already divided by tau when lams_over_tau)
@@ -280,6 +287,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
             int k0[3], k1[3];
             float f[3], dw0[3];
             cell_frac<DIM>(kp, x0, k0, k1, f);
+            if (DIM == 2) k0[2] = k1[2] = layer;
             corner_w<DIM>(kp, k0, k1, f, m, nd0, w0, dw0);
 #pragma unroll
             for (int a = 0; a < DIM; ++a) {
@@ -303,7 +311,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_cells(KP kp, const float *__restri
     if (valid) {
         // noise and the pre-boundary position Y (reflection signs), in every
         // thread of the group
-        const uint4 rw = cell_words(kp, (uint32_t)i, step, TAG_MOVE);
+        const uint4 rw = cell_words(kp, lid, step, TAG_MOVE, (uint32_t)layer);
         const float2 n01 = box_muller(rw.x, rw.y);
         const float xi[3] = {n01.x, n01.y, DIM == 3 ? box_muller(rw.z, rw.w).x : 0.f};
         const float amp = kp.noise[sp];
@@ -401,9 +409,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
     float acc[3] = {0.f, 0.f, 0.f};
     int64_t id = -1;
     if (j < kp.n) {
-        const float4 me = kp.S[j];
-        const uint32_t w = __float_as_uint(me.w);
-        id = w & ID_MASK;
+        id = gid_of(kp, kp.S[j]);  // replicates: the layer's offset plus the id within it
         if (id >= kp.n) id = -1;
     }
     if (id >= 0) {
@@ -428,6 +434,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
                 hi[a] = min(hi[a], kp.nb[a] - 1);
             }
         }
+        if (DIM == 2) c[2] = lo[2] = hi[2] = layer_of(kp, me);  // the rows of the cell's own layer
         const uint32_t n = (uint32_t)kp.n;
         // one candidate: the pair term, added to this cell (and, with the
         // half window, its negation to the partner)
@@ -442,7 +449,7 @@ __global__ void __launch_bounds__(ATPB) k_adj_pairs(KP kp, const float *__restri
             const float r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
             const int st = sp * MAXS + (int)(__float_as_uint(o.w) >> SP_SHIFT);
             if (!(r2 < kp.rc2[st]) || !(r2 > 0.f)) return;
-            const int64_t jd = __float_as_uint(o.w) & ID_MASK;
+            const int64_t jd = gid_of(kp, o);
             if (jd >= kp.n) return;
             const float r = sqrtf(r2), rinv = 1.f / r;
             const float e = __expf(-r * kp.inv_eps[st]);
@@ -538,7 +545,6 @@ unsigned blocks(int64_t n) { return (unsigned)((n + ATPB - 1) / ATPB); }
 int check_adjoint_model(const chemo_sim *s)
 {
     const chemo_params &p = s->prm;
-    if (s->kp.layers > 1) return eng_fail(CHEMO_ENOTSUP, "the adjoint covers single simulations (replicates = 1)");
     if (p.reactions) return eng_fail(CHEMO_ENOTSUP, "the adjoint does not cover type switching (reactions = 1)");
     if (p.move_scheme || p.hard_sphere || p.deposit_kernel)
         return eng_fail(CHEMO_ENOTSUP, "the adjoint covers the Euler-Maruyama move with the CIC deposit only");
@@ -661,6 +667,16 @@ extern "C" int chemo_record_stored(chemo_sim *s, int64_t nsteps, int32_t every, 
     }
     if ((r = talloc(t, &p, (size_t)std::max<int64_t>(t->n, 1)))) return r;
     t->species = (uint8_t *)p;
+    if (kp.layers > 1 && t->n > 0) {  // replicates: the layer of every id, for the reverse sweep
+        std::vector<uint16_t> lid((size_t)t->n);
+        for (int l = 0; l < kp.layers; ++l)
+            for (int64_t i = s->layer_off_host[(size_t)l]; i < s->layer_off_host[(size_t)l + 1]; ++i)
+                lid[(size_t)i] = (uint16_t)l;
+        if ((r = talloc(t, &p, (size_t)t->n * sizeof(uint16_t)))) return r;
+        t->layer_id = (uint16_t *)p;
+        if (cudaMemcpy(t->layer_id, lid.data(), lid.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess)
+            return eng_fail(CHEMO_ECUDA, "chemo_record: layer table copy failed");
+    }
     // the stored segments are the last nstore: steps k0 .. nsteps - 1 of the
     // run, kept in one block; each stored segment is a view into it
     const int fs = t->nseg - (int)nstore;
@@ -896,11 +912,11 @@ extern "C" int chemo_gradient(chemo_sim *s, const float *dL_dpos_final, const fl
                 if (dim == 2)
                     k_adj_cells<2><<<blocks(n * 4), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             t->pstride, G ? 1 : 0, kp.pde_multi);
+                                                             t->pstride, G ? 1 : 0, kp.pde_multi, t->layer_id);
                 else
                     k_adj_cells<3><<<blocks(n * 8), ATPB, 0, sr>>>(kp, Xn, Xn1, t->species, cn, t->lamX[lx], t->lamS, Fk, f_unit,
                                                              t->lamY, t->lamX[lx ^ 1], t->lamC[lc], step, t->dpar,
-                                                             t->pstride, G ? 1 : 0, kp.pde_multi);
+                                                             t->pstride, G ? 1 : 0, kp.pde_multi, t->layer_id);
                 ATRY(cudaGetLastError());
                 if (kp.pairs) {
                     cudaStream_t sp2 = t->s_pair;
