@@ -1137,7 +1137,7 @@ __global__ void k_pack(KP kp, const float *__restrict__ pos, const uint8_t *__re
 // particle kernel has finished reading), which the next step counts into.
 // ---------------------------------------------------------------------------
 #ifndef CHEMO_SCAN_ITEMS
-#define CHEMO_SCAN_ITEMS 16
+#define CHEMO_SCAN_ITEMS 8
 #endif
 constexpr int SCAN_ITEMS = CHEMO_SCAN_ITEMS;        // consecutive groups per thread
 constexpr int SCAN_TILE = TPB * SCAN_ITEMS;         // groups per tile
