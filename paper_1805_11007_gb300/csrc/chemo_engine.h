@@ -46,7 +46,9 @@ struct chemo_sim {
     int cur = 0;                 // c[cur] holds c^n
     int64_t step = 0;            // host mirror of the next step index
     int launches_per_step = 0;
-    cudaStream_t aux = nullptr;  // second stream for the PDE
+    cudaStream_t aux = nullptr;  // second stream for the PDE (lowest priority)
+    cudaStream_t hp = nullptr;   // the particle kernels beside it (highest priority)
+    cudaEvent_t ev_hp = nullptr;
     cudaStream_t cap = nullptr;  // capture stream for graphs
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t graph[2][2][2] = {};  // [2-step, 16-step][grid parity][count parity]
