@@ -133,7 +133,22 @@ class ClockSampler:
         except Exception:
             self.proc = None
 
-    def stop(self):
+    @staticmethod
+    def _when(r):
+        """Host time (seconds since the epoch) of a sample, or None."""
+        try:
+            import datetime
+            return datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except (ValueError, IndexError):
+            return None
+
+    def stop(self, windows=()):
+        """The record of the samples. A sample is under load when it was
+        taken inside one of `windows` ((start, end) host times between which
+        the benchmark's kernels ran, by the same clock as nvidia-smi's
+        timestamps) or when it reports a utilisation of 50 % or more (a
+        utilisation that nvidia-smi averages over a longer time than a short
+        run lasts)."""
         if self.proc is None:
             return None
         time.sleep(0.05)
@@ -144,7 +159,13 @@ class ClockSampler:
             self.proc.kill()
         self.fh.seek(0)
         rows = [r.split(", ") for r in self.fh.read().strip().splitlines() if r.strip()]
-        load = [r for r in rows if len(r) >= 11 and r[2].strip().isdigit() and int(r[2]) >= 50]
+
+        def busy(r):
+            t = self._when(r)
+            in_window = t is not None and any(a <= t <= b for a, b in windows)
+            return in_window or (r[2].strip().isdigit() and int(r[2]) >= 50)
+
+        load = [r for r in rows if len(r) >= 11 and busy(r)]
         use = load if load else rows
         mhz = [float(r[3]) for r in use if r[3].replace(".", "").isdigit()]
         mx = [float(r[4]) for r in use if r[4].replace(".", "").isdigit()]
@@ -584,6 +605,7 @@ def main():
     resets0 = state["resets"]
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    busy = [time.time()]  # host times around the GPU work, for the clock record
     ev0.record(stream)
     advance(args.steps)
     ev1.record(stream)
@@ -591,6 +613,7 @@ def main():
     ms = ev0.elapsed_time(ev1)
     resets_in = state["resets"] - resets0
     chemo.chemo_check(sim, stream=stream)
+    busy.append(time.time())
     t_local = torch.tensor([ms], dtype=torch.float64, device=devc)
     if dist is not None:
         dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
@@ -602,11 +625,13 @@ def main():
     # overlap as a step), and the in-cutoff pair interactions per step
     reset()
     nprof = min(args.profile_steps, RUN_STEPS)
+    busy.append(time.time())
     prof = chemo.chemo_profile_steps(sim, nprof, stream=stream)
+    busy.append(time.time())
     state["in_run"] = nprof
     # the clock record covers the timed region and the profiled run after it
     # (a short timed region can end between two samples)
-    clock_rec = clocks.stop()
+    clock_rec = clocks.stop(windows=[(busy[0], busy[1]), (busy[2], busy[3])])
     clock_rec["covers"] = "timed region + %d profiled steps" % nprof
     G = int(np.prod(p["grid"]))
     s = info["pde_substeps"]

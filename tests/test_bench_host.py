@@ -44,6 +44,23 @@ def test_clock_record_under_load():
     assert rec["reasons"] == [] and rec["samples"] == 7 and rec["samples_under_load"] == 5
 
 
+def test_clock_record_counts_samples_inside_the_busy_windows():
+    """A short run: nvidia-smi's utilisation (averaged over a longer time)
+    stays low, but the samples taken while the kernels ran count."""
+    import datetime
+
+    def at(t, util, mhz):
+        stamp = datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+        return ", ".join([stamp, "0", str(util), str(mhz), "2070", "900.00", "0x0"] + ["Not Active"] * 4)
+
+    t0 = 1.8e9
+    lines = [at(t0 - 1.0, 0, 990), at(t0 + 0.02, 4, 2070), at(t0 + 0.04, 9, 2055), at(t0 + 0.5, 0, 1200),
+             at(t0 + 0.62, 12, 2070)]
+    rec = _sampler(lines).stop(windows=[(t0, t0 + 0.05), (t0 + 0.6, t0 + 0.7)])
+    assert rec["samples"] == 5 and rec["samples_under_load"] == 3
+    assert rec["sm_mhz"] == 2070
+
+
 def test_clock_record_keeps_every_active_reason():
     act = "Active"
     lines = [_row(100, 2070), _row(100, 1800, ("Not Active", "Not Active", "Not Active", act)),
