@@ -817,8 +817,8 @@ int create_sim(const chemo_params *params, int32_t replicates, const std::vector
     kp.scan_seq = ctl + 1;
     kp.err = ctl + 2;
     kp.step = reinterpret_cast<unsigned long long *>(ctl + 4);
-    kp.pair_count = nullptr;  // set only while profiling (ctl + 8)
-    kp.test_count = nullptr;  // set only while profiling (ctl + 10)
+    kp.pair_count = nullptr;  // set only while profiling
+    kp.test_count = nullptr;
     if (replicates > 1) {
         int64_t *lo;
         ALLOC(lo, off.size() * sizeof(int64_t));
@@ -1371,9 +1371,12 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     const bool overlap = grid && s->kp.overlap;
     const bool fused = grid && s->kp.fused_deposit;
     const bool variants = s->kp.hard_sphere || s->kp.kde;
-    // in-cutoff pairs are counted into ctl + 8 while profiling
-    unsigned long long *pc = reinterpret_cast<unsigned long long *>(s->kp.tile_ctr + 8);
-    CUDA_TRY(cudaMemsetAsync(pc, 0, 2 * sizeof(unsigned long long), st));  // pairs, candidate tests
+    // in-cutoff pairs and candidate tests are counted into PROF_SLOTS
+    // counters each (in the simulation's scratch) while profiling
+    void *pcv = nullptr;
+    if (int r = scratch(s, 2 * PROF_SLOTS * sizeof(unsigned long long), &pcv)) return r;
+    unsigned long long *pc = static_cast<unsigned long long *>(pcv);
+    CUDA_TRY(cudaMemsetAsync(pc, 0, 2 * PROF_SLOTS * sizeof(unsigned long long), st));
     // event pairs per step: particle, pde, scan, scatter, whole step
     std::vector<cudaEvent_t> ev((size_t)nsteps * 10, nullptr);
     for (auto &e : ev)
@@ -1386,7 +1389,7 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
     for (int64_t k = 0; k < nsteps && r == CHEMO_OK; ++k) {
         KP kp = view(s);
         kp.pair_count = pc;
-        kp.test_count = pc + 1;
+        kp.test_count = pc + PROF_SLOTS;
         cudaEvent_t *e = &ev[(size_t)k * 10];
         cudaError_t err = cudaEventRecord(e[8], st);
         if (fused && !overlap) {
@@ -1448,9 +1451,15 @@ int chemo_profile_steps(chemo_sim *s, int64_t nsteps, float *kernel_ms, void *st
             }
         }
         for (int q = 0; q < 5; ++q) kernel_ms[q] = (float)(acc[q] / (double)nsteps);
-        unsigned long long cnt[2] = {0ull, 0ull};
+        std::vector<unsigned long long> slots(2 * (size_t)PROF_SLOTS, 0ull);
         kernel_ms[5] = kernel_ms[6] = 0.f;
-        if (cudaMemcpy(cnt, pc, sizeof(cnt), cudaMemcpyDeviceToHost) == cudaSuccess) {
+        if (cudaMemcpy(slots.data(), pc, slots.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost) ==
+            cudaSuccess) {
+            unsigned long long cnt[2] = {0ull, 0ull};
+            for (int k = 0; k < PROF_SLOTS; ++k) {
+                cnt[0] += slots[(size_t)k];
+                cnt[1] += slots[(size_t)PROF_SLOTS + k];
+            }
             kernel_ms[5] = (float)((double)cnt[0] / (double)nsteps);
             kernel_ms[6] = (float)((double)cnt[1] / (double)nsteps);
         }

@@ -125,8 +125,12 @@ struct KP {
     float *srcg, *Rg;            // source and consumption grids (substeps > 1)
     uint32_t *err;               // latched error bits
     unsigned long long *step;    // absolute index of the step being computed
-    unsigned long long *pair_count;  // non-NULL while profiling: in-cutoff pairs are counted here
-    unsigned long long *test_count;  // non-NULL while profiling: candidate tests of the half window
+    // non-NULL while profiling: in-cutoff pairs and candidate tests of the
+    // half window, each counted into PROF_SLOTS counters (a block adds to
+    // slot blockIdx.x mod PROF_SLOTS: one counter for every warp of a launch
+    // serialised its atomics and slowed the profiled kernels)
+    unsigned long long *pair_count;
+    unsigned long long *test_count;
     // adjoint recording (pos == NULL: off): the particle kernel stores, for
     // steps s0 .. s0 + nk - 1 (absolute indices; with period > 0 step s goes
     // to slot (s - s0) mod period, nk = period), the positions before the
@@ -256,6 +260,9 @@ __device__ __forceinline__ uint32_t bin_start(const uint32_t *__restrict__ cnt, 
 // Largest count of one bin: counts are 16-bit halves of a 32-bit word, so a
 // 65536th particle in one bin would carry into the neighbouring bin's count.
 constexpr uint32_t BIN_COUNT_MAX = 0xFFFFu;
+
+// Counters per profiling count (KP::pair_count, KP::test_count); a power of two.
+constexpr int PROF_SLOTS = 512;
 
 // Counts particle key k into the packed counts (zero before the count; the
 // scan turns them into offsets within the group afterwards); returns its

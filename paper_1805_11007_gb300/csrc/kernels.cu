@@ -784,11 +784,11 @@ __global__ void __launch_bounds__(BT, CHEMO_PAIR_BLOCKS *TPB / BT) k_pairs_half(
     count += nl;
     if (kp.pair_count) {  // profiling only: each pair found here is an in-cutoff pair of both cells
         const int wsum = __reduce_add_sync(0xffffffffu, count);
-        if (lane == 0 && wsum) atomicAdd(kp.pair_count, 2ull * (unsigned long long)wsum);
+        if (lane == 0 && wsum) atomicAdd(kp.pair_count + (blockIdx.x & (PROF_SLOTS - 1)), 2ull * (unsigned long long)wsum);
     }
     if (kp.test_count) {  // profiling only: candidates tested
         const uint32_t tsum = __reduce_add_sync(0xffffffffu, tests);
-        if (lane == 0 && tsum) atomicAdd(kp.test_count, (unsigned long long)tsum);
+        if (lane == 0 && tsum) atomicAdd(kp.test_count + (blockIdx.x & (PROF_SLOTS - 1)), (unsigned long long)tsum);
     }
     if (valid && (F.x | F.y | F.z)) {
         unsigned long long *pf = reinterpret_cast<unsigned long long *>(kp.Fh) + (size_t)j * FS;
@@ -964,7 +964,8 @@ __global__ void __launch_bounds__(BT, (HALF ? CHEMO_MOVE_BLOCKS : CHEMO_PAIR_BLO
         }
         if (kp.pair_count) {  // profiling only: in-cutoff pairs of this step
             const int wsum = __reduce_add_sync(0xffffffffu, npairs);
-            if ((threadIdx.x & 31) == 0 && wsum) atomicAdd(kp.pair_count, (unsigned long long)wsum);
+            if ((threadIdx.x & 31) == 0 && wsum)
+                atomicAdd(kp.pair_count + (blockIdx.x & (PROF_SLOTS - 1)), (unsigned long long)wsum);
         }
     }
     if (!valid) return;
