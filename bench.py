@@ -107,7 +107,7 @@ PARTICLE_BYTES = 42.0
 # DRAM bytes (read + write) per launch from one ncu capture, for the roofline's
 # traffic field ("k_step": the particle kernels of one step together, at
 # step 10 of the 3D workload); None where a kernel changed after the capture.
-NCU_TRAFFIC_BYTES = {"k_step": 138.28e6, "k_pde": 93.31e6, "k_scan": None, "k_scatter": None}
+NCU_TRAFFIC_BYTES = {"k_step": 138.16e6, "k_pde": 93.31e6, "k_scan": None, "k_scatter": None}
 
 
 # ---------------------------------------------------------------------------
