@@ -1207,13 +1207,22 @@ __global__ void __launch_bounds__(TPB) k_scan(KP kp)
     uint4 *src = reinterpret_cast<uint4 *>(kp.cnt_nxt);  // one uint4 per group
     uint4 *clr = reinterpret_cast<uint4 *>(kp.cnt_cur);
     const int64_t tbase = (int64_t)tile * SCAN_TILE;
+    // all of a thread's loads first: the in-place offsets stored below go to
+    // the same array, so loads after them could not be issued before them
+    // (each thread would wait for one DRAM round trip per group)
+    uint4 qv[SCAN_ITEMS];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const int64_t g = tbase + i * TPB + (int)threadIdx.x;
+        qv[i] = g < NG ? __ldcs(src + g) : make_uint4(0u, 0u, 0u, 0u);
+    }
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
         const int k = i * TPB + (int)threadIdx.x;
         const int64_t g = tbase + k;
         uint32_t s = 0u;
         if (g < NG) {
-            const uint4 q = __ldcs(src + g);
+            const uint4 q = qv[i];
             s = halfsum(q.x) + halfsum(q.y) + halfsum(q.z) + halfsum(q.w);
             clr[g] = make_uint4(0u, 0u, 0u, 0u);
             if (s) {
