@@ -289,6 +289,30 @@ def test_full_size_clumps_3d_step():
     assert_step_matches(p, pos, sp, c0, pos_g, sp_g, c_g)
 
 
+def test_full_size_graph_steps_equal_direct_steps():
+    """The bench replays its steps as CUDA graphs (chemo_step_n: 2- and
+    16-step graphs of the overlapped step); at full size two graph-replayed
+    steps equal two directly enqueued steps, the path the oracle checks
+    above: species bit for bit, positions within 1e-6 of the unit box (the
+    second step's gradient reads a field whose deposit's float atomics
+    round in any order), the field within that rounding."""
+    p, pos, sp = wl.initial_state("clumps_grid_3d")
+    c0 = wl.random_field(p, seed=7, scale=0.05)
+    with make_sim(p, pos, sp, c0) as sim:
+        chemo.chemo_step_n(sim, 2)  # one 2-step graph
+        xa, sa, _ = chemo.read_state_host(sim)
+        ca = chemo.read_field_host(sim)
+    with make_sim(p, pos, sp, c0) as sim:
+        chemo.chemo_step(sim)
+        chemo.chemo_step(sim)
+        chemo.chemo_check(sim)
+        xb, sb, _ = chemo.read_state_host(sim)
+        cb = chemo.read_field_host(sim)
+    np.testing.assert_array_equal(sa, sb)
+    assert np.abs(xa - xb).max() <= 1e-6
+    assert np.abs(ca - cb).max() <= 1e-5 * np.abs(cb).max()
+
+
 def test_full_size_walls_2d_step():
     p, pos, sp = wl.initial_state("walls_grid_2d")
     c0 = wl.random_field(p, seed=8, scale=0.1)
