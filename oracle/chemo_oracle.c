@@ -882,3 +882,269 @@ void orc_run(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const uin
 {
     for (int64_t k = 0; k < nsteps; ++k) orc_step(p, n, pos, sp, ids, c, step0 + k, disp, NULL, NULL);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Tangent of a step (forward-mode derivative) with respect to              */
+/* theta = (chi, inter, D_0 .. D_{ns-1}), with the noise frozen: every       */
+/* operation of orc_step is differentiated where it acts. dpos[(i d + a) P   */
+/* + k] = dX_ia / dtheta_k and dc[g P + k] = dc_g / dtheta_k are carried     */
+/* from step to step (zero at the start for fixed initial data). The         */
+/* piecewise choices (which pairs are inside the cutoff, the grid cell of a */
+/* particle, the number of wall reflections) are held, so this is the       */
+/* derivative wherever the trajectory is differentiable. The primal state   */
+/* is advanced by the functions above, exactly as orc_step does.             */
+/* Pieces, in the order of orc_step:                                         */
+/*   pair term g(r) u, u = X_i - X_j, g = f(r)/r, f = (inter/eps)(e^{-r/eps} */
+/*   - shift): d(g u) = g du + g'(r) (u.du / r) u + (dg/dinter) u dinter;    */
+/*   drift chi kappa_s sum_m w_m(X) grad_h c(node_m): the product rule over  */
+/*   chi, the weights (dw_m/dx_a = +-1/h_a times the other axes' factors)    */
+/*   and c; noise sqrt(2 D_s dt) xi: d/dD_s = dt / sqrt(2 D_s dt) xi; a wall */
+/*   reflection negates the tangent, a periodic wrap keeps it; the deposit   */
+/*   differentiates the weights; the PDE substep is linear in (c, S) and    */
+/*   bilinear in (R, c).                                                     */
+/* Supported: Euler-Maruyama, cloud-in-cell deposit, no reactions and no    */
+/* hard-sphere correction (returns -1 otherwise; -2 for a wrong P).         */
+/* ------------------------------------------------------------------------ */
+#define ORC_MAX_THETA (2 + ORC_MAX_SPECIES)
+
+typedef struct orc_tan_ctx {
+    const orc_params *p;
+    const double *pos, *dpos;
+    const uint8_t *sp;
+    int64_t i;
+    int P;
+    double dF[3][ORC_MAX_THETA];
+} orc_tan_ctx;
+
+static void orc_tan_visit(void *vctx, int64_t j)
+{
+    orc_tan_ctx *c = (orc_tan_ctx *)vctx;
+    if (j == c->i) return;
+    const orc_params *p = c->p;
+    const int d = p->dim, P = c->P;
+    orc_pair_geom g;
+    orc_geom(p, c->pos + c->i * d, c->pos + j * d, c->sp[c->i], c->sp[j], &g);
+    if (!(g.r > 0.0) || !(g.r < g.rc)) return;
+    double e = exp(-g.r / g.eps);
+    double shift = p->cutoff_mode == 1 ? exp(-p->cutoff_factor) : 0.0;
+    double f = orc_force_mag(p, g.r, g.eps);
+    double gr = f / g.r;
+    double fp = -p->inter / (g.eps * g.eps) * e;  /* df/dr */
+    double gp = (fp * g.r - f) / g.r2;              /* d(f/r)/dr */
+    double gi = (e - shift) / (g.eps * g.r);        /* d(f/r)/dinter */
+    for (int k = 0; k < P; ++k) {
+        double du[3] = {0.0, 0.0, 0.0}, udu = 0.0;
+        for (int a = 0; a < d; ++a) {
+            du[a] = c->dpos[(c->i * d + a) * P + k] - c->dpos[(j * d + a) * P + k];
+            udu += g.d[a] * du[a];
+        }
+        for (int a = 0; a < d; ++a) {
+            double v = gr * du[a] + gp * (udu / g.r) * g.d[a];
+            if (k == 1) v += gi * g.d[a];
+            c->dF[a][k] += v;
+        }
+    }
+}
+
+/* Derivatives of the interpolation weights of orc_corners: dw[m][a]. */
+static void orc_corner_derivs(const orc_params *p, const double *x, double dw[8][3])
+{
+    int k0[3] = {0, 0, 0}, k1[3] = {0, 0, 0};
+    double f[3] = {0, 0, 0};
+    for (int a = 0; a < p->dim; ++a) orc_cell_frac(p, a, x[a], &k0[a], &k1[a], &f[a]);
+    int nc = 1 << p->dim;
+    for (int m = 0; m < nc; ++m)
+        for (int a = 0; a < 3; ++a) {
+            dw[m][a] = 0.0;
+            if (a >= p->dim) continue;
+            double v = (((m >> a) & 1) ? 1.0 : -1.0) / orc_grid_h(p, a);
+            for (int b = 0; b < p->dim; ++b)
+                if (b != a) v *= ((m >> b) & 1) ? f[b] : (1.0 - f[b]);
+            dw[m][a] = v;
+        }
+}
+
+/* Central difference of column k of a tangent grid (dc[g P + k]) at node k3. */
+static double orc_node_grad_col(const orc_params *p, const double *dc, int P, int col, const int k3[3], int a)
+{
+    int kp[3] = {k3[0], k3[1], k3[2]}, km[3] = {k3[0], k3[1], k3[2]};
+    kp[a] = orc_nbr(p, a, k3[a] + 1);
+    km[a] = orc_nbr(p, a, k3[a] - 1);
+    return (dc[orc_gidx(p, kp) * P + col] - dc[orc_gidx(p, km) * P + col]) / (2.0 * orc_grid_h(p, a));
+}
+
+/* Reflection sign of orc_boundary at x: +1 or -1 per the parity of the
+ * reflections, 1 when periodic, 0 when the position was clamped. */
+static double orc_boundary_sign(const orc_params *p, int a, double x)
+{
+    if (p->boundary == 1) return 1.0;
+    double lo = p->lo[a], hi = p->hi[a], sg = 1.0;
+    for (int it = 0; it < 64 && (x < lo || x > hi); ++it) {
+        if (x < lo) x = 2.0 * lo - x;
+        else if (x > hi) x = 2.0 * hi - x;
+        sg = -sg;
+    }
+    return (x < lo || x > hi) ? 0.0 : sg;
+}
+
+int orc_step_tangent(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const uint32_t *ids,
+                     double *c, int64_t step, int P, double *dpos, double *dc)
+{
+    if (p->move_scheme != 0 || p->hard_sphere || p->reactions || p->deposit_kernel != 0) return -1;
+    if (P != 2 + p->n_species || P > ORC_MAX_THETA) return -2;
+    const int d = p->dim;
+    double *F = (double *)malloc(sizeof(double) * (size_t)(n * d + 1));
+    double *drift = (double *)malloc(sizeof(double) * (size_t)(n * d + 1));
+    double *dstep = (double *)calloc((size_t)(n * d * P + 1), sizeof(double));  /* d(F + drift) */
+    orc_pair_forces(p, n, pos, sp, 1, F, NULL, NULL, NULL, NULL, NULL);
+    orc_drift(p, n, pos, sp, c, drift);
+    orc_cells cl;
+    memset(&cl, 0, sizeof(cl));
+    orc_cells_build(p, n, pos, &cl);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < n; ++i) {
+        orc_tan_ctx t;
+        memset(&t, 0, sizeof(t));
+        t.p = p;
+        t.pos = pos;
+        t.dpos = dpos;
+        t.sp = sp;
+        t.i = i;
+        t.P = P;
+        orc_candidates(p, &cl, n, pos, i, orc_tan_visit, &t);
+        /* drift tangent */
+        double kap = p->chemotactic[sp[i]];
+        double ddr[3][ORC_MAX_THETA];
+        memset(ddr, 0, sizeof(ddr));
+        if (kap != 0.0) {
+            if (p->chem_mode == 1) {
+                for (int a = 0; a < d; ++a) ddr[a][0] = kap * p->fixed_grad[a];
+            } else {
+                int nodes[8][3];
+                double w[8], dw[8][3];
+                int nc = orc_corners(p, pos + i * d, nodes, w);
+                orc_corner_derivs(p, pos + i * d, dw);
+                for (int m = 0; m < nc; ++m)
+                    for (int a = 0; a < d; ++a) {
+                        double gm = orc_node_grad(p, c, nodes[m], a);
+                        ddr[a][0] += kap * w[m] * gm;  /* d/dchi */
+                        for (int k = 0; k < P; ++k) {
+                            double wdx = 0.0;
+                            for (int b = 0; b < d; ++b) wdx += dw[m][b] * dpos[(i * d + b) * P + k];
+                            double dgm = dc ? orc_node_grad_col(p, dc, P, k, nodes[m], a) : 0.0;
+                            ddr[a][k] += p->chi * kap * (wdx * gm + w[m] * dgm);
+                        }
+                    }
+            }
+        }
+        for (int a = 0; a < d; ++a)
+            for (int k = 0; k < P; ++k) dstep[(i * d + a) * P + k] = t.dF[a][k] + ddr[a][k];
+    }
+    orc_cells_free(&cl);
+    /* the move (primal as orc_move) and its tangent */
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        double xi[4];
+        orc_normals(p->seed, ids[i], (uint64_t)step, ORC_TAG_MOVE, xi);
+        int s = sp[i];
+        double amp = sqrt(2.0 * p->D[s] * p->dt);
+        double damp = amp > 0.0 ? p->dt / amp : 0.0;  /* d amp / d D_s */
+        for (int a = 0; a < d; ++a) {
+            double x0 = pos[i * d + a];
+            double x1 = x0 + p->dt * (F[i * d + a] + drift[i * d + a]) + amp * xi[a];
+            double sg = orc_boundary_sign(p, a, x1);
+            pos[i * d + a] = orc_boundary(p, a, x1);
+            for (int k = 0; k < P; ++k) {
+                double v = dpos[(i * d + a) * P + k] + p->dt * dstep[(i * d + a) * P + k];
+                if (k == 2 + s) v += damp * xi[a];
+                dpos[(i * d + a) * P + k] = sg * v;
+            }
+        }
+    }
+    free(F);
+    free(drift);
+    free(dstep);
+    if (p->chem_mode != 0) return 0;
+    /* deposit at X^{n+1} and its tangent */
+    int64_t G = orc_grid_size(p);
+    double *S = (double *)malloc(sizeof(double) * (size_t)G);
+    double *R = (double *)malloc(sizeof(double) * (size_t)G);
+    double *dS = (double *)calloc((size_t)(G * P), sizeof(double));
+    double *dR = (double *)calloc((size_t)(G * P), sizeof(double));
+    orc_deposit(p, n, pos, sp, S, R);
+    double hd = 1.0;
+    for (int a = 0; a < d; ++a) hd *= orc_grid_h(p, a);
+    for (int64_t i = 0; i < n; ++i) {
+        double ks = p->secrete[sp[i]], kap = p->consume[sp[i]];
+        if (ks == 0.0 && kap == 0.0) continue;
+        int nodes[8][3];
+        double w[8], dw[8][3];
+        int nc = orc_corners(p, pos + i * d, nodes, w);
+        orc_corner_derivs(p, pos + i * d, dw);
+        for (int m = 0; m < nc; ++m) {
+            int64_t g = orc_gidx(p, nodes[m]);
+            double vol = orc_tau(p, nodes[m]) * hd;
+            for (int k = 0; k < P; ++k) {
+                double wdx = 0.0;
+                for (int b = 0; b < d; ++b) wdx += dw[m][b] * dpos[(i * d + b) * P + k];
+                dS[g * P + k] += p->dt * ks * wdx / vol;
+                dR[g * P + k] += kap * wdx / vol;
+            }
+        }
+    }
+    /* PDE substeps c^n -> c^{n+1} and their tangent */
+    int ns = orc_substeps(p);
+    double dts = p->dt / ns;
+    double *tmp = (double *)malloc(sizeof(double) * (size_t)G);
+    double *dtmp = (double *)malloc(sizeof(double) * (size_t)(G * P));
+    int N0 = orc_gdim(p, 0), N1 = orc_gdim(p, 1), N2 = orc_gdim(p, 2);
+    for (int m = 0; m < ns; ++m) {
+#pragma omp parallel for schedule(static)
+        for (int64_t z = 0; z < N2; ++z)
+            for (int64_t y = 0; y < N1; ++y)
+                for (int64_t x = 0; x < N0; ++x) {
+                    int k3[3] = {(int)x, (int)y, (int)z};
+                    int64_t g = orc_gidx(p, k3);
+                    int wall = 0;
+                    for (int a = 0; a < d; ++a)
+                        if (k3[a] == 0 || k3[a] == p->grid[a] - 1) wall = 1;
+                    for (int k = 0; k < P; ++k) {
+                        if (p->pde_bc == 1 && wall) {
+                            dtmp[g * P + k] = dc[g * P + k];
+                            continue;
+                        }
+                        double lap = 0.0;
+                        for (int a = 0; a < d; ++a) {
+                            int kp[3] = {k3[0], k3[1], k3[2]}, km[3] = {k3[0], k3[1], k3[2]};
+                            kp[a] = orc_nbr(p, a, k3[a] + 1);
+                            km[a] = orc_nbr(p, a, k3[a] - 1);
+                            double h = orc_grid_h(p, a);
+                            lap += (dc[orc_gidx(p, kp) * P + k] - 2.0 * dc[g * P + k] + dc[orc_gidx(p, km) * P + k]) / (h * h);
+                        }
+                        double rhs = p->Dc * lap - p->gamma * dc[g * P + k] - R[g] * dc[g * P + k] - dR[g * P + k] * c[g];
+                        dtmp[g * P + k] = dc[g * P + k] + dts * rhs + dS[g * P + k] / ns;
+                    }
+                }
+        orc_pde_substep(p, c, S, R, ns, tmp);
+        memcpy(c, tmp, sizeof(double) * (size_t)G);
+        memcpy(dc, dtmp, sizeof(double) * (size_t)(G * P));
+    }
+    free(S);
+    free(R);
+    free(dS);
+    free(dR);
+    free(tmp);
+    free(dtmp);
+    return 0;
+}
+
+/* nsteps tangent steps from absolute step index step0 (see orc_step_tangent). */
+int orc_run_tangent(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const uint32_t *ids,
+                    double *c, int64_t step0, int64_t nsteps, int P, double *dpos, double *dc)
+{
+    for (int64_t k = 0; k < nsteps; ++k) {
+        int r = orc_step_tangent(p, n, pos, sp, ids, c, step0 + k, P, dpos, dc);
+        if (r) return r;
+    }
+    return 0;
+}

@@ -165,6 +165,8 @@ def _declare(L):
     L.orc_move.argtypes = [P, i64, vp, vp, vp, vp, i64, vp, vp, vp]
     L.orc_step.argtypes = [P, i64, vp, vp, vp, vp, i64, vp, vp, vp]
     L.orc_run.argtypes = [P, i64, vp, vp, vp, vp, i64, i64, vp]
+    L.orc_run_tangent.argtypes = [P, i64, vp, vp, vp, vp, i64, i64, ctypes.c_int, vp, vp]
+    L.orc_run_tangent.restype = ctypes.c_int
 
 
 def _ptr(a):
@@ -390,3 +392,37 @@ def run(params: dict, pos, species, c=None, step0: int = 0, nsteps: int = 1, ids
     lib().orc_run(ctypes.byref(p), n, _ptr(pos), _ptr(sp), _ptr(ids), _ptr(cg), int(step0), int(nsteps),
                   _ptr(dsp))
     return pos, sp, (cg if p.chem_mode == 0 else None), dsp
+
+
+def run_tangent(params: dict, pos, species, c=None, step0: int = 0, nsteps: int = 1, ids=None,
+                dpos=None, dc=None):
+    """nsteps steps with their forward-mode derivative with respect to
+    theta = (chi, inter, D_0 .. D_{ns-1}), the noise frozen (the tangent of
+    the step written out operation by operation; see orc_step_tangent).
+    Returns (pos, species, c, dpos, dc): dpos[i, a, k] = dX_ia / dtheta_k
+    and dc[..., k] = dc / dtheta_k (grid shape + (P,); None without a grid).
+    dpos / dc carry in a previous tangent (zero: fixed initial data). The
+    positions, species and field are those of run() bit for bit."""
+    p = make_params(params)
+    pos = _pos(pos, p.dim).copy()
+    sp = _u8(species).copy()
+    n = pos.shape[0]
+    P = 2 + int(p.n_species)
+    ids = np.arange(n, dtype=np.uint32) if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
+    if p.chem_mode == 0:
+        cg = _grid(c if c is not None else np.zeros(grid_shape(params)), params).copy()
+        G = int(cg.size)
+        dcg = np.zeros((G, P)) if dc is None else np.ascontiguousarray(np.asarray(dc, np.float64).reshape(G, P)).copy()
+    else:
+        cg = np.zeros(1)
+        dcg = np.zeros((1, P))
+    dp = np.zeros((n, p.dim, P)) if dpos is None else np.ascontiguousarray(np.asarray(dpos, np.float64)).copy()
+    r = lib().orc_run_tangent(ctypes.byref(p), n, _ptr(pos), _ptr(sp), _ptr(ids), _ptr(cg), int(step0),
+                              int(nsteps), P, _ptr(dp), _ptr(dcg))
+    if r:
+        raise ValueError("run_tangent: %s" % ("Euler-Maruyama with cloud-in-cell deposit only, no reactions or "
+                                             "hard spheres" if r == -1 else "wrong parameter count"))
+    if p.chem_mode != 0:
+        return pos, sp, None, dp, None
+    return pos, sp, cg, dp, dcg.reshape(tuple(grid_shape(params)) + (P,))
+
