@@ -902,6 +902,8 @@ void orc_run(const orc_params *p, int64_t n, double *pos, uint8_t *sp, const uin
 /*   reflection negates the tangent, a periodic wrap keeps it; the deposit   */
 /*   differentiates the weights; the PDE substep is linear in (c, S) and    */
 /*   bilinear in (R, c).                                                     */
+/* Columns past 2 + ns carry no parameter: seeded by the caller (a direction */
+/* in the initial positions), they give directional derivatives.            */
 /* Supported: Euler-Maruyama, cloud-in-cell deposit, no reactions and no    */
 /* hard-sphere correction (returns -1 otherwise; -2 for a wrong P).         */
 /* ------------------------------------------------------------------------ */
@@ -991,7 +993,7 @@ int orc_step_tangent(const orc_params *p, int64_t n, double *pos, uint8_t *sp, c
                      double *c, int64_t step, int P, double *dpos, double *dc)
 {
     if (p->move_scheme != 0 || p->hard_sphere || p->reactions || p->deposit_kernel != 0) return -1;
-    if (P != 2 + p->n_species || P > ORC_MAX_THETA) return -2;
+    if (P < 2 + p->n_species || P > ORC_MAX_THETA) return -2;
     const int d = p->dim;
     double *F = (double *)malloc(sizeof(double) * (size_t)(n * d + 1));
     double *drift = (double *)malloc(sizeof(double) * (size_t)(n * d + 1));

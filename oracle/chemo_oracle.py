@@ -395,19 +395,22 @@ def run(params: dict, pos, species, c=None, step0: int = 0, nsteps: int = 1, ids
 
 
 def run_tangent(params: dict, pos, species, c=None, step0: int = 0, nsteps: int = 1, ids=None,
-                dpos=None, dc=None):
+                dpos=None, dc=None, extra: int = 0):
     """nsteps steps with their forward-mode derivative with respect to
     theta = (chi, inter, D_0 .. D_{ns-1}), the noise frozen (the tangent of
     the step written out operation by operation; see orc_step_tangent).
     Returns (pos, species, c, dpos, dc): dpos[i, a, k] = dX_ia / dtheta_k
     and dc[..., k] = dc / dtheta_k (grid shape + (P,); None without a grid).
     dpos / dc carry in a previous tangent (zero: fixed initial data). The
-    positions, species and field are those of run() bit for bit."""
+    positions, species and field are those of run() bit for bit. `extra`
+    columns after the parameters carry no parameter: seeded through dpos
+    (a direction in the initial positions) they give directional
+    derivatives."""
     p = make_params(params)
     pos = _pos(pos, p.dim).copy()
     sp = _u8(species).copy()
     n = pos.shape[0]
-    P = 2 + int(p.n_species)
+    P = 2 + int(p.n_species) + int(extra)
     ids = np.arange(n, dtype=np.uint32) if ids is None else np.ascontiguousarray(ids, dtype=np.uint32)
     if p.chem_mode == 0:
         cg = _grid(c if c is not None else np.zeros(grid_shape(params)), params).copy()

@@ -172,6 +172,38 @@ def test_initial_position_gradient_matches_oracle_finite_differences():
             assert abs(gx[i, a] - fd) <= 0.03 * abs(fd) + 2e-3 * np.abs(gx).max(), (i, a, gx[i, a], fd)
 
 
+def _tangent_direction(p, pos, sp, c0, nsteps, v, nb=NB):
+    """dL/dX_0 . v of the oracle's FP64 trajectory: a free tangent column
+    seeded with v, contracted with dL/dX_N, plus the loss's own dL/dX_0 . v."""
+    P = 2 + int(p["n_species"])
+    d0 = np.zeros(pos.shape + (P + 1,))
+    d0[:, :, P] = v
+    x0 = np.asarray(pos, np.float64)
+    xN, _, _, dx, _ = orc.run_tangent(p, x0, sp, None if c0 is None else c0.astype(np.float64), nsteps=nsteps,
+                                      dpos=d0, extra=1)
+    xt = torch.from_numpy(xN).requires_grad_(True)
+    x0t = torch.from_numpy(x0).requires_grad_(True)
+    L = adj.mean_x_displacement(xt, x0t) + adj.occupancy_loss(xt, nb, p["lo"], p["hi"])
+    L.backward()
+    return float((xt.grad.numpy() * dx[:, :, P]).sum() + (x0t.grad.numpy() * v).sum())
+
+
+@pytest.mark.parametrize("kind,over", [("2d", dict()), ("2d", dict(pde_substeps=5, Dc=20.0, boundary=1, pde_bc=2)),
+                                       ("3d", dict())])
+def test_initial_position_gradient_matches_oracle_tangent(kind, over):
+    """The gradient with respect to every initial position, projected on
+    three random directions, against the oracle's directional derivative
+    (its tangent seeded with the direction)."""
+    p, pos, sp, c0, nsteps, every, nb = _tangent_case(kind, over)
+    _, _, gx = _gpu_grads(p, pos, sp, c0, nsteps, every, nb=nb)
+    rng = np.random.default_rng(11)
+    for r in range(3):
+        v = rng.standard_normal(pos.shape)
+        want = _tangent_direction(p, pos, sp, c0, nsteps, v, nb=nb)
+        got = float((gx * v).sum())
+        assert abs(got - want) <= 2e-3 * abs(want), (r, got, want)
+
+
 def test_record_leaves_final_state_and_gradient_restores_it():
     p, pos, sp, c0 = _setup(n=1000)
     dpos = torch.from_numpy(pos).cuda()

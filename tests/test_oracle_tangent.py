@@ -123,3 +123,25 @@ def test_tangent_fixed_gradient_drift_closed_form():
     kap = np.asarray(p["chemotactic"], np.float32).astype(np.float64)[sp]
     want = steps * dt * kap[:, None] * np.asarray([float(np.float32(v)) for v in g[:2]])[None, :]
     np.testing.assert_allclose(dx[:, :, 0], want, rtol=1e-12, atol=1e-18)
+
+
+@pytest.mark.parametrize("label,name,over,dim,steps", [CASES[0], CASES[2], CASES[5]])
+def test_tangent_direction_in_initial_positions(label, name, over, dim, steps):
+    # a free column seeded with a direction v in the initial positions is the
+    # directional derivative of the trajectory: central differences of run()
+    # from X_0 +- h v
+    p, pos, sp, c = _case(name, over, dim)
+    P = 2 + int(p["n_species"])
+    v = np.random.default_rng(8).standard_normal(pos.shape)
+    d0 = np.zeros(pos.shape + (P + 1,))
+    d0[:, :, P] = v
+    x0 = pos.astype(np.float64)
+    _, _, cN, dx, dc = orc.run_tangent(p, x0, sp, c, nsteps=steps, dpos=d0, extra=1)
+    h = 2.0 ** -24
+    xp, _, cp, _ = orc.run(p, x0 + h * v, sp, c, nsteps=steps)
+    xm, _, cm, _ = orc.run(p, x0 - h * v, sp, c, nsteps=steps)
+    fd = (xp - xm) / (2 * h)
+    assert np.abs(fd - dx[:, :, P]).max() <= 1e-5 * np.abs(fd).max(), label
+    if cN is not None:
+        fdc = (cp - cm) / (2 * h)
+        assert np.abs(fdc - dc[..., P]).max() <= 1e-4 * np.abs(fdc).max(), label
