@@ -145,3 +145,50 @@ def test_tangent_direction_in_initial_positions(label, name, over, dim, steps):
     if cN is not None:
         fdc = (cp - cm) / (2 * h)
         assert np.abs(fdc - dc[..., P]).max() <= 1e-4 * np.abs(fdc).max(), label
+
+
+def _golden(name):
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    return os.path.join(here, name)
+
+
+def test_tangent_growth_golden_reproduces_and_matches_differences():
+    # tests/golden/adjoint_tangent_growth.txt: the exact gradient of the
+    # differentiable workload's loss along the oracle trajectory against the
+    # horizon K. Its first steps recompute exactly; up to K = 5 the central
+    # differences of adjoint_fd_horizon.txt (their two steps agreeing within
+    # 1 %) equal it; and it grows by many orders (the dynamics is chaotic
+    # under frozen noise). At K = 7 the two differences still agree with
+    # each other but not with the tangent (dL/dD_1 6.945e-3 against
+    # 7.268e-3): a pair lies within the step of its cutoff, where the
+    # shifted force's derivative jumps, so both differences straddle the
+    # kink and average its two slopes, while the tangent is the slope at
+    # theta itself
+    import importlib.util
+    tan = {}
+    for line in open(_golden("adjoint_tangent_growth.txt")):
+        if line.startswith("#"):
+            continue
+        f = line.split()
+        tan[int(f[0])] = np.array([float(v) for v in f[1:5]])
+    fd = {}
+    for line in open(_golden("adjoint_fd_horizon.txt")):
+        if line.startswith("#"):
+            continue
+        f = line.split()
+        fd[int(f[0])] = (np.array([float(v) for v in f[7:11]]), float(f[12]))
+    spec = importlib.util.spec_from_file_location("tangent_growth", _golden("adjoint_tangent_growth.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    p, x, sp = wl.initial_state("adjoint_2d")
+    x0 = x.astype(np.float64)
+    pos, _, _, dpos, _ = orc.run_tangent(p, x0, sp, np.zeros(orc.grid_shape(p)), nsteps=3)
+    g = np.einsum("ia,iak->k", mod.loss_and_grad(pos, x0)[1], dpos)
+    np.testing.assert_allclose(g, tan[3], rtol=1e-6, atol=1e-12)
+    resolved = [k for k, (_, agree) in fd.items() if agree < 0.01 and k <= 5]
+    assert len(resolved) == 4
+    for k in resolved:
+        g_fd, _ = fd[k]
+        assert np.all(np.abs(g_fd - tan[k]) <= 5e-3 * (np.abs(tan[k]) + np.abs(tan[k]).max())), k
+    assert np.abs(tan[200]).max() > 1e18 * np.abs(tan[5]).max()
